@@ -1,0 +1,24 @@
+"""CPU oracle for the xTC grid build (test infrastructure only).
+
+Plain, slow FP64 numpy restatements of the paper (arXiv 2304.07006), written
+from its equations and sharing nothing with the CUDA library:
+
+* ``jastrow``     -- the Jastrow factor u(r1, r2) and its gradient with respect
+                     to the first electron (the nabla_1 u in the three-body L).
+* ``direct``      -- Route 2: the restricted closed-shell working equations of
+                     Appendix B (Delta U, Delta h, <Phi0|L|Phi0>), with the
+                     intermediate vector field V of the "Decomposition of two-body
+                     correction" section.
+* ``bruteforce``  -- Route 1: the six-index L from eq. (Ldecomp) or from the
+                     literal triple quadrature of its definition, normal-ordered
+                     explicitly in spin orbitals with eqs. (dU), (Delta h with the
+                     two-body density), (zero-body) and (1Ddens).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU baseline leg of
+``bench.py`` may import this package; the library never does.
+
+Parity status: every function here is pinned by CPU tests
+(``tests/test_oracle_*.py``) against finite differences, the literal triple
+quadrature, the paper's own identities between its two routes, symmetry and
+homogeneity invariants and a closed form for a separable Jastrow factor.
+"""
