@@ -1,0 +1,311 @@
+"""Benchmark of the xTC one-/two-body build (steps a-d) on one GB300.
+
+One step = one complete xTC build of the N2/CO-like workload (N = 120 orbitals, 100,000
+grid points, 7 doubly occupied orbitals, 2 Jastrow centre sets x 9 terms): Delta U, Delta h and
+the constant, in the mixed-precision path.  The metric is algorithmic TFLOP/s of the build,
+
+    F = F_b + F_c + F_d,  F_b = 2*3*N_g^2*N_pair,  F_c = 12*N_g*N^3,  F_d = 2*4*N_g*N_pair^2,
+
+divided by the device time of one build (inputs resident in HBM).  The per-step working set
+(pair-product tables of several GB) is far larger than L2, so no flush is needed between steps.
+
+Also reported: the same metric end to end through the C ABI with host buffers (``e2e``), the
+roofline of the dominant kernel (steps a+b on the tensor cores), the FP64 GPU path timed on
+sampled outer points (time is linear in the outer sum) with the mixed/FP64 speed ratio, the
+mixed-vs-FP64 error in Hartree on those points, and the CPU oracle timed on a bounded sample.
+
+``--impl reference`` times the CPU oracle (the plain FP64 numpy restatement of the paper) on
+the same workload and metric instead.  With several GPUs (torchrun) every rank runs an
+independent replica (the build does not shard in this version) and the value is the sum.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "n2"
+METRIC = "xTC 2-body build TFLOP/s & seconds at N=120 (mixed vs FP64, same GB300) at stated Eh error"
+
+
+def flops(n_orb: int, n_grid: int, n_outer: int | None = None) -> dict:
+    n_outer = n_grid if n_outer is None else n_outer
+    npair = n_orb * (n_orb + 1) // 2
+    fb = 2.0 * 3 * n_outer * n_grid * npair
+    fc = 12.0 * n_outer * n_orb ** 3
+    fd = 2.0 * 4 * n_outer * npair * npair
+    return {"b": fb, "c": fc, "d": fd, "total": fb + fc + fd}
+
+
+def config_dict(p, prec):
+    return {"workload": f"{WORKLOAD}: N2/CO-like diatomic at 2.07 bohr, N={p.n_orb} orbitals, "
+                        f"{p.n_grid} grid points, {p.n_occ} doubly occupied, {p.n_sets} Jastrow centre sets x "
+                        f"{p.terms.shape[0]} terms",
+            "n_orb": p.n_orb, "n_grid": p.n_grid, "n_occ": p.n_occ, "precision": prec,
+            "l2": "per-step working set (rho split tables, several GB) >> 129 MB L2; no flush needed"}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.send_signal(signal.SIGTERM)
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, name in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def oracle_sample(p, n_sample: int, seed: int = 0):
+    """Times the CPU oracle on n_sample outer points (full inner sum)."""
+    from oracle import direct
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(p.n_grid, size=n_sample, replace=False))
+    t0 = time.perf_counter()
+    direct.build(p, outer=idx, i_block=n_sample)
+    dt = time.perf_counter() - t0
+    f = flops(p.n_orb, p.n_grid, n_sample)["total"]
+    return {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "seconds": dt,
+            "sample": f"{n_sample} random outer grid points of the {WORKLOAD} workload with the full inner sum "
+                      f"(the build is linear in the outer sum); numpy FP64, BLAS threads = all host cores"}
+
+
+def run_reference(args):
+    import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = synth.make_config(WORKLOAD)
+    n_sample = 2
+    for _ in range(args.warmup):
+        oracle_sample(p, n_sample)
+    times, vals = [], []
+    for s in range(args.steps):
+        r = oracle_sample(p, n_sample, seed=s + 1)
+        times.append(r["seconds"])
+        vals.append(r["value"])
+    value = float(np.mean(vals))
+    cpu = {"value": value, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": r["sample"].replace(f"{n_sample} random", f"{n_sample} random")}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(p, "fp64 (CPU oracle)"), "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp16x2", choices=["fp16x2", "bf16x3"])
+    ap.add_argument("--fp64-sample", type=int, default=512, help="outer points for the FP64 GPU comparison")
+    ap.add_argument("--cpu-sample", type=int, default=4, help="outer points for the CPU oracle baseline")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import synth
+    from paper_2304_07006_gb300 import Context
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    p = synth.make_config(WORKLOAD)
+    N, NG = p.n_orb, p.n_grid
+    F = flops(N, NG)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    grid, w, phi, gamma = t(p.grid), t(p.weights), t(p.phi), t(p.gamma)
+    dU = torch.empty((N,) * 4, dtype=torch.float64, device=dev)
+    dh = torch.empty((N, N), dtype=torch.float64, device=dev)
+    e0 = torch.empty(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    ctx = Context(args.precision, device=local, stream=stream.cuda_stream, timing=True)
+    ctx.set_jastrow(p.nuc_xyz, p.nuc_set, p.terms, p.coef)
+    run = lambda: ctx.build(grid, w, phi, gamma, dU=dU, dh=dh, e0=e0)
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern_ms = np.zeros(5)
+    kern_n = np.zeros(5, dtype=np.int64)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        run()
+        tm = ctx.timings()
+        kern_ms += np.array([v[0] for v in tm.values()])
+        kern_n += np.array([v[1] for v in tm.values()])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    if dist:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    value = world * F["total"] / (ms_step * 1e-3) / 1e12
+
+    # roofline of the dominant kernel: steps (a)+(b), per-launch algorithmic flops / mean launch time
+    names = ["prep", "vfield", "fields", "assemble", "final"]
+    per_kernel = {names[k]: {"ms_per_step": kern_ms[k] / args.steps, "launches_per_step": int(kern_n[k] // args.steps)}
+                  for k in range(5)}
+    n_vf = kern_n[1] / args.steps
+    vf_ms = kern_ms[1] / max(kern_n[1], 1)
+    vf_flops_launch = F["b"] / n_vf
+    peaks, peak_src = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    achieved = vf_flops_launch / (vf_ms * 1e-3) / 1e12
+    issued_factor = 3 if args.precision == "fp16x2" else 6
+    roofline = {"kernel": "vfield (steps a+b, tcgen05 split-precision GEMM with fused Jastrow gradient)",
+                "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peak_src} bf16 dense sustained (fp16 nominal ratio 1:1)",
+                "issued_tflops": achieved * issued_factor,
+                "issued_frac": achieved * issued_factor / peak,
+                "launch_ms": vf_ms, "algorithmic_flops_per_launch": vf_flops_launch}
+    asm_ms = kern_ms[3] / max(kern_n[3], 1)
+    asm_ach = F["d"] / (kern_n[3] / args.steps) / (asm_ms * 1e-3) / 1e12
+    assemble = {"bound": "tensor", "achieved": asm_ach, "issued_tflops": asm_ach * 6, "frac": asm_ach / peak,
+                "issued_frac": asm_ach * 6 / peak, "launch_ms": asm_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "seconds_per_build": ms_step / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16x2 split (steps a+b) / bf16x3 split (step d), f32 tensor accumulate, f64 chunk sums"
+            if args.precision == "fp16x2" else "bf16x3 split, f32 tensor accumulate, f64 chunk sums",
+            "data": "synthetic", "config": config_dict(p, args.precision),
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "algorithmic_flops_per_build": F, "roofline": roofline, "assemble_roofline": assemble,
+            "per_kernel": per_kernel, "clocks": clk,
+            "gpu_launches": int(kern_n.sum())}
+
+    if rank == 0:
+        # FP64 GPU path and the mixed error, on sampled outer points (same kernels, outer range)
+        rng = np.random.default_rng(7)
+        perm = rng.permutation(NG)
+        ps = synth.permute_grid(p, perm)
+        S = args.fp64_sample
+        res = {}
+        for prec in ("fp64", args.precision):
+            with Context(prec, device=local, timing=True) as c:
+                c.set_jastrow(ps.nuc_xyz, ps.nuc_set, ps.terms, ps.coef)
+                c.set_outer_range(0, S)
+                c.build(ps.grid, ps.weights, ps.phi, ps.gamma, want_dU=False)  # warm-up
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                out = c.build(ps.grid, ps.weights, ps.phi, ps.gamma)
+                dt = time.perf_counter() - t0
+                tm = c.timings()
+                dev_ms = sum(v[0] for k, v in tm.items() if k != "prep")
+                res[prec] = (out, dt, dev_ms, tm)
+        full_fp64_s = res["fp64"][2] / 1e3 * NG / S
+        err = {k: float(np.abs(np.asarray(res[args.precision][0][k]) - np.asarray(res["fp64"][0][k])).max())
+               for k in ("dU", "dh", "e0")}
+        line["fp64_path"] = {"sample_outer_points": S, "device_ms_on_sample": res["fp64"][2],
+                             "seconds_per_build_extrapolated": full_fp64_s,
+                             "tflops_extrapolated": F["total"] / full_fp64_s / 1e12,
+                             "mixed_speedup_vs_fp64": full_fp64_s / (ms_step / 1e3)}
+        line["error_eh_vs_fp64_gpu"] = dict(err, sample=f"{S} random outer points, full inner sum; max |diff| "
+                                                         f"over every Delta U / Delta h entry and the constant")
+
+        # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hg, hw, hphi, hgam = pin(p.grid), pin(p.weights), pin(p.phi), pin(p.gamma)
+        hdU = torch.empty((N,) * 4, dtype=torch.float64).pin_memory()
+        hdh = torch.empty((N, N), dtype=torch.float64).pin_memory()
+        he0 = torch.empty(1, dtype=torch.float64).pin_memory()
+        ctx.build(hg, hw, hphi, hgam, dU=hdU, dh=hdh, e0=he0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ctx.build(hg, hw, hphi, hgam, dU=hdU, dh=hdh, e0=he0)
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        h2d = sum(int(a.numel()) * 8 for a in (hg, hw, hphi, hgam))
+        d2h = sum(int(a.numel()) * 8 for a in (hdU, hdh, he0))
+        line["e2e"] = {"value": F["total"] / dt / 1e12, "unit": "TFLOP/s", "seconds_per_build": dt,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        line["cpu_baseline"] = oracle_sample(p, args.cpu_sample)
+        line["cpu_baseline"].pop("seconds", None)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

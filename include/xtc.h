@@ -1,0 +1,163 @@
+/*
+ * xtc.h -- C ABI of the GB300 (sm_103a) grid-quadrature build of the xTC
+ * corrections (arXiv 2304.07006).
+ *
+ * The library computes, on one GPU and without ever forming the six-index
+ * three-body tensor L, the three outputs of eq. (xTC):
+ *
+ *   dU[p][q][r][s] = Delta U_pr^qs        two-body correction, chemists' (pq|rs) order
+ *   dh[p][q]       = Delta h_p^q          one-body correction
+ *   e0             = <Phi0|L|Phi0>        constant added to E_nuc
+ *
+ * for a closed-shell reference with real orbitals, using the restricted
+ * closed-shell working equations of Appendix B together with the intermediate
+ * V_rs(i) = sum_j w_j phi_r(j) nabla_1 u(r_i, r_j) phi_s(j) of the section
+ * "Decomposition of two-body correction" (eq. Ldecomp).  The path has four
+ * steps, all in the library's own CUDA kernels:
+ *   (a) the Jastrow gradient nabla_1 u over grid-point pairs,
+ *   (b) the vector pair fields V (a dense contraction over the inner grid index),
+ *   (c) the density-contracted intermediates rho, W, Vt, X, Zt, Wt, Y, Z, A, B,
+ *   (d) Delta U = -P^(pq)_(rs) sum_i (rho_pq A_rs + V_pq . B_rs), then
+ *       Delta h = -1/2 (2 Delta U_pr^qs gamma_rs - Delta U_pr^sq gamma_rs) and
+ *       e0 = -2/3 Delta h_pq gamma_pq.
+ *
+ * Units are Hartree atomic units (bohr, Eh).  Conventions:
+ *   - gamma is the per-spin (alpha) density matrix; the spin factor 2 is explicit
+ *     in the equations (Appendix B).  It must be symmetric.
+ *   - The Jastrow factor is u(r1,r2) = sum_I sum_t c[set(I)][t]
+ *       (a1^m a2^n + a1^n a2^m) b^o, a_k = |r_k - R_I|/(1 + |r_k - R_I|),
+ *       b = r12/(1 + r12), t = (m, n, o) with 0 <= m, n, o <= 2.
+ *   - Where a unit vector is undefined (r12 = 0, including the grid diagonal
+ *     j = i, or a point on a nucleus) its contribution to nabla_1 u is zero.
+ *
+ * Ownership and memory: the caller owns every input and output buffer.  Each
+ * pointer may address host memory or device memory of the context's device;
+ * the library detects which.  The library owns only its device workspace,
+ * allocated on first use, reused by later calls of the same sizes, and released
+ * by xtc_destroy.  Calls are synchronous with respect to the host: when a call
+ * returns XTC_OK its outputs are complete (device outputs included).  All
+ * device work is issued on the stream given in xtc_params.  One context must
+ * not be used by two host threads at once.
+ *
+ * Errors: every function returns an xtc_status (0 = success).  Nothing throws
+ * across the ABI.  xtc_strerror gives a static message; xtc_last_error_detail
+ * gives a per-context message describing the last failure.
+ */
+#ifndef XTC_H
+#define XTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define XTC_API __attribute__((visibility("default")))
+#else
+#define XTC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct xtc_ctx xtc_ctx;
+
+typedef enum {
+  XTC_OK = 0,
+  XTC_ERR_ARG = -1,           /* bad size, null pointer where one is required, term out of range */
+  XTC_ERR_NOT_SYMMETRIC = -2, /* gamma is not symmetric to 1e-12 relative */
+  XTC_ERR_NONFINITE = -3,     /* NaN or Inf in an input */
+  XTC_ERR_OOM = -4,           /* device workspace allocation failed */
+  XTC_ERR_CUDA = -5,          /* a CUDA runtime or driver call failed */
+  XTC_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up (kernel returned early) */
+  XTC_ERR_STATE = -7,         /* xtc_set_jastrow not called, or context unusable */
+  XTC_ERR_UNSUPPORTED = -8    /* device is not sm_103 / sm_100 class */
+} xtc_status;
+
+typedef enum {
+  XTC_PREC_FP64 = 0,   /* all four steps in FP64 (SIMT) */
+  XTC_PREC_FP16X2 = 1, /* step (b): 2-term FP16 split (3 tensor-core products) with power-of-2 scaling;
+                          step (d): 3-term BF16 split (6 products); FP32 accumulation in TMEM;
+                          FP64 accumulation of Delta U across grid chunks, of Delta h and of e0 */
+  XTC_PREC_BF16X3 = 2  /* steps (b) and (d): 3-term BF16 split (6 products), otherwise as FP16X2 */
+} xtc_precision;
+
+typedef struct {
+  int device;          /* CUDA device ordinal */
+  void* stream;        /* cudaStream_t for all device work; NULL = the legacy default stream */
+  int precision;       /* xtc_precision */
+  int64_t grid_chunk;  /* outer grid points per chunk (multiple of 128); 0 = automatic */
+  int split_k;         /* inner-grid slices of step (b) accumulated separately (1..16); 0 = automatic */
+  int timing;          /* non-zero: record CUDA events around every kernel (see xtc_get_timings) */
+} xtc_params;
+
+/* Fills *p with defaults: device 0, default stream, XTC_PREC_FP16X2, automatic chunking. */
+XTC_API void xtc_default_params(xtc_params* p);
+
+/* Creates a context bound to p->device.  *out receives the handle (NULL on failure).
+ * Errors: XTC_ERR_ARG (null), XTC_ERR_CUDA, XTC_ERR_UNSUPPORTED (compute capability < 10.0). */
+XTC_API int xtc_create(xtc_ctx** out, const xtc_params* p);
+
+/* Releases the context and its device workspace.  Accepts NULL. */
+XTC_API int xtc_destroy(xtc_ctx* ctx);
+
+/* Static message for a status code. */
+XTC_API const char* xtc_strerror(int status);
+
+/* Detail of the last error on this context (static storage owned by the context). */
+XTC_API const char* xtc_last_error_detail(const xtc_ctx* ctx);
+
+/* Jastrow factor (Results, "Computational details" gives the paper's DTN form; this
+ * library takes the polynomial form in the header comment).  Host arrays, copied.
+ *   n_nuc    >= 1        nuclei
+ *   nuc_xyz  [n_nuc][3]  bohr
+ *   nuc_set  [n_nuc]     centre-set index of each nucleus, 0 <= nuc_set[I] < n_sets
+ *   n_terms  >= 1, mno [n_terms][3] = (m, n, o), each in 0..2
+ *   coef     [n_sets][n_terms]
+ * Errors: XTC_ERR_ARG, XTC_ERR_NONFINITE. */
+XTC_API int xtc_set_jastrow(xtc_ctx* ctx, int n_nuc, const double* nuc_xyz, const int* nuc_set, int n_sets,
+                    int n_terms, const int* mno, const double* coef);
+
+/* Restricts the outer grid sum over i (eqs. Ldecomp, tcmf:2el) to points
+ * [begin, end); end < 0 means n_grid.  The inner sum over j always covers the
+ * whole grid.  The outputs are linear in the outer sum, so disjoint ranges add
+ * up to the full result.  Default: the whole grid. */
+XTC_API int xtc_set_outer_range(xtc_ctx* ctx, int64_t begin, int64_t end);
+
+/* The xTC build (steps a-d).
+ *   n_grid >= 1, n_orb >= 1
+ *   grid_xyz [n_grid][3], weights [n_grid], phi [n_grid][n_orb] (row-major, real MOs),
+ *   gamma [n_orb][n_orb] symmetric per-spin density           -- inputs, FP64
+ *   dU     [n_orb]^4 FP64 or NULL; dU_f32 [n_orb]^4 FP32 or NULL -- dU[p][q][r][s] = Delta U_pr^qs
+ *   dh     [n_orb][n_orb] FP64 (required), e0 [1] FP64 (required)
+ * Errors: XTC_ERR_ARG, XTC_ERR_STATE, XTC_ERR_NOT_SYMMETRIC, XTC_ERR_NONFINITE,
+ *         XTC_ERR_OOM, XTC_ERR_CUDA, XTC_ERR_TIMEOUT. */
+XTC_API int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
+                   const double* phi, const double* gamma, double* dU, float* dU_f32, double* dh, double* e0);
+
+/* Step (a) alone: out[k][0..2] = nabla_1 u(r1[k], r2[k]) in FP64 arithmetic on the device.
+ * r1, r2 [n][3], out [n][3]. */
+XTC_API int xtc_jastrow_grad(xtc_ctx* ctx, int64_t n, const double* r1, const double* r2, double* out);
+
+/* Steps (a)+(b) alone, in the context's precision, for the outer points [outer_begin, outer_end):
+ * V[k][x][pq] = V_pq(i = outer_begin + k) component x, pq the packed index of p <= q
+ * (pq = p*n_orb - p*(p-1)/2 + (q - p)).  V has (outer_end - outer_begin) * 3 * n_orb(n_orb+1)/2 doubles. */
+XTC_API int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
+               const double* phi, int64_t outer_begin, int64_t outer_end, double* V);
+
+/* Kernel timers of the last build (requires params.timing != 0).  Kernel ids: */
+enum {
+  XTC_K_PREP = 0,     /* per-grid-point tables, orbital transposition, pair products rho (split) */
+  XTC_K_VFIELD = 1,   /* steps (a)+(b) */
+  XTC_K_FIELDS = 2,   /* step (c) */
+  XTC_K_ASSEMBLE = 3, /* step (d): Delta U accumulation */
+  XTC_K_FINAL = 4,    /* Delta U unpacking, Delta h, e0 */
+  XTC_N_KERNELS = 5
+};
+/* ms[k] = summed device milliseconds of kernel class k over the last build, launches[k] = launch
+ * count; either pointer may be NULL.  n = array length (>= XTC_N_KERNELS). */
+XTC_API int xtc_get_timings(xtc_ctx* ctx, double* ms, int64_t* launches, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XTC_H */

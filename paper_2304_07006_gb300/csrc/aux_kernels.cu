@@ -1,0 +1,511 @@
+// Preparation kernels, the FP64 SIMT twins of steps (a)+(b) and (d), and the final kernels
+// (Delta U unpacking, the one-body correction and the constant of Appendix B).
+#include <algorithm>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "jastrow_coef.cuh"
+#include "xtc_internal.cuh"
+
+namespace xtc {
+namespace {
+
+__device__ __forceinline__ int pair_of(int p, int q, int N) {
+  // packed index of the unordered pair {p, q}
+  const int a = min(p, q), b = max(p, q);
+  return a * N - a * (a - 1) / 2 + (b - a);
+}
+
+// ------------------------------------------------------------------ inner-point tables
+__global__ void jtab_kernel(const double* __restrict__ grid, int64_t n_grid, int64_t n_pad,
+                            const JastrowParams* __restrict__ jp, int n_nuc, int js, float* __restrict__ jtab) {
+  const int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (j >= n_pad) return;
+  double x = 1.0e3, y = 1.0e3, z = 1.0e3;  // padding points: far away and finite (their rho is zero)
+  if (j < n_grid) {
+    x = grid[3 * j];
+    y = grid[3 * j + 1];
+    z = grid[3 * j + 2];
+  }
+  // layout (12 floats): x_hi y_hi z_hi a_0 | x_lo y_lo z_lo a_1 | a_2 a_3 0 0, with x = x_hi + x_lo so that
+  // differences of nearby points keep FP64-level accuracy in FP32 arithmetic
+  float* o = jtab + j * js;
+  for (int k = 0; k < js; ++k) o[k] = 0.0f;
+  const float xh = static_cast<float>(x), yh = static_cast<float>(y), zh = static_cast<float>(z);
+  o[0] = xh;
+  o[1] = yh;
+  o[2] = zh;
+  o[4] = static_cast<float>(x - static_cast<double>(xh));
+  o[5] = static_cast<float>(y - static_cast<double>(yh));
+  o[6] = static_cast<float>(z - static_cast<double>(zh));
+  const int slot[4] = {3, 7, 8, 9};
+  for (int I = 0; I < n_nuc && I < 4; ++I) {
+    const double dx = x - jp->nuc[I][0], dy = y - jp->nuc[I][1], dz = z - jp->nuc[I][2];
+    const double d = sqrt(dx * dx + dy * dy + dz * dz);
+    o[slot[I]] = static_cast<float>(d / (1.0 + d));
+  }
+}
+
+__global__ void transpose_phi_kernel(const double* __restrict__ phi, int64_t n_grid, int64_t n_pad, int N,
+                                     double* __restrict__ phiT) {
+  __shared__ double tile[32][33];
+  const int64_t j0 = blockIdx.x * 32ll;
+  const int p0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t j = j0 + k;
+    const int p = p0 + threadIdx.x;
+    tile[k][threadIdx.x] = (j < n_grid && p < N) ? phi[j * N + p] : 0.0;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int p = p0 + k;
+    const int64_t j = j0 + threadIdx.x;
+    if (p < N && j < n_pad) phiT[p * n_pad + j] = tile[threadIdx.x][k];
+  }
+}
+
+__global__ void check_finite_kernel(const double* __restrict__ x, int64_t n, int* flag) {
+  int bad = 0;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    bad |= !isfinite(x[k]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+// ------------------------------------------------------------------ pair products rho
+// colmax[pq] = max_j |w_j phi_p(j) phi_q(j)| (as float bits; values are non-negative)
+__global__ void rho_colmax_kernel(const double* __restrict__ phiT, const double* __restrict__ w, int64_t n_grid,
+                                  int64_t n_pad, int n_pair, const int* __restrict__ pp, const int* __restrict__ pq_,
+                                  unsigned int* __restrict__ colmax) {
+  const int pq = blockIdx.y;
+  const int p = pp[pq], q = pq_[pq];
+  float m = 0.0f;
+  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n_grid;
+       j += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    m = fmaxf(m, static_cast<float>(fabs(w[j] * phiT[p * n_pad + j] * phiT[q * n_pad + j])));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(colmax + pq, __float_as_uint(m));
+}
+
+// power-of-2 exponent that brings the column maximum near 2^14 (fp16 split); 0 when unscaled
+__device__ __forceinline__ int col_exponent(const unsigned int* colmax, int pq, bool scale) {
+  if (!scale) return 0;
+  const float m = __uint_as_float(colmax[pq]);
+  if (!(m > 0.0f)) return 0;
+  int e;
+  frexpf(m, &e);           // m = f * 2^e, f in [0.5, 1)
+  return min(max(14 - e, -60), 60);
+}
+
+template <int PARTS, bool BF16>
+__global__ void rho_split_kernel(const double* __restrict__ phiT, const double* __restrict__ w, int64_t n_grid,
+                                 int64_t n_pad, int n_pair, const int* __restrict__ pp, const int* __restrict__ pq_,
+                                 const unsigned int* __restrict__ colmax, bool scale, int* __restrict__ colexp,
+                                 uint16_t* __restrict__ out) {
+  const int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int pq0 = blockIdx.y * 8;
+  const int64_t part_stride = static_cast<int64_t>(n_pair) * n_pad;
+  for (int u = 0; u < 8; ++u) {
+    const int pq = pq0 + u;
+    if (pq >= n_pair) break;
+    const int e = col_exponent(colmax, pq, scale);
+    if (j == 0) colexp[pq] = e;
+    if (j >= n_pad) continue;
+    const int p = pp[pq], q = pq_[pq];
+    double v = j < n_grid ? w[j] * phiT[p * n_pad + j] * phiT[q * n_pad + j] : 0.0;
+    v = ldexp(v, e);
+    const int64_t o = static_cast<int64_t>(pq) * n_pad + j;
+    if (!BF16) {
+      const __half h = __double2half(v);
+      const __half l = __double2half(v - static_cast<double>(__half2float(h)));
+      out[o] = __half_as_ushort(h);
+      out[part_stride + o] = __half_as_ushort(l);
+    } else {
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      const double r1 = v - static_cast<double>(__bfloat162float(h));
+      const __nv_bfloat16 m = __double2bfloat16(r1);
+      const __nv_bfloat16 l = __double2bfloat16(r1 - static_cast<double>(__bfloat162float(m)));
+      out[o] = __bfloat16_as_ushort(h);
+      out[part_stride + o] = __bfloat16_as_ushort(m);
+      out[2 * part_stride + o] = __bfloat16_as_ushort(l);
+    }
+  }
+}
+
+__global__ void rho_f64_kernel(const double* __restrict__ phi, const double* __restrict__ w, int64_t n_grid,
+                               int64_t n_pad, int N, int n_pair, const int* __restrict__ pp,
+                               const int* __restrict__ pq_, double* __restrict__ rho) {
+  const int64_t j = blockIdx.x;
+  for (int pq = blockIdx.y * blockDim.x + threadIdx.x; pq < n_pair; pq += gridDim.y * blockDim.x) {
+    double v = 0.0;
+    if (j < n_grid) v = w[j] * phi[j * N + pp[pq]] * phi[j * N + pq_[pq]];
+    rho[j * n_pair + pq] = v;
+  }
+}
+
+// ------------------------------------------------------------------ step (a) alone, FP64
+__global__ void jastrow_grad_kernel(const JastrowParams* __restrict__ jp, const double* __restrict__ r1,
+                                    const double* __restrict__ r2, int64_t n, double* __restrict__ out) {
+  const int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (k >= n) return;
+  double pc[PT_COEF];
+  double nc[MAX_NUC * NUC_COEF];
+  double aj[MAX_NUC];
+  point_coefs<double>(*jp, r1[3 * k], r1[3 * k + 1], r1[3 * k + 2], 1.0, pc, nc, 0, jp->n_nuc);
+  const double x = r2[3 * k], y = r2[3 * k + 1], z = r2[3 * k + 2];
+  for (int I = 0; I < jp->n_nuc; ++I) {
+    const double dx = x - jp->nuc[I][0], dy = y - jp->nuc[I][1], dz = z - jp->nuc[I][2];
+    const double d = sqrt(dx * dx + dy * dy + dz * dz);
+    aj[I] = d / (1.0 + d);
+  }
+  double gx, gy, gz;
+  pair_grad_f64(pc, nc, jp->n_nuc, x, y, z, aj, gx, gy, gz);
+  out[3 * k] = gx;
+  out[3 * k + 1] = gy;
+  out[3 * k + 2] = gz;
+}
+
+// ------------------------------------------------------------------ steps (a)+(b), FP64 SIMT
+// CTA: 32 outer points x 64 pairs x 3 components; K steps of 16 inner points.  The gradient
+// tile is generated in shared memory from per-point coefficients (computed once per CTA) and a
+// per-inner-point FP64 table (x, y, z, a_jI...).
+constexpr int F64_TI = 32, F64_TP = 64, F64_KJ = 16;
+
+__global__ void jtab64_kernel(const double* __restrict__ grid, int64_t n_grid, int64_t n_pad,
+                              const JastrowParams* __restrict__ jp, int n_nuc, double* __restrict__ jtab) {
+  const int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (j >= n_pad) return;
+  double x = 1.0e3, y = 1.0e3, z = 1.0e3;
+  if (j < n_grid) {
+    x = grid[3 * j];
+    y = grid[3 * j + 1];
+    z = grid[3 * j + 2];
+  }
+  double* o = jtab + j * (3 + n_nuc);
+  o[0] = x;
+  o[1] = y;
+  o[2] = z;
+  for (int I = 0; I < n_nuc; ++I) {
+    const double dx = x - jp->nuc[I][0], dy = y - jp->nuc[I][1], dz = z - jp->nuc[I][2];
+    const double d = sqrt(dx * dx + dy * dy + dz * dz);
+    o[3 + I] = d / (1.0 + d);
+  }
+}
+
+__global__ void __launch_bounds__(256) vfield_f64_kernel(const double* __restrict__ grid,
+                                                          const JastrowParams* __restrict__ jp,
+                                                          const double* __restrict__ jtab64,
+                                                          const double* __restrict__ rho, int64_t n_pad, int n_pair,
+                                                          int64_t i0, int64_t n_i, int64_t gcp,
+                                                          double* __restrict__ V) {
+  extern __shared__ double sm64[];
+  const int n_nuc = jp->n_nuc;
+  const int cstride = PT_COEF + NUC_COEF * n_nuc;
+  double* coef = sm64;                                  // [TI][cstride]
+  double* Gs = coef + F64_TI * cstride;                 // [KJ][3][TI]
+  double* Rs = Gs + F64_KJ * 3 * F64_TI;                // [KJ][TP]
+  const int t = threadIdx.x;
+  const int64_t ib = static_cast<int64_t>(blockIdx.x) * F64_TI;
+  const int pb = blockIdx.y * F64_TP;
+  if (t < F64_TI) {
+    const int64_t il = ib + t;
+    const int64_t ig = i0 + (il < n_i ? il : n_i - 1);
+    double* c = coef + t * cstride;
+    point_coefs<double>(*jp, grid[3 * ig], grid[3 * ig + 1], grid[3 * ig + 2], 1.0, c, c + PT_COEF, 0, n_nuc);
+  }
+  __syncthreads();
+  const int tx = t & 31, ty = t >> 5;  // pairs tx, tx+32; points ty*4 .. ty*4+3
+  double acc[4][2][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int x = 0; x < 3; ++x) acc[a][b][x] = 0.0;
+  const int js = 3 + n_nuc;
+  for (int64_t j0 = 0; j0 < n_pad; j0 += F64_KJ) {
+    for (int k = t; k < F64_KJ * F64_TI; k += 256) {
+      const int jj = k / F64_TI, ii = k % F64_TI;
+      const double* jr = jtab64 + (j0 + jj) * js;
+      const double* c = coef + ii * cstride;
+      double gx, gy, gz;
+      pair_grad_f64(c, c + PT_COEF, n_nuc, jr[0], jr[1], jr[2], jr + 3, gx, gy, gz);
+      Gs[(jj * 3 + 0) * F64_TI + ii] = gx;
+      Gs[(jj * 3 + 1) * F64_TI + ii] = gy;
+      Gs[(jj * 3 + 2) * F64_TI + ii] = gz;
+    }
+    for (int k = t; k < F64_KJ * F64_TP; k += 256) {
+      const int jj = k / F64_TP, pp = k % F64_TP;
+      Rs[k] = (pb + pp < n_pair) ? rho[(j0 + jj) * n_pair + pb + pp] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < F64_KJ; ++jj) {
+      const double r0 = Rs[jj * F64_TP + tx], r1 = Rs[jj * F64_TP + tx + 32];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          const double g = Gs[(jj * 3 + x) * F64_TI + ty * 4 + a];
+          acc[a][0][x] = fma(g, r0, acc[a][0][x]);
+          acc[a][1][x] = fma(g, r1, acc[a][1][x]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t il = ib + ty * 4 + a;
+    if (il >= n_i) continue;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int pq = pb + tx + 32 * b;
+      if (pq >= n_pair) continue;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) V[(static_cast<int64_t>(pq) * 3 + x) * gcp + il] = acc[a][b][x];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ step (d), FP64 SIMT
+// M[pq][rs] += sum_k L[k][pq] R[k][rs]; 64 x 64 tiles, 16-deep K steps, 4 x 4 per thread.
+__global__ void __launch_bounds__(256) assemble_f64_kernel(const double* __restrict__ L,
+                                                            const double* __restrict__ R, int n_pair, int kdim,
+                                                            int ldm, double* __restrict__ M) {
+  __shared__ double Ls[16][64];
+  __shared__ double Rs[16][64];
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int k0 = 0; k0 < kdim; k0 += 16) {
+    for (int k = t; k < 16 * 64; k += 256) {
+      const int kk = k / 64, c = k % 64;
+      const int64_t row = static_cast<int64_t>(k0 + kk) * n_pair;
+      Ls[kk][c] = (k0 + kk < kdim && m0 + c < n_pair) ? L[row + m0 + c] : 0.0;
+      Rs[kk][c] = (k0 + kk < kdim && n0 + c < n_pair) ? R[row + n0 + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = Ls[kk][ty * 4 + u];
+        b[u] = Rs[kk][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int row = m0 + ty * 4 + u;
+    if (row >= n_pair) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int col = n0 + tx * 4 + v;
+      if (col < n_pair) M[static_cast<int64_t>(row) * ldm + col] += acc[u][v];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ final kernels
+// In place: M <- Delta U = -(M + M^T) (packed pairs), one CTA per pair of 32 x 32 tiles.
+__global__ void symmetrize_kernel(double* __restrict__ M, int n_pair, int ldm) {
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bj < bi) return;
+  __shared__ double A[32][33], B[32][33];
+  const int i0 = bi * 32, j0 = bj * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int ri = i0 + r, rj = j0 + r, ci = j0 + threadIdx.x, cj = i0 + threadIdx.x;
+    A[r][threadIdx.x] = (ri < n_pair && ci < n_pair) ? M[static_cast<int64_t>(ri) * ldm + ci] : 0.0;
+    B[r][threadIdx.x] = (rj < n_pair && cj < n_pair) ? M[static_cast<int64_t>(rj) * ldm + cj] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int ri = i0 + r, ci = j0 + threadIdx.x;
+    if (ri < n_pair && ci < n_pair) M[static_cast<int64_t>(ri) * ldm + ci] = -(A[r][threadIdx.x] + B[threadIdx.x][r]);
+    const int rj = j0 + r, cj = i0 + threadIdx.x;
+    if (bi != bj && rj < n_pair && cj < n_pair)
+      M[static_cast<int64_t>(rj) * ldm + cj] = -(B[r][threadIdx.x] + A[threadIdx.x][r]);
+  }
+}
+
+// dU[p][q][r][s] = U[pair(p,q)][pair(r,s)]
+__global__ void unpack_kernel(const double* __restrict__ U, int N, int ldm, double* __restrict__ dU,
+                              float* __restrict__ dU32) {
+  const int64_t n2 = static_cast<int64_t>(N) * N;
+  const int64_t rs = blockIdx.y * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t pqi = blockIdx.x;
+  if (rs >= n2) return;
+  const int p = static_cast<int>(pqi / N), q = static_cast<int>(pqi % N);
+  const int r = static_cast<int>(rs / N), s = static_cast<int>(rs % N);
+  const double v = U[static_cast<int64_t>(pair_of(p, q, N)) * ldm + pair_of(r, s, N)];
+  const int64_t o = pqi * n2 + rs;
+  if (dU) dU[o] = v;
+  if (dU32) dU32[o] = static_cast<float>(v);
+}
+
+// Delta h_pq = -1/2 (2 sum_rs U(pq|rs) gamma_rs - sum_rs U(ps|rq) gamma_rs), one CTA per (p, q).
+__global__ void onebody_kernel(const double* __restrict__ U, const double* __restrict__ gamma, int N, int ldm,
+                               double* __restrict__ dh) {
+  const int p = blockIdx.y, q = blockIdx.x;
+  const int pq = pair_of(p, q, N);
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < N * N; k += blockDim.x) {
+    const int r = k / N, s = k % N;
+    const double g = gamma[k];
+    acc += g * (2.0 * U[static_cast<int64_t>(pq) * ldm + pair_of(r, s, N)] -
+                U[static_cast<int64_t>(pair_of(p, s, N)) * ldm + pair_of(r, q, N)]);
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dh[p * N + q] = -0.5 * red[0];
+}
+
+// e0 = -2/3 sum_pq Delta h_pq gamma_pq
+__global__ void constant_kernel(const double* __restrict__ dh, const double* __restrict__ gamma, int n2,
+                                double* __restrict__ e0) {
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) acc += dh[k] * gamma[k];
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *e0 = -2.0 / 3.0 * red[0];
+}
+
+template <typename TV>
+__global__ void vfield_export_kernel(const TV* __restrict__ V, int splits, int n_pair, int64_t n_i, int64_t gcp,
+                                     double* __restrict__ out) {
+  const int64_t total = n_i * 3 * n_pair;
+  const int64_t sstride = static_cast<int64_t>(n_pair) * 3 * gcp;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < total;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t pq = k % n_pair, x = (k / n_pair) % 3, i = k / (3 * n_pair);
+    double v = 0.0;
+    for (int z = 0; z < splits; ++z) v += static_cast<double>(V[z * sstride + (pq * 3 + x) * gcp + i]);
+    out[k] = v;
+  }
+}
+
+inline unsigned int blocks_for(int64_t n, int bs) { return static_cast<unsigned int>((n + bs - 1) / bs); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+void launch_jtab(const double* grid, int64_t n_grid, int64_t n_pad, const JastrowParams* jp, int n_nuc, int js,
+                 float* jtab, cudaStream_t st) {
+  jtab_kernel<<<blocks_for(n_pad, 256), 256, 0, st>>>(grid, n_grid, n_pad, jp, n_nuc, js, jtab);
+}
+
+void launch_transpose_phi(const double* phi, int64_t n_grid, int64_t n_pad, int N, double* phiT, cudaStream_t st) {
+  dim3 grid(blocks_for(n_pad, 32), blocks_for(N, 32));
+  transpose_phi_kernel<<<grid, dim3(32, 8), 0, st>>>(phi, n_grid, n_pad, N, phiT);
+}
+
+void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t st) {
+  if (n <= 0) return;
+  const unsigned int b = std::min<unsigned int>(blocks_for(n, 256), 4096u);
+  check_finite_kernel<<<b, 256, 0, st>>>(x, n, flag);
+}
+
+void launch_rho_split(const double* phiT, const double* w, int64_t n_grid, int64_t n_pad, int n_orb, int parts,
+                      bool bf16, bool scale, const int* pp, const int* pq, unsigned int* colmax, int* colexp,
+                      void* out, cudaStream_t st) {
+  const int n_pair = n_orb * (n_orb + 1) / 2;
+  if (scale) {
+    cudaMemsetAsync(colmax, 0, sizeof(unsigned int) * n_pair, st);
+    dim3 g(std::min<unsigned int>(blocks_for(n_grid, 256), 64u), n_pair);
+    rho_colmax_kernel<<<g, 256, 0, st>>>(phiT, w, n_grid, n_pad, n_pair, pp, pq, colmax);
+  }
+  dim3 g2(blocks_for(n_pad, 256), blocks_for(n_pair, 8));
+  if (parts == 2)
+    rho_split_kernel<2, false><<<g2, 256, 0, st>>>(phiT, w, n_grid, n_pad, n_pair, pp, pq, colmax, scale, colexp,
+                                                     static_cast<uint16_t*>(out));
+  else
+    rho_split_kernel<3, true><<<g2, 256, 0, st>>>(phiT, w, n_grid, n_pad, n_pair, pp, pq, colmax, scale, colexp,
+                                                    static_cast<uint16_t*>(out));
+  (void)bf16;
+}
+
+void launch_rho_f64(const double* phi, const double* w, int64_t n_grid, int64_t n_pad, int n_orb, const int* pp,
+                    const int* pq, double* rho, cudaStream_t st) {
+  const int n_pair = n_orb * (n_orb + 1) / 2;
+  dim3 g(static_cast<unsigned int>(n_pad), std::min<unsigned int>(blocks_for(n_pair, 256), 65535u));
+  rho_f64_kernel<<<g, 256, 0, st>>>(phi, w, n_grid, n_pad, n_orb, n_pair, pp, pq, rho);
+}
+
+void launch_jastrow_grad(const JastrowParams* jp, const double* r1, const double* r2, int64_t n, double* out,
+                         cudaStream_t st) {
+  jastrow_grad_kernel<<<blocks_for(n, 64), 64, 0, st>>>(jp, r1, r2, n, out);
+}
+
+void launch_jtab64(const double* grid, int64_t n_grid, int64_t n_pad, const JastrowParams* jp, int n_nuc,
+                   double* jtab, cudaStream_t st) {
+  jtab64_kernel<<<blocks_for(n_pad, 256), 256, 0, st>>>(grid, n_grid, n_pad, jp, n_nuc, jtab);
+}
+
+void launch_vfield_f64_impl(const double* grid, const JastrowParams* jp, int n_nuc, const double* jtab64,
+                            const double* rho, int64_t n_pad, int n_pair, int64_t i0, int64_t n_i, int64_t gcp,
+                            double* V, cudaStream_t st) {
+  const size_t smem = sizeof(double) * (F64_TI * (PT_COEF + NUC_COEF * n_nuc) + F64_KJ * 3 * F64_TI + F64_KJ * F64_TP);
+  cudaFuncSetAttribute(vfield_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  dim3 g(blocks_for(n_i, F64_TI), blocks_for(n_pair, F64_TP));
+  vfield_f64_kernel<<<g, 256, smem, st>>>(grid, jp, jtab64, rho, n_pad, n_pair, i0, n_i, gcp, V);
+}
+
+void launch_assemble_f64(const double* L, const double* R, int n_pair, int kdim, double* M, cudaStream_t st) {
+  const int ldm = static_cast<int>(round_up(n_pair, AS_BN));
+  dim3 g(blocks_for(n_pair, 64), blocks_for(n_pair, 64));
+  assemble_f64_kernel<<<g, 256, 0, st>>>(L, R, n_pair, kdim, ldm, M);
+}
+
+void launch_unpack(const double* M, int n_orb, int n_pair, double* dU, float* dU32, cudaStream_t st) {
+  const int ldm = static_cast<int>(round_up(n_pair, AS_BN));
+  if (dU || dU32) {
+    dim3 g(static_cast<unsigned int>(n_orb) * n_orb, blocks_for(static_cast<int64_t>(n_orb) * n_orb, 256));
+    unpack_kernel<<<g, 256, 0, st>>>(M, n_orb, ldm, dU, dU32);
+  }
+}
+
+void launch_symmetrize(double* M, int n_pair, cudaStream_t st) {
+  const int ldm = static_cast<int>(round_up(n_pair, AS_BN));
+  dim3 g(blocks_for(n_pair, 32), blocks_for(n_pair, 32));
+  symmetrize_kernel<<<g, dim3(32, 8), 0, st>>>(M, n_pair, ldm);
+}
+
+void launch_onebody(const double* M, const double* gamma, int n_orb, int n_pair, double* dh, double* e0,
+                    cudaStream_t st) {
+  const int ldm = static_cast<int>(round_up(n_pair, AS_BN));
+  onebody_kernel<<<dim3(n_orb, n_orb), 256, 0, st>>>(M, gamma, n_orb, ldm, dh);
+  constant_kernel<<<1, 256, 0, st>>>(dh, gamma, n_orb * n_orb, e0);
+}
+
+void launch_vfield_export(const void* V, bool f64, int splits, int n_pair, int64_t n_i, int64_t gcp, double* out,
+                          cudaStream_t st) {
+  const unsigned int b = std::min<unsigned int>(blocks_for(n_i * 3 * n_pair, 256), 8192u);
+  if (f64)
+    vfield_export_kernel<double><<<b, 256, 0, st>>>(static_cast<const double*>(V), splits, n_pair, n_i, gcp, out);
+  else
+    vfield_export_kernel<float><<<b, 256, 0, st>>>(static_cast<const float*>(V), splits, n_pair, n_i, gcp, out);
+}
+
+}  // namespace xtc

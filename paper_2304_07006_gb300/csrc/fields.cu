@@ -1,0 +1,256 @@
+// Step (c): the per-point intermediates of Appendix B ("Restricted closed-shell working
+// equations"), from the vector pair fields V of step (b):
+//     rho_pq = w phi_p phi_q            Wt  = 2 rho_tu gamma_tu
+//     W_x    = 2 V_x,tu gamma_tu        Vt  = W . V
+//     X_x    = gamma V_x                Zt  = V_x . X_x  (= sum_x V_x gamma V_x)
+//     Y_x    = V_x gamma                Z_x = rho X_x + Y_x rho
+//     A      = Vt - Zt                  B_x = 1/2 Wt V_x - Z_x
+// With gamma = sum_k lam_k c_k c_k^T (the library factorises it on the host) the N^3 products
+// become rank-r updates: H_xk = V_x c_k, Zt = sum_xk lam_k H_xk H_xk^T, W_x = 2 sum_k lam_k c_k.H_xk,
+// h_x = V_x gamma phi = sum_k lam_k (c_k.phi) H_xk, Z_x = w (phi h_x^T + h_x phi^T),
+// Wt = 2 w sum_k lam_k (c_k.phi)^2.  (Exact reformulation; no approximation.)
+//
+// A CTA owns `pts` consecutive outer points (lane-contiguous, so every global read of V is a
+// contiguous run of the outer index) and all orbital pairs; H for its points lives in shared
+// memory.  Outputs, per point and pair, are L = (rho, Vx, Vy, Vz) and R = (A, Bx, By, Bz), written
+// as the K-major operands of step (d): three bf16 parts [part][pq][4*gcp] or FP64 [4*gcp][pq].
+// Points past the chunk end are written as zeros.
+#include <cuda_bf16.h>
+
+#include "xtc_internal.cuh"
+
+namespace xtc {
+namespace {
+
+constexpr int THREADS = 256;
+constexpr int RMAX = 16;
+
+template <typename TC>
+struct FieldsSmem {
+  TC* phis;  // [N][P]
+  TC* ws;    // [P]
+  TC* cs;    // [R][N]
+  TC* lam;   // [R]
+  TC* cph;   // [R][P]
+  TC* Hs;    // [3][R][N][P]
+  TC* hs;    // [3][N][P]
+  TC* Wv;    // [3][P]
+  TC* Wt;    // [P]
+  TC* part;  // [3][R][P]
+};
+
+template <typename TC>
+__host__ __device__ inline size_t carve(FieldsSmem<TC>* s, uint8_t* base, int N, int R, int P) {
+  size_t off = 0;
+  TC* p[10];
+  const size_t n[10] = {static_cast<size_t>(N) * P,
+                        static_cast<size_t>(P),
+                        static_cast<size_t>(R) * N,
+                        static_cast<size_t>(R),
+                        static_cast<size_t>(R) * P,
+                        static_cast<size_t>(3) * R * N * P,
+                        static_cast<size_t>(3) * N * P,
+                        static_cast<size_t>(3) * P,
+                        static_cast<size_t>(P),
+                        static_cast<size_t>(3) * R * P};
+  for (int k = 0; k < 10; ++k) {
+    p[k] = reinterpret_cast<TC*>(base + off);
+    off += ((n[k] * sizeof(TC) + 15) / 16) * 16;
+  }
+  if (s) *s = FieldsSmem<TC>{p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8], p[9]};
+  return off;
+}
+
+template <typename TV>
+__device__ __forceinline__ TV vload(const TV* V, int splits, int64_t split_stride, int64_t idx) {
+  TV v = V[idx];
+  for (int z = 1; z < splits; ++z) v += V[z * split_stride + idx];
+  return v;
+}
+
+__device__ __forceinline__ void split3_bf16(float v, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+template <typename TC, int OUT_PARTS>
+__device__ __forceinline__ void write4(void* base, int64_t n_pair, int64_t gcp, int q, int64_t il,
+                                       const TC (&v)[4]) {
+  if (OUT_PARTS == 0) {
+    double* o = static_cast<double*>(base);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) o[(4 * il + c) * n_pair + q] = static_cast<double>(v[c]);
+  } else {
+    __nv_bfloat16* o = static_cast<__nv_bfloat16*>(base);
+    __nv_bfloat16 h[4], m[4], l[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) split3_bf16(static_cast<float>(v[c]), h[c], m[c], l[c]);
+    const int64_t part_stride = n_pair * 4 * gcp;
+    const int64_t off = static_cast<int64_t>(q) * 4 * gcp + 4 * il;
+    uint2 uh, um, ul;
+    uh.x = static_cast<uint32_t>(__bfloat16_as_ushort(h[0])) | (static_cast<uint32_t>(__bfloat16_as_ushort(h[1])) << 16);
+    uh.y = static_cast<uint32_t>(__bfloat16_as_ushort(h[2])) | (static_cast<uint32_t>(__bfloat16_as_ushort(h[3])) << 16);
+    um.x = static_cast<uint32_t>(__bfloat16_as_ushort(m[0])) | (static_cast<uint32_t>(__bfloat16_as_ushort(m[1])) << 16);
+    um.y = static_cast<uint32_t>(__bfloat16_as_ushort(m[2])) | (static_cast<uint32_t>(__bfloat16_as_ushort(m[3])) << 16);
+    ul.x = static_cast<uint32_t>(__bfloat16_as_ushort(l[0])) | (static_cast<uint32_t>(__bfloat16_as_ushort(l[1])) << 16);
+    ul.y = static_cast<uint32_t>(__bfloat16_as_ushort(l[2])) | (static_cast<uint32_t>(__bfloat16_as_ushort(l[3])) << 16);
+    *reinterpret_cast<uint2*>(o + off) = uh;
+    *reinterpret_cast<uint2*>(o + part_stride + off) = um;
+    *reinterpret_cast<uint2*>(o + 2 * part_stride + off) = ul;
+  }
+}
+
+template <typename TV, typename TC, int OUT_PARTS>
+__global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  const int N = a.n_orb, R = a.rank, P = a.pts;
+  FieldsSmem<TC> sm;
+  carve<TC>(&sm, smem_raw, N, R, P);
+  const int t = threadIdx.x;
+  const int pt = t % P, sub = t / P, nsub = THREADS / P;
+  const int64_t il = static_cast<int64_t>(blockIdx.x) * P + pt;  // chunk-local outer point
+  const bool live = il < a.n_i;
+  const TV* V = static_cast<const TV*>(a.V);
+  const int64_t sstride = static_cast<int64_t>(a.n_pair) * 3 * a.gcp;
+
+  // ---------------------------------------------------------------- phase 0: orbitals and gamma factors
+  for (int k = t; k < N * P; k += THREADS) {
+    const int p = k / P, q = k % P;
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * P + q;
+    sm.phis[k] = i < a.n_i ? static_cast<TC>(a.phiT[static_cast<int64_t>(p) * a.ldphi + a.i0 + i]) : TC(0);
+  }
+  for (int k = t; k < P; k += THREADS) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * P + k;
+    sm.ws[k] = i < a.n_i ? static_cast<TC>(a.w[a.i0 + i]) : TC(0);
+  }
+  for (int k = t; k < R * N; k += THREADS) sm.cs[k] = static_cast<TC>(a.evec[k]);
+  for (int k = t; k < R; k += THREADS) sm.lam[k] = static_cast<TC>(a.lam[k]);
+  __syncthreads();
+  for (int k = t; k < R * P; k += THREADS) {
+    const int kk = k / P, q = k % P;
+    TC acc = 0;
+    for (int p = 0; p < N; ++p) acc += sm.cs[kk * N + p] * sm.phis[p * P + q];
+    sm.cph[k] = acc;
+  }
+  __syncthreads();
+  for (int q = t; q < P; q += THREADS) {
+    TC acc = 0;
+    for (int kk = 0; kk < R; ++kk) acc += sm.lam[kk] * sm.cph[kk * P + q] * sm.cph[kk * P + q];
+    sm.Wt[q] = TC(2) * sm.ws[q] * acc;
+  }
+
+  // ---------------------------------------------------------------- phase 1: H_xk = V_x c_k, h_x
+  for (int row = sub; row < 3 * N; row += nsub) {
+    const int x = row / N, p = row % N;
+    TC acc[RMAX];
+#pragma unroll
+    for (int kk = 0; kk < RMAX; ++kk) acc[kk] = 0;
+    int q = p;  // pair index of (s, p) for s = 0
+    for (int s = 0; s < N; ++s) {
+      int qi;
+      if (s < p) {
+        qi = q;
+        q += N - s - 1;
+      } else if (s == p) {
+        q = p * N - p * (p - 1) / 2;
+        qi = q;
+        ++q;
+      } else {
+        qi = q;
+        ++q;
+      }
+      const TC v = live ? static_cast<TC>(vload<TV>(V, a.splits, sstride,
+                                                    (static_cast<int64_t>(qi) * 3 + x) * a.gcp + il))
+                        : TC(0);
+#pragma unroll
+      for (int kk = 0; kk < RMAX; ++kk)
+        if (kk < R) acc[kk] += v * sm.cs[kk * N + s];
+    }
+    TC h = 0;
+#pragma unroll
+    for (int kk = 0; kk < RMAX; ++kk)
+      if (kk < R) {
+        sm.Hs[((x * R + kk) * N + p) * P + pt] = acc[kk];
+        h += sm.lam[kk] * sm.cph[kk * P + pt] * acc[kk];
+      }
+    sm.hs[(x * N + p) * P + pt] = h;
+  }
+  __syncthreads();
+  // W_x = 2 sum_k lam_k sum_p c_k[p] H_xk[p]  (deterministic two-level sum)
+  for (int k = t; k < 3 * R * P; k += THREADS) {
+    const int q = k % P, xk = k / P, kk = xk % R;
+    TC acc = 0;
+    for (int p = 0; p < N; ++p) acc += sm.cs[kk * N + p] * sm.Hs[(xk * N + p) * P + q];
+    sm.part[k] = sm.lam[kk] * acc;
+  }
+  __syncthreads();
+  for (int k = t; k < 3 * P; k += THREADS) {
+    const int x = k / P, q = k % P;
+    TC acc = 0;
+    for (int kk = 0; kk < R; ++kk) acc += sm.part[(x * R + kk) * P + q];
+    sm.Wv[k] = TC(2) * acc;
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- phase 2: pair outputs
+  const TC w = sm.ws[pt];
+  const TC wt = sm.Wt[pt];
+  const TC W0 = sm.Wv[pt], W1 = sm.Wv[P + pt], W2 = sm.Wv[2 * P + pt];
+  for (int q = sub; q < a.n_pair; q += nsub) {
+    TC Lv[4] = {0, 0, 0, 0}, Rv[4] = {0, 0, 0, 0};
+    if (live) {
+      const int p = __ldg(a.pair_p + q), s = __ldg(a.pair_q + q);
+      TC v[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+        v[x] = static_cast<TC>(vload<TV>(V, a.splits, sstride, (static_cast<int64_t>(q) * 3 + x) * a.gcp + il));
+      TC zt = 0;
+      for (int x = 0; x < 3; ++x) {
+        const TC* Hp = sm.Hs + (x * R * N + p) * P + pt;
+        const TC* Hq = sm.Hs + (x * R * N + s) * P + pt;
+#pragma unroll 4
+        for (int kk = 0; kk < R; ++kk) zt += sm.lam[kk] * Hp[kk * N * P] * Hq[kk * N * P];
+      }
+      const TC vt = W0 * v[0] + W1 * v[1] + W2 * v[2];
+      const TC php = sm.phis[p * P + pt], phs = sm.phis[s * P + pt];
+      Lv[0] = w * php * phs;
+      Lv[1] = v[0];
+      Lv[2] = v[1];
+      Lv[3] = v[2];
+      Rv[0] = vt - zt;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const TC zx = w * (php * sm.hs[(x * N + s) * P + pt] + sm.hs[(x * N + p) * P + pt] * phs);
+        Rv[1 + x] = TC(0.5) * wt * v[x] - zx;
+      }
+    }
+    write4<TC, OUT_PARTS>(a.L, a.n_pair, a.gcp, q, il, Lv);
+    write4<TC, OUT_PARTS>(a.R, a.n_pair, a.gcp, q, il, Rv);
+  }
+}
+
+template <typename TV, typename TC, int OUT>
+void launch_t(const FieldsArgs& a, cudaStream_t st) {
+  const size_t smem = fields_smem_bytes(a.n_orb, a.rank, a.pts, sizeof(TC) == 8);
+  auto kern = fields_kernel<TV, TC, OUT>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  const int blocks = static_cast<int>(a.gcp / a.pts);
+  kern<<<blocks, THREADS, smem, st>>>(a);
+}
+
+}  // namespace
+
+size_t fields_smem_bytes(int n_orb, int rank, int pts, bool f64) {
+  return f64 ? carve<double>(nullptr, nullptr, n_orb, rank, pts) : carve<float>(nullptr, nullptr, n_orb, rank, pts);
+}
+
+void launch_fields(const FieldsArgs& a, bool v_is_f64, cudaStream_t st) {
+  if (v_is_f64)
+    launch_t<double, double, 0>(a, st);
+  else
+    launch_t<float, float, 3>(a, st);
+}
+
+}  // namespace xtc

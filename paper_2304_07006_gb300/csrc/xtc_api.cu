@@ -1,0 +1,738 @@
+// Host side of the xTC library: the C ABI of include/xtc.h, input validation, the
+// factorisation of gamma, the device workspace, TMA descriptors and the chunked build loop.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/xtc.h"
+#include "xtc_internal.cuh"
+
+using namespace xtc;
+
+namespace {
+
+struct DBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  template <typename T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+bool ensure(DBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.n >= bytes) return true;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.n = 0;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  b.n = bytes;
+  return true;
+}
+
+struct TimedLaunch {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+constexpr int RANK_GROUP = 16;
+constexpr int MAX_ORB = 320;
+
+}  // namespace
+
+struct xtc_ctx {
+  xtc_params prm{};
+  cudaStream_t st = nullptr;
+  int n_sm = 0;
+  JastrowParams jp{};
+  bool jastrow_set = false;
+  double g_bound = 0.0;  // bound on |nabla_1 u|
+  int64_t outer_begin = 0, outer_end = -1;
+  char detail[512] = {0};
+  // device workspace
+  DBuf jp_dev, err_dev, flag_dev;
+  DBuf grid, w, phi, gamma, phiT, pair_p, pair_q;
+  DBuf jtab, jtab64, rho, colmax, colexp;
+  DBuf V, L, R, M, evec, lam, dU_tmp, dh_tmp, e0_tmp, vout, r1, r2;
+  // prepared state key (pair tables)
+  int pair_n = -1;
+  // timers
+  std::vector<TimedLaunch> timed;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  double ms[XTC_N_KERNELS] = {0};
+  int64_t launches[XTC_N_KERNELS] = {0};
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+};
+
+namespace {
+
+int fail(xtc_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->detail, sizeof(c->detail), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CUDA_OK(call)                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(ctx, XTC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cudaEvent_t next_event(xtc_ctx* c) {
+  if (c->pool_used == c->pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->pool.push_back(e);
+  }
+  return c->pool[c->pool_used++];
+}
+
+// Runs `fn` (which launches kernels of class `kind`, `count` of them) bracketed by events when timing.
+template <typename F>
+void timed(xtc_ctx* c, int kind, int count, F&& fn) {
+  c->launches[kind] += count;
+  if (!c->prm.timing) {
+    fn();
+    return;
+  }
+  TimedLaunch t{kind, next_event(c), next_event(c)};
+  cudaEventRecord(t.a, c->st);
+  fn();
+  cudaEventRecord(t.b, c->st);
+  c->timed.push_back(t);
+}
+
+void reset_timers(xtc_ctx* c) {
+  c->timed.clear();
+  c->pool_used = 0;
+  for (int k = 0; k < XTC_N_KERNELS; ++k) {
+    c->ms[k] = 0.0;
+    c->launches[k] = 0;
+  }
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (row-major).  On return a holds
+// the eigenvalues on its diagonal and v (row-major) the eigenvectors as columns.
+void jacobi_eigen(std::vector<double>& a, std::vector<double>& v, int n) {
+  v.assign(static_cast<size_t>(n) * n, 0.0);
+  for (int i = 0; i < n; ++i) v[static_cast<size_t>(i) * n + i] = 1.0;
+  double total = 0.0;
+  for (double x : a) total += x * x;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += a[static_cast<size_t>(p) * n + q] * a[static_cast<size_t>(p) * n + q];
+    if (off <= 1e-32 * total || off == 0.0) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = a[static_cast<size_t>(p) * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        const double app = a[static_cast<size_t>(p) * n + p], aqq = a[static_cast<size_t>(q) * n + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double akp = a[static_cast<size_t>(k) * n + p], akq = a[static_cast<size_t>(k) * n + q];
+          a[static_cast<size_t>(k) * n + p] = c * akp - s * akq;
+          a[static_cast<size_t>(k) * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double apk = a[static_cast<size_t>(p) * n + k], aqk = a[static_cast<size_t>(q) * n + k];
+          a[static_cast<size_t>(p) * n + k] = c * apk - s * aqk;
+          a[static_cast<size_t>(q) * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = v[static_cast<size_t>(k) * n + p], vkq = v[static_cast<size_t>(k) * n + q];
+          v[static_cast<size_t>(k) * n + p] = c * vkp - s * vkq;
+          v[static_cast<size_t>(k) * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+int make_tmap_3d(xtc_ctx* ctx, CUtensorMap* tm, void* base, bool bf16, uint64_t d0, uint64_t d1, uint64_t d2,
+                 uint32_t b0, uint32_t b1) {
+  const cuuint64_t dims[3] = {d0, d1, d2};
+  const cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
+  const cuuint32_t box[3] = {b0, b1, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = ctx->encode(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims,
+                           strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, XTC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return XTC_OK;
+}
+
+// Copies (or aliases) an input array into device memory.
+int stage_input(xtc_ctx* ctx, DBuf& buf, const double* src, size_t count, const double** dev) {
+  if (is_device_ptr(src)) {
+    *dev = src;
+    return XTC_OK;
+  }
+  if (!ensure(buf, count * sizeof(double))) return fail(ctx, XTC_ERR_OOM, "input staging (%zu bytes)", count * 8);
+  CUDA_OK(cudaMemcpyAsync(buf.p, src, count * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  *dev = buf.as<double>();
+  return XTC_OK;
+}
+
+struct Plan {
+  int N, NP;
+  int64_t NG, NGp;
+  int64_t ob, oe;    // outer range
+  int64_t gc;        // chunk length (multiple of 128)
+  int splits;
+  int parts_b;       // step (b) parts (2 fp16 / 3 bf16), 0 = FP64
+  bool f64;
+};
+
+int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t n_outer, bool f64) {
+  // memory budget for V and the step (d) operands, then the chunk that fills whole waves best
+  const double vbytes = f64 ? 3.0 * 8 : 3.0 * 4;
+  const double lrbytes = f64 ? 2 * 4 * 8.0 : 2 * 3 * 4 * 2.0;
+  const double per_point = NP * (vbytes + lrbytes);
+  int64_t cap = static_cast<int64_t>(6.0e9 / per_point);
+  cap = std::max<int64_t>(128, std::min<int64_t>(cap, 32768) / 128 * 128);
+  const int64_t need = round_up(n_outer, 128);
+  if (need <= cap) return need;
+  const int nt = (NP + VF_BN - 1) / VF_BN;
+  int64_t best = cap;
+  double best_eff = 0.0;
+  for (int64_t tiles = cap / 128; tiles >= std::max<int64_t>(1, cap / 256); --tiles) {
+    const double ctas = static_cast<double>(tiles) * nt;
+    const double eff = ctas / (std::ceil(ctas / c->n_sm) * c->n_sm);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = tiles * 128;
+    }
+  }
+  return best;
+}
+
+int choose_pts(int N, int R, bool f64) {
+  for (int p : {8, 4, 2, 1})
+    if (fields_smem_bytes(N, R, p, f64) <= 200 * 1024) return p;
+  return 0;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void xtc_default_params(xtc_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->device = 0;
+  p->stream = nullptr;
+  p->precision = XTC_PREC_FP16X2;
+  p->grid_chunk = 0;
+  p->split_k = 0;
+  p->timing = 0;
+}
+
+const char* xtc_strerror(int s) {
+  switch (s) {
+    case XTC_OK: return "success";
+    case XTC_ERR_ARG: return "invalid argument";
+    case XTC_ERR_NOT_SYMMETRIC: return "gamma is not symmetric";
+    case XTC_ERR_NONFINITE: return "non-finite input";
+    case XTC_ERR_OOM: return "device allocation failed";
+    case XTC_ERR_CUDA: return "CUDA error";
+    case XTC_ERR_TIMEOUT: return "device-side wait timed out";
+    case XTC_ERR_STATE: return "context not ready (xtc_set_jastrow missing?)";
+    case XTC_ERR_UNSUPPORTED: return "unsupported device or configuration";
+    default: return "unknown status";
+  }
+}
+
+const char* xtc_last_error_detail(const xtc_ctx* ctx) { return ctx ? ctx->detail : "null context"; }
+
+int xtc_create(xtc_ctx** out, const xtc_params* p) {
+  if (!out || !p) return XTC_ERR_ARG;
+  *out = nullptr;
+  if (p->precision < XTC_PREC_FP64 || p->precision > XTC_PREC_BF16X3) return XTC_ERR_ARG;
+  if (p->grid_chunk < 0 || p->grid_chunk % 128 != 0 || p->split_k < 0 || p->split_k > 16) return XTC_ERR_ARG;
+  if (cudaSetDevice(p->device) != cudaSuccess) {
+    cudaGetLastError();
+    return XTC_ERR_CUDA;
+  }
+  cudaDeviceProp prop{};
+  if (cudaGetDeviceProperties(&prop, p->device) != cudaSuccess) return XTC_ERR_CUDA;
+  if (prop.major < 10) return XTC_ERR_UNSUPPORTED;
+  xtc_ctx* ctx = new xtc_ctx();
+  ctx->prm = *p;
+  ctx->st = static_cast<cudaStream_t>(p->stream);
+  ctx->n_sm = prop.multiProcessorCount;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q{};
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    delete ctx;
+    return XTC_ERR_CUDA;
+  }
+  ctx->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  if (!ensure(ctx->jp_dev, sizeof(JastrowParams)) || !ensure(ctx->err_dev, 16) || !ensure(ctx->flag_dev, 16)) {
+    xtc_destroy(ctx);
+    return XTC_ERR_OOM;
+  }
+  *out = ctx;
+  return XTC_OK;
+}
+
+int xtc_destroy(xtc_ctx* ctx) {
+  if (!ctx) return XTC_OK;
+  cudaSetDevice(ctx->prm.device);
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  else cudaDeviceSynchronize();
+  DBuf* bufs[] = {&ctx->jp_dev, &ctx->err_dev, &ctx->flag_dev, &ctx->grid, &ctx->w, &ctx->phi, &ctx->gamma,
+                  &ctx->phiT, &ctx->pair_p, &ctx->pair_q, &ctx->jtab, &ctx->jtab64, &ctx->rho, &ctx->colmax,
+                  &ctx->colexp, &ctx->V, &ctx->L, &ctx->R, &ctx->M, &ctx->evec, &ctx->lam, &ctx->dU_tmp,
+                  &ctx->dh_tmp, &ctx->e0_tmp, &ctx->vout, &ctx->r1, &ctx->r2};
+  for (DBuf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+  delete ctx;
+  return XTC_OK;
+}
+
+int xtc_set_jastrow(xtc_ctx* ctx, int n_nuc, const double* nuc_xyz, const int* nuc_set, int n_sets, int n_terms,
+                    const int* mno, const double* coef) {
+  if (!ctx) return XTC_ERR_ARG;
+  if (n_nuc < 1 || n_nuc > MAX_NUC || n_sets < 1 || n_sets > MAX_SETS || n_terms < 1 || n_terms > MAX_TERMS ||
+      !nuc_xyz || !nuc_set || !mno || !coef)
+    return fail(ctx, XTC_ERR_ARG, "set_jastrow: bad sizes or null pointer");
+  JastrowParams jp{};
+  jp.n_nuc = n_nuc;
+  jp.n_terms = n_terms;
+  jp.n_sets = n_sets;
+  double bound = 0.0;
+  for (int I = 0; I < n_nuc; ++I) {
+    for (int k = 0; k < 3; ++k) {
+      if (!std::isfinite(nuc_xyz[3 * I + k])) return fail(ctx, XTC_ERR_NONFINITE, "nucleus coordinate");
+      jp.nuc[I][k] = nuc_xyz[3 * I + k];
+    }
+    if (nuc_set[I] < 0 || nuc_set[I] >= n_sets) return fail(ctx, XTC_ERR_ARG, "nuc_set[%d] out of range", I);
+    jp.set[I] = nuc_set[I];
+  }
+  for (int t = 0; t < n_terms; ++t)
+    for (int k = 0; k < 3; ++k) {
+      if (mno[3 * t + k] < 0 || mno[3 * t + k] > 2) return fail(ctx, XTC_ERR_ARG, "term %d: powers must be 0..2", t);
+      jp.mno[t][k] = mno[3 * t + k];
+    }
+  for (int s = 0; s < n_sets; ++s)
+    for (int t = 0; t < n_terms; ++t) {
+      const double c = coef[s * n_terms + t];
+      if (!std::isfinite(c)) return fail(ctx, XTC_ERR_NONFINITE, "Jastrow coefficient");
+      jp.coef[s][t] = c;
+    }
+  // |nabla_1 u| <= sum_I sum_t |c| (m + n + 2 o): a, b, a', b' are all in [0, 1]
+  for (int I = 0; I < n_nuc; ++I)
+    for (int t = 0; t < n_terms; ++t)
+      bound += std::fabs(jp.coef[jp.set[I]][t]) * (jp.mno[t][0] + jp.mno[t][1] + 2.0 * jp.mno[t][2]);
+  cudaSetDevice(ctx->prm.device);
+  CUDA_OK(cudaMemcpy(ctx->jp_dev.p, &jp, sizeof(jp), cudaMemcpyHostToDevice));
+  ctx->jp = jp;
+  ctx->g_bound = bound;
+  ctx->jastrow_set = true;
+  return XTC_OK;
+}
+
+int xtc_set_outer_range(xtc_ctx* ctx, int64_t begin, int64_t end) {
+  if (!ctx || begin < 0 || (end >= 0 && end < begin)) return XTC_ERR_ARG;
+  ctx->outer_begin = begin;
+  ctx->outer_end = end;
+  return XTC_OK;
+}
+
+int xtc_get_timings(xtc_ctx* ctx, double* ms, int64_t* launches, int n) {
+  if (!ctx || n < XTC_N_KERNELS) return XTC_ERR_ARG;
+  if (ms) for (int k = 0; k < XTC_N_KERNELS; ++k) ms[k] = ctx->ms[k];
+  if (launches) for (int k = 0; k < XTC_N_KERNELS; ++k) launches[k] = ctx->launches[k];
+  return XTC_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== build
+namespace {
+
+int finish_timers(xtc_ctx* ctx) {
+  for (const TimedLaunch& t : ctx->timed) {
+    float m = 0.0f;
+    if (cudaEventElapsedTime(&m, t.a, t.b) == cudaSuccess) ctx->ms[t.kind] += m;
+  }
+  cudaGetLastError();
+  return XTC_OK;
+}
+
+int check_device_error(xtc_ctx* ctx) {
+  int h[2] = {0, 0};
+  CUDA_OK(cudaMemcpyAsync(h, ctx->err_dev.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CUDA_OK(cudaStreamSynchronize(ctx->st));
+  if (h[0] != 0) return fail(ctx, XTC_ERR_TIMEOUT, "device wait timed out (code %d)", h[0]);
+  return XTC_OK;
+}
+
+// Common preparation of grid-wide tables.  Fills the plan.
+int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
+            const double* phi, const double** d_grid, const double** d_w, const double** d_phi) {
+  if (!ctx->jastrow_set) return fail(ctx, XTC_ERR_STATE, "xtc_set_jastrow has not been called");
+  if (n_grid < 1 || n_orb < 1 || n_orb > MAX_ORB || !grid_xyz || !weights || !phi)
+    return fail(ctx, XTC_ERR_ARG, "bad sizes (n_grid=%lld, n_orb=%d) or null input", (long long)n_grid, n_orb);
+  const bool f64 = ctx->prm.precision == XTC_PREC_FP64;
+  if (!f64 && !vfield_tc_supported(ctx->jp.n_nuc))
+    return fail(ctx, XTC_ERR_UNSUPPORTED, "the tensor-core path supports 1..4 nuclei (got %d)", ctx->jp.n_nuc);
+  pl.N = n_orb;
+  pl.NP = n_orb * (n_orb + 1) / 2;
+  pl.NG = n_grid;
+  pl.NGp = round_up(n_grid, 128);
+  pl.f64 = f64;
+  pl.parts_b = f64 ? 0 : (ctx->prm.precision == XTC_PREC_FP16X2 ? 2 : 3);
+  pl.ob = std::min<int64_t>(ctx->outer_begin, n_grid);
+  pl.oe = ctx->outer_end < 0 ? n_grid : std::min<int64_t>(ctx->outer_end, n_grid);
+  if (pl.oe < pl.ob) pl.oe = pl.ob;
+  const int64_t n_outer = pl.oe - pl.ob;
+  pl.gc = ctx->prm.grid_chunk > 0 ? ctx->prm.grid_chunk : auto_chunk(ctx, pl.NP, std::max<int64_t>(n_outer, 1), f64);
+  const int n_kb = static_cast<int>(pl.NGp / VF_BK);
+  pl.splits = ctx->prm.split_k > 0 ? std::min(ctx->prm.split_k, n_kb) : 1;
+  if (f64) pl.splits = 1;
+
+  cudaStream_t st = ctx->st;
+  int rc;
+  if ((rc = stage_input(ctx, ctx->grid, grid_xyz, static_cast<size_t>(n_grid) * 3, d_grid))) return rc;
+  if ((rc = stage_input(ctx, ctx->w, weights, static_cast<size_t>(n_grid), d_w))) return rc;
+  if ((rc = stage_input(ctx, ctx->phi, phi, static_cast<size_t>(n_grid) * n_orb, d_phi))) return rc;
+
+  CUDA_OK(cudaMemsetAsync(ctx->flag_dev.p, 0, 16, st));
+  CUDA_OK(cudaMemsetAsync(ctx->err_dev.p, 0, 16, st));
+  timed(ctx, XTC_K_PREP, 3, [&] {
+    launch_check_finite(*d_grid, n_grid * 3, ctx->flag_dev.as<int>(), st);
+    launch_check_finite(*d_w, n_grid, ctx->flag_dev.as<int>(), st);
+    launch_check_finite(*d_phi, n_grid * n_orb, ctx->flag_dev.as<int>(), st);
+  });
+  int flag = 0;
+  CUDA_OK(cudaMemcpyAsync(&flag, ctx->flag_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_OK(cudaStreamSynchronize(st));
+  if (flag) return fail(ctx, XTC_ERR_NONFINITE, "NaN or Inf in grid, weights or orbitals");
+
+  if (ctx->pair_n != n_orb) {
+    std::vector<int> pp(pl.NP), pq(pl.NP);
+    int k = 0;
+    for (int p = 0; p < n_orb; ++p)
+      for (int q = p; q < n_orb; ++q) {
+        pp[k] = p;
+        pq[k] = q;
+        ++k;
+      }
+    if (!ensure(ctx->pair_p, pl.NP * sizeof(int)) || !ensure(ctx->pair_q, pl.NP * sizeof(int)))
+      return fail(ctx, XTC_ERR_OOM, "pair tables");
+    CUDA_OK(cudaMemcpy(ctx->pair_p.p, pp.data(), pl.NP * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_OK(cudaMemcpy(ctx->pair_q.p, pq.data(), pl.NP * sizeof(int), cudaMemcpyHostToDevice));
+    ctx->pair_n = n_orb;
+  }
+  if (!ensure(ctx->phiT, sizeof(double) * pl.NGp * n_orb)) return fail(ctx, XTC_ERR_OOM, "phiT");
+  const int n_nuc = ctx->jp.n_nuc;
+  if (f64) {
+    if (!ensure(ctx->jtab64, sizeof(double) * pl.NGp * (3 + n_nuc)) ||
+        !ensure(ctx->rho, sizeof(double) * pl.NGp * pl.NP))
+      return fail(ctx, XTC_ERR_OOM, "FP64 grid tables (%.2f GB)", 8.0 * pl.NGp * pl.NP / 1e9);
+  } else {
+    const int js = 12;
+    if (!ensure(ctx->jtab, sizeof(float) * pl.NGp * js) ||
+        !ensure(ctx->rho, 2ull * pl.parts_b * pl.NGp * pl.NP) || !ensure(ctx->colmax, 4ull * pl.NP) ||
+        !ensure(ctx->colexp, 4ull * pl.NP))
+      return fail(ctx, XTC_ERR_OOM, "grid tables (%.2f GB)", 2.0 * pl.parts_b * pl.NGp * pl.NP / 1e9);
+  }
+  const int nprep = f64 ? 3 : (pl.parts_b == 2 ? 4 : 3);
+  timed(ctx, XTC_K_PREP, nprep, [&] {
+    launch_transpose_phi(*d_phi, n_grid, pl.NGp, n_orb, ctx->phiT.as<double>(), st);
+    if (f64) {
+      launch_jtab64(*d_grid, n_grid, pl.NGp, ctx->jp_dev.as<JastrowParams>(), n_nuc, ctx->jtab64.as<double>(), st);
+      launch_rho_f64(*d_phi, *d_w, n_grid, pl.NGp, n_orb, ctx->pair_p.as<int>(), ctx->pair_q.as<int>(),
+                     ctx->rho.as<double>(), st);
+    } else {
+      const int js = 12;
+      launch_jtab(*d_grid, n_grid, pl.NGp, ctx->jp_dev.as<JastrowParams>(), n_nuc, js, ctx->jtab.as<float>(), st);
+      launch_rho_split(ctx->phiT.as<double>(), *d_w, n_grid, pl.NGp, n_orb, pl.parts_b, pl.parts_b == 3,
+                       pl.parts_b == 2, ctx->pair_p.as<int>(), ctx->pair_q.as<int>(), ctx->colmax.as<unsigned int>(),
+                       ctx->colexp.as<int>(), ctx->rho.p, st);
+    }
+  });
+  const size_t vbytes = static_cast<size_t>(pl.splits) * pl.NP * 3 * pl.gc * (f64 ? 8 : 4);
+  if (!ensure(ctx->V, vbytes)) return fail(ctx, XTC_ERR_OOM, "V chunk (%.2f GB)", vbytes / 1e9);
+  return XTC_OK;
+}
+
+// Steps (a)+(b) for outer points [i0, i0 + n_i) into ctx->V.
+int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, int64_t n_i, const CUtensorMap* tm) {
+  cudaStream_t st = ctx->st;
+  if (pl.f64) {
+    timed(ctx, XTC_K_VFIELD, 1, [&] {
+      launch_vfield_f64_impl(d_grid, ctx->jp_dev.as<JastrowParams>(), ctx->jp.n_nuc, ctx->jtab64.as<double>(),
+                             ctx->rho.as<double>(), pl.NGp, pl.NP, i0, n_i, pl.gc, ctx->V.as<double>(), st);
+    });
+    return XTC_OK;
+  }
+  VfieldArgs a{};
+  a.grid = d_grid;
+  a.jp = ctx->jp_dev.as<JastrowParams>();
+  a.jtab = ctx->jtab.as<float>();
+  a.colexp = ctx->colexp.as<int>();
+  a.V = ctx->V.as<float>();
+  a.i0 = i0;
+  a.n_i = n_i;
+  a.gcp = pl.gc;
+  a.n_pair = pl.NP;
+  a.n_nuc = ctx->jp.n_nuc;
+  a.js = 12;
+  a.n_kb = static_cast<int>(pl.NGp / VF_BK);
+  a.kb_per_split = (a.n_kb + pl.splits - 1) / pl.splits;
+  int sg = 0;
+  if (pl.parts_b == 2 && ctx->g_bound > 0.0) {
+    sg = static_cast<int>(std::floor(std::log2(16384.0 / ctx->g_bound)));
+    sg = std::max(-30, std::min(30, sg));
+  }
+  a.g_scale = std::ldexp(1.0f, sg);
+  a.unscale_g = std::ldexp(1.0f, -sg);
+  a.err = ctx->err_dev.as<int>();
+  const int splits = (a.n_kb + a.kb_per_split - 1) / a.kb_per_split;  // every slice non-empty
+  timed(ctx, XTC_K_VFIELD, 1, [&] { launch_vfield_tc(tm, a, pl.parts_b, pl.parts_b == 3, splits, st); });
+  return XTC_OK;
+}
+
+}  // namespace
+
+extern "C" int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
+                              const double* phi, const double* gamma, double* dU, float* dU_f32, double* dh,
+                              double* e0) {
+  if (!ctx) return XTC_ERR_ARG;
+  if (!gamma || !dh || !e0) return fail(ctx, XTC_ERR_ARG, "gamma, dh and e0 are required");
+  CUDA_OK(cudaSetDevice(ctx->prm.device));
+  reset_timers(ctx);
+  cudaStream_t st = ctx->st;
+
+  // ---- gamma: symmetry, finiteness, factorisation gamma = sum_k lam_k c_k c_k^T
+  if (n_orb < 1 || n_orb > MAX_ORB) return fail(ctx, XTC_ERR_ARG, "n_orb=%d out of range", n_orb);
+  const int N = n_orb;
+  std::vector<double> g(static_cast<size_t>(N) * N);
+  if (is_device_ptr(gamma)) CUDA_OK(cudaMemcpy(g.data(), gamma, g.size() * 8, cudaMemcpyDeviceToHost));
+  else std::memcpy(g.data(), gamma, g.size() * 8);
+  double gmax = 0.0, asym = 0.0;
+  for (int p = 0; p < N; ++p)
+    for (int q = 0; q < N; ++q) {
+      const double v = g[static_cast<size_t>(p) * N + q];
+      if (!std::isfinite(v)) return fail(ctx, XTC_ERR_NONFINITE, "gamma has NaN/Inf");
+      gmax = std::max(gmax, std::fabs(v));
+      asym = std::max(asym, std::fabs(v - g[static_cast<size_t>(q) * N + p]));
+    }
+  if (asym > 1e-12 * gmax) return fail(ctx, XTC_ERR_NOT_SYMMETRIC, "max |gamma - gamma^T| = %g", asym);
+  std::vector<double> a = g, vecs;
+  jacobi_eigen(a, vecs, N);
+  double lmax = 0.0;
+  for (int k = 0; k < N; ++k) lmax = std::max(lmax, std::fabs(a[static_cast<size_t>(k) * N + k]));
+  std::vector<double> lam, ev;  // ev[k][p]
+  for (int k = 0; k < N; ++k) {
+    const double l = a[static_cast<size_t>(k) * N + k];
+    if (std::fabs(l) <= 1e-13 * lmax || l == 0.0) continue;
+    lam.push_back(l);
+    for (int p = 0; p < N; ++p) ev.push_back(vecs[static_cast<size_t>(p) * N + k]);
+  }
+  const int rank = static_cast<int>(lam.size());
+
+  Plan pl{};
+  const double *d_grid = nullptr, *d_w = nullptr, *d_phi = nullptr;
+  int rc = prepare(ctx, pl, n_grid, n_orb, grid_xyz, weights, phi, &d_grid, &d_w, &d_phi);
+  if (rc) return rc;
+  const int NP = pl.NP;
+  const int ldm = static_cast<int>(round_up(NP, AS_BN));
+
+  // ---- device copies of gamma and its factors
+  if (!ensure(ctx->gamma, g.size() * 8) || !ensure(ctx->evec, std::max<size_t>(ev.size(), 1) * 8) ||
+      !ensure(ctx->lam, std::max<size_t>(lam.size(), 1) * 8) || !ensure(ctx->M, 8ull * NP * ldm))
+    return fail(ctx, XTC_ERR_OOM, "gamma / accumulator (%.2f GB)", 8.0 * NP * ldm / 1e9);
+  CUDA_OK(cudaMemcpyAsync(ctx->gamma.p, g.data(), g.size() * 8, cudaMemcpyHostToDevice, st));
+  if (rank > 0) {
+    CUDA_OK(cudaMemcpyAsync(ctx->evec.p, ev.data(), ev.size() * 8, cudaMemcpyHostToDevice, st));
+    CUDA_OK(cudaMemcpyAsync(ctx->lam.p, lam.data(), lam.size() * 8, cudaMemcpyHostToDevice, st));
+  }
+  CUDA_OK(cudaMemsetAsync(ctx->M.p, 0, 8ull * NP * ldm, st));
+
+  // ---- step (d) operands
+  const int64_t kdim = 4 * pl.gc;
+  const size_t lr_bytes = pl.f64 ? 8ull * kdim * NP : 2ull * 3 * kdim * NP;
+  if (!ensure(ctx->L, lr_bytes) || !ensure(ctx->R, lr_bytes))
+    return fail(ctx, XTC_ERR_OOM, "step (d) operands (%.2f GB)", 2.0 * lr_bytes / 1e9);
+  CUtensorMap tm_rho{}, tm_L{}, tm_R{};
+  if (!pl.f64) {
+    if ((rc = make_tmap_3d(ctx, &tm_rho, ctx->rho.p, pl.parts_b == 3, pl.NGp, NP, pl.parts_b, VF_BK, VF_BN))) return rc;
+    if ((rc = make_tmap_3d(ctx, &tm_L, ctx->L.p, true, kdim, NP, 3, AS_BK, AS_BM))) return rc;
+    if ((rc = make_tmap_3d(ctx, &tm_R, ctx->R.p, true, kdim, NP, 3, AS_BK, AS_BN))) return rc;
+  }
+  const int groups = std::max(1, (rank + RANK_GROUP - 1) / RANK_GROUP);
+  int pts = 0;
+  for (int gi = 0; gi < groups; ++gi) {
+    const int rg = std::min(RANK_GROUP, rank - gi * RANK_GROUP);
+    const int p = choose_pts(N, std::max(rg, 0), pl.f64);
+    if (!p) return fail(ctx, XTC_ERR_UNSUPPORTED, "step (c) shared memory exceeded (n_orb=%d)", N);
+    pts = pts ? std::min(pts, p) : p;
+  }
+
+  // ---- chunk loop
+  for (int64_t c0 = pl.ob; c0 < pl.oe; c0 += pl.gc) {
+    const int64_t n_i = std::min<int64_t>(pl.gc, pl.oe - c0);
+    if ((rc = run_vfield(ctx, pl, d_grid, c0, n_i, &tm_rho))) return rc;
+    for (int gi = 0; gi < groups; ++gi) {
+      const int k0 = gi * RANK_GROUP;
+      const int rg = std::max(0, std::min(RANK_GROUP, rank - k0));
+      FieldsArgs fa{};
+      fa.V = ctx->V.p;
+      fa.splits = pl.f64 ? 1 : pl.splits;
+      fa.phiT = ctx->phiT.as<double>();
+      fa.ldphi = pl.NGp;
+      fa.w = d_w;
+      fa.evec = ctx->evec.as<double>() + static_cast<size_t>(k0) * N;
+      fa.lam = ctx->lam.as<double>() + k0;
+      fa.rank = rg;
+      fa.i0 = c0;
+      fa.n_i = n_i;
+      fa.gcp = pl.gc;
+      fa.n_orb = N;
+      fa.n_pair = NP;
+      fa.pts = pts;
+      fa.pair_p = ctx->pair_p.as<int>();
+      fa.pair_q = ctx->pair_q.as<int>();
+      fa.L = ctx->L.p;
+      fa.R = ctx->R.p;
+      fa.out_parts = pl.f64 ? 0 : 3;
+      timed(ctx, XTC_K_FIELDS, 1, [&] { launch_fields(fa, pl.f64, st); });
+      timed(ctx, XTC_K_ASSEMBLE, 1, [&] {
+        if (pl.f64)
+          launch_assemble_f64(ctx->L.as<double>(), ctx->R.as<double>(), NP, static_cast<int>(kdim),
+                              ctx->M.as<double>(), st);
+        else
+          launch_assemble_tc(&tm_L, &tm_R, NP, static_cast<int>(kdim), ctx->M.as<double>(), ctx->err_dev.as<int>(), st);
+      });
+    }
+  }
+
+  // ---- final: Delta U, Delta h, e0
+  const bool dU_dev = dU && is_device_ptr(dU), dU32_dev = dU_f32 && is_device_ptr(dU_f32);
+  const bool dh_dev = is_device_ptr(dh), e0_dev = is_device_ptr(e0);
+  const size_t n4 = static_cast<size_t>(N) * N * N * N;
+  double* udst = dU ? (dU_dev ? dU : nullptr) : nullptr;
+  float* u32dst = dU_f32 ? (dU32_dev ? dU_f32 : nullptr) : nullptr;
+  if (dU && !dU_dev) {
+    if (!ensure(ctx->dU_tmp, n4 * 8)) return fail(ctx, XTC_ERR_OOM, "dU staging");
+    udst = ctx->dU_tmp.as<double>();
+  }
+  if (dU_f32 && !dU32_dev) {
+    if (!ensure(ctx->vout, n4 * 4)) return fail(ctx, XTC_ERR_OOM, "dU_f32 staging");
+    u32dst = ctx->vout.as<float>();
+  }
+  if (!ensure(ctx->dh_tmp, static_cast<size_t>(N) * N * 8) || !ensure(ctx->e0_tmp, 8))
+    return fail(ctx, XTC_ERR_OOM, "dh staging");
+  double* dh_d = dh_dev ? dh : ctx->dh_tmp.as<double>();
+  double* e0_d = e0_dev ? e0 : ctx->e0_tmp.as<double>();
+  timed(ctx, XTC_K_FINAL, (udst || u32dst) ? 4 : 3, [&] {
+    launch_symmetrize(ctx->M.as<double>(), NP, st);
+    launch_unpack(ctx->M.as<double>(), N, NP, udst, u32dst, st);
+    launch_onebody(ctx->M.as<double>(), ctx->gamma.as<double>(), N, NP, dh_d, e0_d, st);
+  });
+  CUDA_OK(cudaGetLastError());
+  if (dU && !dU_dev) CUDA_OK(cudaMemcpyAsync(dU, udst, n4 * 8, cudaMemcpyDeviceToHost, st));
+  if (dU_f32 && !dU32_dev) CUDA_OK(cudaMemcpyAsync(dU_f32, u32dst, n4 * 4, cudaMemcpyDeviceToHost, st));
+  if (!dh_dev) CUDA_OK(cudaMemcpyAsync(dh, dh_d, static_cast<size_t>(N) * N * 8, cudaMemcpyDeviceToHost, st));
+  if (!e0_dev) CUDA_OK(cudaMemcpyAsync(e0, e0_d, 8, cudaMemcpyDeviceToHost, st));
+  if ((rc = check_device_error(ctx))) return rc;
+  finish_timers(ctx);
+  return XTC_OK;
+}
+
+extern "C" int xtc_jastrow_grad(xtc_ctx* ctx, int64_t n, const double* r1, const double* r2, double* out) {
+  if (!ctx) return XTC_ERR_ARG;
+  if (!ctx->jastrow_set) return fail(ctx, XTC_ERR_STATE, "xtc_set_jastrow has not been called");
+  if (n < 0 || (n > 0 && (!r1 || !r2 || !out))) return fail(ctx, XTC_ERR_ARG, "bad arguments");
+  if (n == 0) return XTC_OK;
+  CUDA_OK(cudaSetDevice(ctx->prm.device));
+  cudaStream_t st = ctx->st;
+  const double *d1 = nullptr, *d2 = nullptr;
+  int rc;
+  if ((rc = stage_input(ctx, ctx->r1, r1, static_cast<size_t>(n) * 3, &d1))) return rc;
+  if ((rc = stage_input(ctx, ctx->r2, r2, static_cast<size_t>(n) * 3, &d2))) return rc;
+  const bool out_dev = is_device_ptr(out);
+  double* o = out;
+  if (!out_dev) {
+    if (!ensure(ctx->vout, static_cast<size_t>(n) * 24)) return fail(ctx, XTC_ERR_OOM, "output staging");
+    o = ctx->vout.as<double>();
+  }
+  launch_jastrow_grad(ctx->jp_dev.as<JastrowParams>(), d1, d2, n, o, st);
+  CUDA_OK(cudaGetLastError());
+  if (!out_dev) CUDA_OK(cudaMemcpyAsync(out, o, static_cast<size_t>(n) * 24, cudaMemcpyDeviceToHost, st));
+  CUDA_OK(cudaStreamSynchronize(st));
+  return XTC_OK;
+}
+
+extern "C" int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
+                          const double* phi, int64_t outer_begin, int64_t outer_end, double* V) {
+  if (!ctx) return XTC_ERR_ARG;
+  if (!V || outer_begin < 0 || outer_end < outer_begin || outer_end > n_grid)
+    return fail(ctx, XTC_ERR_ARG, "bad outer range or null output");
+  CUDA_OK(cudaSetDevice(ctx->prm.device));
+  reset_timers(ctx);
+  const int64_t ob = ctx->outer_begin, oe = ctx->outer_end;
+  ctx->outer_begin = outer_begin;
+  ctx->outer_end = outer_end;
+  Plan pl{};
+  const double *d_grid = nullptr, *d_w = nullptr, *d_phi = nullptr;
+  int rc = prepare(ctx, pl, n_grid, n_orb, grid_xyz, weights, phi, &d_grid, &d_w, &d_phi);
+  ctx->outer_begin = ob;
+  ctx->outer_end = oe;
+  if (rc) return rc;
+  cudaStream_t st = ctx->st;
+  CUtensorMap tm_rho{};
+  if (!pl.f64 && (rc = make_tmap_3d(ctx, &tm_rho, ctx->rho.p, pl.parts_b == 3, pl.NGp, pl.NP, pl.parts_b, VF_BK, VF_BN)))
+    return rc;
+  const bool out_dev = is_device_ptr(V);
+  const size_t per_point = static_cast<size_t>(3) * pl.NP;
+  const int64_t n_out = pl.oe - pl.ob;
+  DBuf tmp;
+  for (int64_t c0 = pl.ob; c0 < pl.oe; c0 += pl.gc) {
+    const int64_t n_i = std::min<int64_t>(pl.gc, pl.oe - c0);
+    if ((rc = run_vfield(ctx, pl, d_grid, c0, n_i, &tm_rho))) return rc;
+    double* dst = V + (c0 - pl.ob) * per_point;
+    if (!out_dev) {
+      if (!ensure(ctx->vout, n_i * per_point * 8)) return fail(ctx, XTC_ERR_OOM, "V staging");
+      dst = ctx->vout.as<double>();
+    }
+    launch_vfield_export(ctx->V.p, pl.f64, pl.f64 ? 1 : pl.splits, pl.NP, n_i, pl.gc, dst, st);
+    CUDA_OK(cudaGetLastError());
+    if (!out_dev)
+      CUDA_OK(cudaMemcpyAsync(V + (c0 - pl.ob) * per_point, dst, n_i * per_point * 8, cudaMemcpyDeviceToHost, st));
+  }
+  (void)n_out;
+  if ((rc = check_device_error(ctx))) return rc;
+  finish_timers(ctx);
+  return XTC_OK;
+}

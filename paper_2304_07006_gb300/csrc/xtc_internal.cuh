@@ -1,0 +1,137 @@
+// Internal declarations shared by the xTC library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda.h>
+#include <stdint.h>
+
+namespace xtc {
+
+constexpr int MAX_NUC = 64;
+constexpr int MAX_TERMS = 27;   // (m, n, o) in {0,1,2}^3
+constexpr int MAX_SETS = 64;
+
+// Jastrow parameters as copied to the device (global memory).
+struct JastrowParams {
+  int n_nuc, n_terms, n_sets, pad;
+  double nuc[MAX_NUC][3];
+  int set[MAX_NUC];
+  int mno[MAX_TERMS][3];
+  double coef[MAX_SETS][MAX_TERMS];
+};
+
+// Per (outer point, nucleus) coefficients of the pair formula (see jastrow_coef.cuh).
+constexpr int NUC_COEF = 13;    // g[3], a01 a02 a11 a12 a21 a22, b11 b12 b21 b22
+constexpr int PT_COEF = 14;     // x y z, K0[3] K1[3] K2[3], Hc1 Hc2
+
+// Tile shapes of the tensor-core kernels.
+constexpr int VF_BM = 128;      // outer points per tile (TMEM lanes)
+constexpr int VF_BN = 160;      // orbital pairs per tile; 3 accumulators of 160 columns
+constexpr int VF_BK = 32;       // inner points per pipeline stage (64-byte rows, SWIZZLE_64B)
+constexpr int AS_BM = 128;      // step (d) tile rows (pairs pq)
+constexpr int AS_BN = 256;      // step (d) tile columns (pairs rs)
+constexpr int AS_BK = 32;
+constexpr int CHUNK_ALIGN = 128;
+
+// Error codes written by kernels into the context's device error word.
+constexpr int DEV_ERR_TIMEOUT_VF = 1;
+constexpr int DEV_ERR_TIMEOUT_AS = 2;
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// ---------------------------------------------------------------- launchers
+
+// Per-inner-point table for the producer: stride js floats per point:
+// x, y, z, a_j0, a_j1, ...  (a_jI = |r_j - R_I| / (1 + |r_j - R_I|)), padded points far away.
+void launch_jtab(const double* grid, int64_t n_grid, int64_t n_grid_pad, const JastrowParams* jp_dev,
+                 int n_nuc, int js, float* jtab, cudaStream_t st);
+
+// Pair products rho^T[pq][j] = w_j phi_p(j) phi_q(j) split into parts (fp16 or bf16), with
+// per-pair power-of-2 scale (fp16).  colexp[pq] receives the exponent used.
+void launch_rho_split(const double* phiT, const double* w, int64_t n_grid, int64_t n_grid_pad, int n_orb,
+                      int parts, bool bf16, bool scale, const int* pair_p, const int* pair_q,
+                      unsigned int* colmax_bits, int* colexp, void* out, cudaStream_t st);
+
+// FP64 pair products rho[j][pq] for the FP64 path (n_grid_pad rows, zero padded).
+void launch_rho_f64(const double* phi, const double* w, int64_t n_grid, int64_t n_grid_pad, int n_orb,
+                    const int* pair_p, const int* pair_q, double* rho, cudaStream_t st);
+
+// Transposed orbitals phiT[p][j] (FP64), zero padded to n_grid_pad.
+void launch_transpose_phi(const double* phi, int64_t n_grid, int64_t n_grid_pad, int n_orb, double* phiT,
+                          cudaStream_t st);
+
+// Finite check: sets *flag non-zero if any of n values is NaN/Inf.
+void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t st);
+
+// Steps (a)+(b), tensor cores.  V[z][pq][x][gcp] (FP32) for outer points [i0, i0 + n_i).
+struct VfieldArgs {
+  const double* grid;          // outer-point coordinates (global index space)
+  const JastrowParams* jp;
+  const float* jtab;           // [n_grid_pad][js]
+  const int* colexp;           // per-pair exponent of the rho scaling (0 when unscaled)
+  float* V;                    // output base
+  int64_t i0, n_i;             // outer range of this chunk
+  int64_t gcp;                 // padded chunk length (row stride of V)
+  int n_pair, n_nuc, js;
+  int kb_per_split, n_kb;      // inner K-blocks per split slice, total K-blocks
+  float g_scale;               // 2^sG folded into the gradient
+  float unscale_g;             // 2^-sG
+  int* err;
+};
+bool vfield_tc_supported(int n_nuc);
+void launch_vfield_tc(const CUtensorMap* tm_rho, const VfieldArgs& a, int parts, bool bf16, int splits,
+                      cudaStream_t st);
+
+// Steps (a)+(b), FP64 SIMT twin.  V[pq][x][gcp] (FP64).  jtab64[n_grid_pad][3 + n_nuc].
+void launch_jtab64(const double* grid, int64_t n_grid, int64_t n_pad, const JastrowParams* jp, int n_nuc,
+                   double* jtab, cudaStream_t st);
+void launch_vfield_f64_impl(const double* grid, const JastrowParams* jp, int n_nuc, const double* jtab64,
+                            const double* rho, int64_t n_pad, int n_pair, int64_t i0, int64_t n_i, int64_t gcp,
+                            double* V, cudaStream_t st);
+
+// Step (a) alone in FP64.
+void launch_jastrow_grad(const JastrowParams* jp, const double* r1, const double* r2, int64_t n, double* out,
+                         cudaStream_t st);
+
+// Step (c).  Reads V (T = float or double, [splits][pq][x][gcp]), writes L = (rho, Vx, Vy, Vz) and
+// R = (A, Bx, By, Bz) per outer point, either as split parts [part][pq][4*gcp] (fp16/bf16) or as FP64
+// [4*gcp][pq].
+struct FieldsArgs {
+  const void* V;
+  int splits;
+  const double* phiT;          // [n_orb][ldphi], global grid index
+  int64_t ldphi;
+  const double* w;
+  const double* evec;          // [rank][n_orb]  (gamma = sum_k lam_k c_k c_k^T)
+  const double* lam;           // [rank]
+  int rank;
+  int64_t i0, n_i, gcp;
+  int n_orb, n_pair;
+  int pts;                     // outer points per CTA
+  const int* pair_p;
+  const int* pair_q;
+  void* L;                     // outputs
+  void* R;
+  int out_parts;               // 0 = FP64 [4*gcp][pq]; 3 = bf16 x3 split [part][pq][4*gcp]
+};
+size_t fields_smem_bytes(int n_orb, int rank, int pts, bool f64);
+void launch_fields(const FieldsArgs& a, bool v_is_f64, cudaStream_t st);
+
+// Step (d), tensor cores: M[pq][rs] += sum_k L[pq][k] R[rs][k] over k < kdim (FP64 accumulator).
+void launch_assemble_tc(const CUtensorMap* tm_L, const CUtensorMap* tm_R, int n_pair, int kdim, double* M,
+                        int* err, cudaStream_t st);
+
+// Step (d), FP64 SIMT twin: M[pq][rs] += sum_k L[k][pq] R[k][rs].
+void launch_assemble_f64(const double* L, const double* R, int n_pair, int kdim, double* M, cudaStream_t st);
+
+// Final: M <- Delta U = -(M + M^T) in place; unpacking; Delta h; e0.  M row stride round_up(n_pair, AS_BN).
+void launch_symmetrize(double* M, int n_pair, cudaStream_t st);
+void launch_unpack(const double* M, int n_orb, int n_pair, double* dU, float* dU32, cudaStream_t st);
+void launch_onebody(const double* M, const double* gamma, int n_orb, int n_pair, double* dh, double* e0,
+                    cudaStream_t st);
+
+// V (FP32 or FP64, [splits][pq][x][gcp]) -> FP64 [n_i][3][pq] (for xtc_vfield).
+void launch_vfield_export(const void* V, bool f64, int splits, int n_pair, int64_t n_i, int64_t gcp,
+                          double* out, cudaStream_t st);
+
+}  // namespace xtc

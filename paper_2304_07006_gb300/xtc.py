@@ -1,0 +1,198 @@
+"""ctypes binding of the C ABI in include/xtc.h (argument marshalling only).
+
+Every step of the xTC build runs inside ``libxtc.so``.  Arrays may be numpy arrays (host) or
+torch tensors (host or CUDA); they are passed to the library as plain pointers.  Loading
+fails loudly when the library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libxtc.so")
+
+PREC_FP64, PREC_FP16X2, PREC_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp64": PREC_FP64, "fp16x2": PREC_FP16X2, "bf16x3": PREC_BF16X3}
+KERNEL_NAMES = ("prep", "vfield", "fields", "assemble", "final")
+
+EXPORTED = ("xtc_default_params", "xtc_create", "xtc_destroy", "xtc_strerror", "xtc_last_error_detail",
+            "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b", "xtc_jastrow_grad", "xtc_vfield",
+            "xtc_get_timings")
+
+
+class XtcParams(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int),
+                ("grid_chunk", ctypes.c_int64), ("split_k", ctypes.c_int), ("timing", ctypes.c_int)]
+
+
+class XtcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"xtc status {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libxtc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+    lib.xtc_default_params.argtypes = [ctypes.POINTER(XtcParams)]
+    lib.xtc_default_params.restype = None
+    lib.xtc_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(XtcParams)]
+    lib.xtc_destroy.argtypes = [P]
+    lib.xtc_strerror.argtypes = [I]
+    lib.xtc_strerror.restype = ctypes.c_char_p
+    lib.xtc_last_error_detail.argtypes = [P]
+    lib.xtc_last_error_detail.restype = ctypes.c_char_p
+    lib.xtc_set_jastrow.argtypes = [P, I, D, D, I, I, D, D]
+    lib.xtc_set_outer_range.argtypes = [P, I64, I64]
+    lib.xtc_build_1b2b.argtypes = [P, I64, I, D, D, D, D, D, D, D, D]
+    lib.xtc_jastrow_grad.argtypes = [P, I64, D, D, D]
+    lib.xtc_vfield.argtypes = [P, I64, I, D, D, D, I64, I64, D]
+    lib.xtc_get_timings.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), I]
+    for name in ("xtc_create", "xtc_destroy", "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b",
+                 "xtc_jastrow_grad", "xtc_vfield", "xtc_get_timings"):
+        getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Address of a contiguous numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _f64(a):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float64)
+    if hasattr(a, "dtype") and str(a.dtype) != "torch.float64":
+        raise TypeError("float64 tensors are required")
+    return a
+
+
+class Context:
+    """One library context (one device, one stream, one precision)."""
+
+    def __init__(self, precision="fp16x2", device=0, stream=None, grid_chunk=0, split_k=0, timing=False):
+        lib = load()
+        self._lib = lib
+        p = XtcParams()
+        lib.xtc_default_params(ctypes.byref(p))
+        p.device = device
+        p.stream = stream
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.grid_chunk = grid_chunk
+        p.split_k = split_k
+        p.timing = 1 if timing else 0
+        h = ctypes.c_void_p()
+        rc = lib.xtc_create(ctypes.byref(h), ctypes.byref(p))
+        if rc != 0:
+            raise XtcError(rc, lib.xtc_strerror(rc).decode())
+        self._h = h
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.xtc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc):
+        if rc != 0:
+            detail = self._lib.xtc_last_error_detail(self._h).decode()
+            raise XtcError(rc, f"{self._lib.xtc_strerror(rc).decode()} ({detail})")
+
+    def set_jastrow(self, nuc_xyz, nuc_set, terms, coef):
+        nuc = np.ascontiguousarray(nuc_xyz, dtype=np.float64)
+        ns = np.ascontiguousarray(nuc_set, dtype=np.int32)
+        tm = np.ascontiguousarray(terms, dtype=np.int32)
+        cf = np.ascontiguousarray(coef, dtype=np.float64)
+        self._check(self._lib.xtc_set_jastrow(self._h, nuc.shape[0], _ptr(nuc), _ptr(ns), cf.shape[0],
+                                              tm.shape[0], _ptr(tm), _ptr(cf)))
+
+    def set_outer_range(self, begin=0, end=-1):
+        self._check(self._lib.xtc_set_outer_range(self._h, int(begin), int(end)))
+
+    def build(self, grid, weights, phi, gamma, dU=None, dU_f32=None, dh=None, e0=None, want_dU=True):
+        """Runs the build.  With numpy inputs and no outputs given, returns numpy outputs."""
+        grid, weights, phi, gamma = _f64(grid), _f64(weights), _f64(phi), _f64(gamma)
+        n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+        if dU is None and dU_f32 is None and want_dU:
+            dU = np.empty((n_orb,) * 4)
+        if dh is None:
+            dh = np.empty((n_orb, n_orb))
+        if e0 is None:
+            e0 = np.empty(1)
+        self._check(self._lib.xtc_build_1b2b(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
+                                             _ptr(gamma), _ptr(dU), _ptr(dU_f32), _ptr(dh), _ptr(e0)))
+        return {"dU": dU if dU is not None else dU_f32, "dh": dh, "e0": e0}
+
+    def jastrow_grad(self, r1, r2, out=None):
+        r1, r2 = _f64(r1), _f64(r2)
+        n = int(r1.shape[0])
+        if out is None:
+            out = np.empty((n, 3))
+        self._check(self._lib.xtc_jastrow_grad(self._h, n, _ptr(r1), _ptr(r2), _ptr(out)))
+        return out
+
+    def vfield(self, grid, weights, phi, outer_begin, outer_end, out=None):
+        grid, weights, phi = _f64(grid), _f64(weights), _f64(phi)
+        n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+        n_pair = n_orb * (n_orb + 1) // 2
+        if out is None:
+            out = np.empty((outer_end - outer_begin, 3, n_pair))
+        self._check(self._lib.xtc_vfield(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
+                                         int(outer_begin), int(outer_end), _ptr(out)))
+        return out
+
+    def timings(self):
+        ms = (ctypes.c_double * 5)()
+        ln = (ctypes.c_int64 * 5)()
+        self._check(self._lib.xtc_get_timings(self._h, ms, ln, 5))
+        return {k: (ms[i], ln[i]) for i, k in enumerate(KERNEL_NAMES)}
+
+
+def pair_index(n_orb):
+    """(p, q) of every packed pair index, p <= q, row-major upper triangle."""
+    p, q = np.triu_indices(n_orb)
+    return p, q
+
+
+def unpack_pairs(Vp, n_orb):
+    """[..., n_pair] -> [..., n_orb, n_orb] symmetric."""
+    p, q = pair_index(n_orb)
+    out = np.zeros(Vp.shape[:-1] + (n_orb, n_orb))
+    out[..., p, q] = Vp
+    out[..., q, p] = Vp
+    return out

@@ -1,0 +1,66 @@
+"""CPU checks of the C ABI: the library loads without a GPU and exports every entry point that
+include/xtc.h declares, and the binding names the same set."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "xtc.h")
+
+
+def declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"XTC_API\s+[\w\s\*]+?\b(xtc_\w+)\s*\(", src)))
+
+
+def _lib_path():
+    from paper_2304_07006_gb300 import xtc
+    if not os.path.exists(xtc.LIB_PATH):
+        from paper_2304_07006_gb300 import _build
+        _build.build()
+    return xtc.LIB_PATH
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for must in ("xtc_create", "xtc_set_jastrow", "xtc_build_1b2b", "xtc_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(_lib_path())
+    missing = [n for n in declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_the_declared_symbols():
+    from paper_2304_07006_gb300 import xtc
+    assert sorted(xtc.EXPORTED) == declared()
+
+
+def test_strerror_and_defaults_without_gpu():
+    from paper_2304_07006_gb300 import xtc
+    lib = xtc.load(_lib_path())
+    assert lib.xtc_strerror(0) == b"success"
+    assert b"symmetric" in lib.xtc_strerror(-2)
+    p = xtc.XtcParams()
+    lib.xtc_default_params(ctypes.byref(p))
+    assert p.precision == xtc.PREC_FP16X2 and p.grid_chunk == 0
+    # argument checks happen before any device call
+    h = ctypes.c_void_p()
+    assert lib.xtc_create(ctypes.byref(h), None) == -1
+    p.grid_chunk = 100  # not a multiple of 128
+    assert lib.xtc_create(ctypes.byref(h), ctypes.byref(p)) == -1
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2304_07006_gb300 import xtc
+    saved = xtc._lib
+    xtc._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="missing"):
+            xtc.load(str(tmp_path / "nope.so"))
+    finally:
+        xtc._lib = saved

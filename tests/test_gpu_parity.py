@@ -1,0 +1,231 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Tolerances (Hartree): FP64 path 1e-8 absolute on every Delta U / Delta h entry and on the
+constant (observed ~1e-14 on small inputs); mixed paths (fp16x2, bf16x3) 1e-6 absolute, the
+accuracy target of the mixed-precision build.  Full-size workloads are compared on sampled
+outer points: the outputs are linear in the outer grid sum, so the GPU run restricted to an
+outer range equals the oracle restricted to the same points (full inner sum in both)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import direct, jastrow
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-8, "fp16x2": 1e-6, "bf16x3": 1e-6}
+MIXED = ("fp16x2", "bf16x3")
+
+
+def ctx_for(p, prec, **kw):
+    from paper_2304_07006_gb300 import Context
+    c = Context(prec, **kw)
+    c.set_jastrow(p.nuc_xyz, p.nuc_set, p.terms, p.coef)
+    return c
+
+
+def max_err(out, ref):
+    return max(np.abs(out["dU"] - ref["dU"]).max(), np.abs(out["dh"] - ref["dh"]).max(),
+               abs(float(out["e0"][0]) - ref["e0"]))
+
+
+@pytest.fixture(scope="module")
+def small():
+    p = synth.make_small(n_orb=6, n_rad=8, n_theta=4, n_phi=5, n_atoms=2, seed=5, n_occ=2)  # 320 points
+    g = synth.random_density(p.n_orb, 3)
+    return p, g, direct.build(p, g)
+
+
+# ------------------------------------------------------------------ step (a)
+
+def test_jastrow_gradient_fp64_matches_oracle():
+    p = synth.make_small(n_atoms=4, seed=2, terms=np.array([(0, 0, 1), (1, 2, 1), (2, 2, 2), (0, 2, 0), (1, 1, 0)]))
+    rng = np.random.default_rng(0)
+    r1 = rng.uniform(-3, 3, size=(500, 3))
+    r2 = rng.uniform(-3, 3, size=(500, 3))
+    r2[:7] = r1[:7]                       # coincident pairs
+    r1[7] = p.nuc_xyz[0]                  # a point on a nucleus
+    want = jastrow.grad1(r1, r2, p.nuc_xyz, p.nuc_set, p.terms, p.coef)
+    with ctx_for(p, "fp64") as c:
+        got = c.jastrow_grad(r1, r2)
+    assert np.abs(got - want).max() < 1e-14 * max(1.0, np.abs(want).max())
+
+
+# ------------------------------------------------------------------ step (b)
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16x2", "bf16x3"])
+def test_vfield_matches_oracle(small, prec):
+    from paper_2304_07006_gb300 import unpack_pairs
+    p, _, _ = small
+    jas = (p.nuc_xyz, p.nuc_set, p.terms, p.coef)
+    want = direct.vfield(p.grid, p.weights, p.phi, jas, np.arange(p.n_grid))
+    with ctx_for(p, prec) as c:
+        got = unpack_pairs(c.vfield(p.grid, p.weights, p.phi, 0, p.n_grid), p.n_orb)
+    rel = np.abs(got - want).max() / np.abs(want).max()
+    assert rel < (1e-13 if prec == "fp64" else 2e-6), rel
+
+
+# ------------------------------------------------------------------ whole path, small inputs
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16x2", "bf16x3"])
+def test_build_small_random_density(small, prec):
+    p, g, ref = small
+    with ctx_for(p, prec) as c:
+        out = c.build(p.grid, p.weights, p.phi, g)
+    err = max_err(out, ref)
+    assert err < TOL[prec], err
+    if prec == "fp64":
+        assert err < 1e-13
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16x2"])
+def test_chunks_splits_and_ragged_tail(small, prec):
+    p, g, ref = small
+    # three chunks of 128 outer points (the last one ragged), inner sum split in 3 slices
+    with ctx_for(p, prec, grid_chunk=128, split_k=3) as c:
+        out = c.build(p.grid, p.weights, p.phi, g)
+    assert max_err(out, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_four_nuclei_full_rank_density_in_two_groups(prec):
+    # rank 20 > 16 exercises the grouped factorisation of gamma
+    p = synth.make_small(n_orb=20, n_rad=6, n_theta=4, n_phi=5, n_atoms=4, seed=9)
+    g = synth.random_density(20, 4)
+    ref = direct.build(p, g)
+    with ctx_for(p, prec) as c:
+        out = c.build(p.grid, p.weights, p.phi, g)
+    assert max_err(out, ref) < TOL[prec]
+
+
+def test_single_orbital_and_single_nucleus():
+    p = synth.make_small(n_orb=1, n_rad=5, n_theta=3, n_phi=4, n_atoms=1, seed=3)
+    ref = direct.build(p)
+    for prec in ("fp64", "fp16x2"):
+        with ctx_for(p, prec) as c:
+            out = c.build(p.grid, p.weights, p.phi, p.gamma)
+        assert max_err(out, ref) < TOL[prec]
+
+
+def test_zero_density_and_empty_outer_range(small):
+    p, _, _ = small
+    with ctx_for(p, "fp16x2") as c:
+        out = c.build(p.grid, p.weights, p.phi, np.zeros((p.n_orb, p.n_orb)))
+        assert np.abs(out["dU"]).max() == 0.0 and out["e0"][0] == 0.0
+        c.set_outer_range(5, 5)
+        out = c.build(p.grid, p.weights, p.phi, p.gamma)
+        assert np.abs(out["dU"]).max() == 0.0
+
+
+def test_outer_ranges_add_up(small):
+    p, g, ref = small
+    with ctx_for(p, "fp64") as c:
+        c.set_outer_range(0, 100)
+        a = c.build(p.grid, p.weights, p.phi, g)
+        c.set_outer_range(100, -1)
+        b = c.build(p.grid, p.weights, p.phi, g)
+    assert np.abs(a["dU"] + b["dU"] - ref["dU"]).max() < 1e-13
+
+
+def test_device_inputs_match_host_inputs_bitwise(small):
+    torch = pytest.importorskip("torch")
+    p, g, _ = small
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with ctx_for(p, "fp16x2") as c:
+        host = c.build(p.grid, p.weights, p.phi, g)
+        dU = torch.empty((p.n_orb,) * 4, dtype=torch.float64, device="cuda")
+        dh = torch.empty((p.n_orb,) * 2, dtype=torch.float64, device="cuda")
+        e0 = torch.empty(1, dtype=torch.float64, device="cuda")
+        c.build(dev(p.grid), dev(p.weights), dev(p.phi), dev(g), dU=dU, dh=dh, e0=e0)
+    assert np.array_equal(dU.cpu().numpy(), host["dU"])
+    assert np.array_equal(dh.cpu().numpy(), host["dh"])
+    assert e0.item() == host["e0"][0]
+
+
+# ------------------------------------------------------------------ error statuses
+
+def test_error_statuses(small):
+    from paper_2304_07006_gb300 import Context, XtcError
+    p, g, _ = small
+    with Context("fp16x2") as c:
+        with pytest.raises(XtcError) as e:
+            c.build(p.grid, p.weights, p.phi, g)
+        assert e.value.code == -7                              # no Jastrow yet
+        with pytest.raises(XtcError) as e:
+            c.set_jastrow(p.nuc_xyz, p.nuc_set, np.array([(0, 3, 1)]), np.ones((p.n_sets, 1)))
+        assert e.value.code == -1                              # power out of range
+        c.set_jastrow(p.nuc_xyz, p.nuc_set, p.terms, p.coef)
+        bad = g.copy()
+        bad[0, 1] += 1e-3
+        with pytest.raises(XtcError) as e:
+            c.build(p.grid, p.weights, p.phi, bad)
+        assert e.value.code == -2                              # gamma not symmetric
+        phi = p.phi.copy()
+        phi[3, 1] = np.nan
+        with pytest.raises(XtcError) as e:
+            c.build(p.grid, p.weights, phi, g)
+        assert e.value.code == -3                              # non-finite input
+        five = np.vstack([p.nuc_xyz, p.nuc_xyz + 1.0, [[3.0, 0, 0]]])
+        c.set_jastrow(five, [0] * 5, p.terms, p.coef[:1])
+        with pytest.raises(XtcError) as e:
+            c.build(p.grid, p.weights, p.phi, g)
+        assert e.value.code == -8                              # > 4 nuclei on tensor cores
+        # the context stays usable after errors
+        c.set_jastrow(p.nuc_xyz, p.nuc_set, p.terms, p.coef)
+        c.build(p.grid, p.weights, p.phi, g)
+
+
+def test_fp64_path_takes_many_nuclei():
+    p = synth.make_small(n_orb=3, n_rad=4, n_theta=3, n_phi=3, n_atoms=2, seed=1)
+    rng = np.random.default_rng(2)
+    nuc = rng.uniform(-2, 2, size=(7, 3))
+    from dataclasses import replace
+    p = replace(p, nuc_xyz=nuc, nuc_set=np.arange(7) % 2, coef=rng.uniform(-0.1, 0.1, (2, 9)))
+    ref = direct.build(p)
+    with ctx_for(p, "fp64") as c:
+        out = c.build(p.grid, p.weights, p.phi, p.gamma)
+    assert max_err(out, ref) < 1e-12
+
+
+# ------------------------------------------------------------------ measured workloads
+
+def test_h2_workload_all_precisions():
+    p = synth.make_config("h2")
+    ref = direct.build(p)
+    for prec in ("fp64", "fp16x2", "bf16x3"):
+        with ctx_for(p, prec) as c:
+            out = c.build(p.grid, p.weights, p.phi, p.gamma)
+        assert max_err(out, ref) < TOL[prec], prec
+
+
+def _sampled(name, n_sample, seed):
+    p = synth.make_config(name)
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(p.n_grid)
+    return synth.permute_grid(p, perm)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16x2", "bf16x3"])
+def test_water_workload_sampled_outer_points(prec):
+    p = _sampled("water", 48, 11)
+    ref = direct.build(p, outer=np.arange(48))
+    with ctx_for(p, prec) as c:
+        c.set_outer_range(0, 48)
+        out = c.build(p.grid, p.weights, p.phi, p.gamma)
+    assert max_err(out, ref) < TOL[prec]
+
+
+@pytest.fixture(scope="module")
+def n2_sampled():
+    p = _sampled("n2", 16, 12)
+    return p, direct.build(p, outer=np.arange(16))
+
+
+@pytest.mark.parametrize("prec", ["fp16x2", "bf16x3", "fp64"])
+def test_n2_workload_sampled_outer_points(n2_sampled, prec):
+    p, ref = n2_sampled
+    with ctx_for(p, prec) as c:
+        c.set_outer_range(0, 16)
+        out = c.build(p.grid, p.weights, p.phi, p.gamma, want_dU=True)
+    err = max_err(out, ref)
+    assert err < TOL[prec], err
