@@ -161,8 +161,7 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
         qi = q;
         ++q;
       }
-      const TC v = live ? static_cast<TC>(vload<TV>(V, a.splits, sstride,
-                                                    (static_cast<int64_t>(qi) * 3 + x) * a.gcp + il))
+      const TC v = live ? static_cast<TC>(vload<TV>(V, a.splits, sstride, (static_cast<int64_t>(qi) * 3 + x) * a.gcp + il))
                         : TC(0);
 #pragma unroll
       for (int kk = 0; kk < RMAX; ++kk)
@@ -246,8 +245,8 @@ size_t fields_smem_bytes(int n_orb, int rank, int pts, bool f64) {
   return f64 ? carve<double>(nullptr, nullptr, n_orb, rank, pts) : carve<float>(nullptr, nullptr, n_orb, rank, pts);
 }
 
-void launch_fields(const FieldsArgs& a, bool v_is_f64, cudaStream_t st) {
-  if (v_is_f64)
+void launch_fields(const FieldsArgs& a, bool f64, cudaStream_t st) {
+  if (f64)
     launch_t<double, double, 0>(a, st);
   else
     launch_t<float, float, 3>(a, st);

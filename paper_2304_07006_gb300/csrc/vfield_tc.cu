@@ -2,21 +2,26 @@
 // correction" section,
 //     V_x[i][pq] = sum_j G_x(i, j) rho^T[pq][j],   G_x(i, j) = d/dx_i u(r_i, r_j),
 //     rho^T[pq][j] = w_j phi_p(j) phi_q(j),
-// as one GEMM per outer-point tile with the Jastrow gradient generated on the fly.
+// as a GEMM whose A operand (the Jastrow gradient) is generated on the fly.
 //
-// CTA tile: 128 outer points (TMEM lanes) x 160 orbital pairs x 3 components, three FP32
-// accumulators of 160 TMEM columns each.  Per pipeline stage (32 inner points):
-//   * warp 0 (one lane) TMA-loads the rho^T tile of each split part (160 rows x 64 B, 64-byte
-//     swizzle) onto an mbarrier with a transaction count;
-//   * warps 2..9 (256 threads, one outer point and 16 inner points each) evaluate nabla_1 u in
-//     FP32, split every value into fp16 (2 parts) or bf16 (3 parts) and store the A tiles in the
-//     same swizzled K-major layout, then arrive on a second mbarrier;
-//   * warp 1 (one lane) issues tcgen05.mma for every component and every split product into the
-//     TMEM accumulators and commits the stage back to the producers.
-// After the last stage warps 2..5 read the accumulators with tcgen05.ld, undo the power-of-2
-// scalings and store V[pq][x][i] (FP32, outer index contiguous).
-#include <cuda_fp16.h>
+// CTA tile: 32 outer points x 3 components = 96 A rows (row x*32 + point; rows 96..127 stay zero)
+// x 160 orbital pairs, 32 inner points per pipeline stage (64-byte rows, 64-byte swizzle, K-major).
+//   * warp 0 (one lane): per stage, TMA loads of the rho^T tile of each split part (160 x 64 B)
+//     and a bulk copy of the 32-point inner table (coordinates hi/lo and a_jI) into shared memory;
+//   * warps 2..9: two groups of four warps take alternate stages; in a stage, warp c of a group
+//     evaluates nabla_1 u in FP32 for its 8 inner points (one 16-byte chunk of every row) and all
+//     32 outer points (one per lane, coefficients in registers), splits it into fp16 (2 parts)
+//     or bf16 (3 parts) and stores the swizzled A tiles;
+//   * warp 1 (one lane): tcgen05.mma for every split product into one of two TMEM accumulators;
+//   * warps 10..13: every `kd` stages they add the finished accumulator into an FP32 running sum
+//     kept in TMEM (tcgen05.ld / st) while the MMA fills the other accumulator, and at the end
+//     store the sum, unscaled, as V[pq][x][i].
+// The tensor-core accumulator truncates toward zero at each MMA, which biases a long inner sum.
+// Each range is short (default two stages), its MMAs issue the small cross products of all its
+// stages first so that only the hi x hi products meet a large accumulator, and the ranges are
+// summed with round-to-nearest FP32 adds.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "jastrow_coef.cuh"
 #include "ptx_sm100.cuh"
@@ -25,26 +30,42 @@
 namespace xtc {
 namespace {
 
-constexpr int PROD_WARPS = 8;
-constexpr int VF_THREADS = 64 + PROD_WARPS * 32;
-constexpr int A_TILE = VF_BM * 64;  // bytes per (component, part) tile
-constexpr int B_TILE = VF_BN * 64;  // bytes per part tile
+constexpr int TP = 32;               // outer points per tile
+constexpr int PROD_WARPS = 8;        // two groups of four, alternate stages
+constexpr int GROUP_WARPS = 4;       // one per 16-byte chunk (8 inner points) of a stage
+constexpr int DRAIN_WARPS = 4;
+constexpr int THREADS = (2 + PROD_WARPS + DRAIN_WARPS) * 32;
+constexpr int A_TILE = 128 * 64;     // bytes per part tile (128 rows of 64 B)
+constexpr int B_TILE = VF_BN * 64;   // bytes per part tile (160 rows of 64 B)
+constexpr int JT_BYTES = VF_BK * 12 * 4;
+constexpr int D_COLS = VF_BN;        // accumulator columns
+constexpr uint32_t S_COL = 2 * D_COLS;  // running-sum columns start
 
 template <int PARTS>
 struct VfCfg {
-  static constexpr int STAGES = PARTS == 2 ? 3 : 2;
+  static constexpr int STAGES = PARTS == 2 ? 5 : 3;
   static constexpr int NPROD = PARTS == 2 ? 3 : 6;
-  static constexpr int A_BYTES = 3 * PARTS * A_TILE;
-  static constexpr int STAGE_BYTES = A_BYTES + PARTS * B_TILE;
+  static constexpr int A_BYTES = PARTS * A_TILE;
+  static constexpr int B_BYTES = PARTS * B_TILE;
+  static constexpr int STAGE_BYTES = ((A_BYTES + B_BYTES + JT_BYTES + 1023) / 1024) * 1024;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 };
 
-// (A part, B part) of each split product, in issue order.
+// (A part, B part) of each split product in issue order: the small cross products first and
+// hi x hi last, so that the truncations of the early MMAs act on a small accumulator.
+template <int PARTS>
 __device__ __forceinline__ void prod_parts(int p, int& pa, int& pb) {
-  constexpr int a[6] = {0, 0, 1, 0, 1, 2};
-  constexpr int b[6] = {0, 1, 0, 2, 1, 0};
-  pa = a[p];
-  pb = b[p];
+  if (PARTS == 2) {
+    constexpr int a[3] = {0, 1, 0};
+    constexpr int b[3] = {1, 0, 0};
+    pa = a[p];
+    pb = b[p];
+  } else {
+    constexpr int a[6] = {1, 0, 2, 0, 1, 0};
+    constexpr int b[6] = {1, 2, 0, 1, 0, 0};
+    pa = a[p];
+    pb = b[p];
+  }
 }
 
 __device__ __forceinline__ float rsqrt_approx(float x) {
@@ -59,7 +80,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 template <bool BF16>
-__device__ __forceinline__ void split_pair(float a, float b, uint32_t* out /*[PARTS]*/, int parts) {
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t* out) {
   if (!BF16) {
     __half2 h = __floats2half2_rn(a, b);
     const float2 hf = __half22float2(h);
@@ -80,40 +101,77 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t* out /*[PA
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+__device__ __forceinline__ float4 ld_shared_f4(uint32_t addr) {
+  float4 r;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "r"(addr));
+  return r;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+__device__ __forceinline__ void tmem_st_32x32b_x32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 template <int PARTS, int NNUC>
-__global__ void __launch_bounds__(VF_THREADS, 1)
+__global__ void __launch_bounds__(THREADS, 1)
     vfield_tc_kernel(const __grid_constant__ CUtensorMap tm_rho, const VfieldArgs args) {
   using Cfg = VfCfg<PARTS>;
   constexpr bool BF16 = PARTS == 3;
   constexpr int STAGES = Cfg::STAGES;
-  constexpr int JS = 12;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
-  uint64_t* tma_full = bars;
-  uint64_t* g_full = bars + STAGES;
-  uint64_t* empty = bars + 2 * STAGES;
-  uint64_t* acc_bar = bars + 3 * STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 1);
+  uint64_t* tma_full = bars;                 // [STAGES]
+  uint64_t* g_full = bars + STAGES;          // [STAGES]
+  uint64_t* empty = bars + 2 * STAGES;       // [STAGES]
+  uint64_t* d_full = bars + 3 * STAGES;      // [2]
+  uint64_t* d_free = bars + 3 * STAGES + 2;  // [2]
+  uint64_t* fin_bar = bars + 3 * STAGES + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m_tile = blockIdx.x, n_tile = blockIdx.y, split = blockIdx.z;
   const int kb0 = split * args.kb_per_split;
   const int kb1 = min(args.n_kb, kb0 + args.kb_per_split);
+  const int n_it = kb1 - kb0;
+  const int kd = args.kd;
+  const int n_ranges = (n_it + kd - 1) / kd;
 
+  // rows 96..127 of every A tile are never written by the producers: zero them once
+  for (int s = 0; s < STAGES; ++s)
+    for (int p = 0; p < PARTS; ++p) {
+      uint4* z = reinterpret_cast<uint4*>(smem + s * Cfg::STAGE_BYTES + p * A_TILE + 96 * 64);
+      for (int k = threadIdx.x; k < 32 * 64 / 16; k += THREADS) z[k] = make_uint4(0, 0, 0, 0);
+    }
+  fence_proxy_async_smem();
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&tma_full[s], 1);
-      mbar_init(&g_full[s], PROD_WARPS);
+      mbar_init(&g_full[s], GROUP_WARPS);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(acc_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&d_full[b], 1);
+      mbar_init(&d_free[b], DRAIN_WARPS);
+    }
+    mbar_init(fin_bar, 1);
     *abort_flag = 0;
     fence_mbar_init();
     tma_prefetch_desc(&tm_rho);
@@ -130,18 +188,19 @@ __global__ void __launch_bounds__(VF_THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------------------------------------------------------- TMA producer
+      // ---------------------------------------------------------------- TMA / bulk-copy producer
       int issued_end = kb0;
       for (int kb = kb0; kb < kb1; ++kb) {
         const int it = kb - kb0, s = it % STAGES, n = it / STAGES;
         if (n > 0 && !mbar_wait(&empty[s], (n - 1) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)) break;
-        mbar_arrive_expect_tx(&tma_full[s], PARTS * B_TILE);
-        uint8_t* bdst = smem + s * Cfg::STAGE_BYTES + Cfg::A_BYTES;
+        mbar_arrive_expect_tx(&tma_full[s], PARTS * B_TILE + JT_BYTES);
+        uint8_t* st = smem + s * Cfg::STAGE_BYTES;
         for (int p = 0; p < PARTS; ++p)
-          tma_load_3d(bdst + p * B_TILE, &tm_rho, &tma_full[s], kb * VF_BK, n_tile * VF_BN, p);
+          tma_load_3d(st + Cfg::A_BYTES + p * B_TILE, &tm_rho, &tma_full[s], kb * VF_BK, n_tile * VF_BN, p);
+        bulk_g2s(st + Cfg::A_BYTES + Cfg::B_BYTES, args.jtab + static_cast<int64_t>(kb) * VF_BK * 12, JT_BYTES,
+                 &tma_full[s]);
         issued_end = kb + 1;
       }
-      // make sure no bulk copy into this CTA's shared memory is still in flight
       int zero = 0;
       for (int kb = max(kb0, issued_end - STAGES); kb < issued_end; ++kb) {
         const int it = kb - kb0;
@@ -152,144 +211,175 @@ __global__ void __launch_bounds__(VF_THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------------------------------------------------------- MMA issuer
-      constexpr uint32_t idesc = idesc_f16(VF_BM, VF_BN, BF16);
-      for (int kb = kb0; kb < kb1; ++kb) {
-        const int it = kb - kb0, s = it % STAGES, n = it / STAGES;
-        if (!mbar_wait(&tma_full[s], n & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)) break;
-        if (!mbar_wait(&g_full[s], n & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)) break;
+      // A range of kd stages goes into one TMEM accumulator: first every cross product of all its
+      // stages (the accumulator is still small), then every hi x hi product.
+      constexpr uint32_t idesc = idesc_f16(128, VF_BN, BF16);
+      bool alive = true;
+      for (int r = 0; r < n_ranges && alive; ++r) {
+        const int it0 = r * kd, it1 = min(n_it, it0 + kd);
+        const int b = r & 1, u = r >> 1;
+        if (u >= 1 && !mbar_wait(&d_free[b], (u - 1) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)) break;
+        for (int it = it0; it < it1 && alive; ++it) {
+          const int s = it % STAGES, n = it / STAGES;
+          alive = mbar_wait(&tma_full[s], n & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF) &&
+                  mbar_wait(&g_full[s], n & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF);
+        }
+        if (!alive) break;
         tc_fence_after();
-        const uint32_t sa = smem_base + s * Cfg::STAGE_BYTES;
-        const uint32_t sb = sa + Cfg::A_BYTES;
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int it = it0; it < it1; ++it) {
+            const uint32_t sa = smem_base + (it % STAGES) * Cfg::STAGE_BYTES;
+            const uint32_t sb = sa + Cfg::A_BYTES;
 #pragma unroll
-        for (int x = 0; x < 3; ++x) {
+            for (int p = 0; p < Cfg::NPROD; ++p) {
+              if ((p == Cfg::NPROD - 1) != (pass == 1)) continue;
+              int pa, pb;
+              prod_parts<PARTS>(p, pa, pb);
 #pragma unroll
-          for (int p = 0; p < Cfg::NPROD; ++p) {
-            int pa, pb;
-            prod_parts(p, pa, pb);
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-              const uint64_t ad = sdesc_kmajor_sw64(sa + (x * PARTS + pa) * A_TILE + ks * 32);
-              const uint64_t bd = sdesc_kmajor_sw64(sb + pb * B_TILE + ks * 32);
-              tc_mma_f16(tmem + x * VF_BN, ad, bd, idesc, (it > 0 || p > 0 || ks > 0) ? 1u : 0u);
+              for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t ad = sdesc_kmajor_sw64(sa + pa * A_TILE + ks * 32);
+                const uint64_t bd = sdesc_kmajor_sw64(sb + pb * B_TILE + ks * 32);
+                tc_mma_f16(tmem + b * D_COLS, ad, bd, idesc, (it == it0 && p == 0 && ks == 0) ? 0u : 1u);
+              }
             }
           }
         }
-        tc_commit(&empty[s]);
+        for (int it = it0; it < it1; ++it) tc_commit(&empty[it % STAGES]);
+        tc_commit(&d_full[b]);
       }
-      tc_commit(acc_bar);  // also on an abort, so the accumulator wait below ends
+      // every MMA issued by this thread has completed once fin_bar fires
+      tc_commit(fin_bar);
+      int zero = 0;
+      mbar_wait(fin_bar, 0, reinterpret_cast<volatile int*>(&zero), args.err, DEV_ERR_TIMEOUT_VF);
     }
-  } else {
+  } else if (warp < 2 + PROD_WARPS) {
     // ------------------------------------------------------------------ gradient producers
-    const int pt = threadIdx.x - 64;
-    const int row = pt & (VF_BM - 1);
-    const int jh = pt >> 7;
-    const int64_t il = static_cast<int64_t>(m_tile) * VF_BM + row;
+    const int group = (warp - 2) >> 2;  // stages it = group, group + 2, ...
+    const int c = (warp - 2) & 3;       // inner points 8c .. 8c+7 of the stage
+    const int pt = lane;                // outer point of the tile
+    const int64_t il = static_cast<int64_t>(m_tile) * TP + pt;
     const int64_t ig = args.i0 + (il < args.n_i ? il : args.n_i - 1);
     float pc[PT_COEF];
     float nc[NNUC * NUC_COEF];
     const double gx = args.grid[3 * ig], gy = args.grid[3 * ig + 1], gz = args.grid[3 * ig + 2];
     point_coefs_fixed<float, NNUC>(*args.jp, gx, gy, gz, static_cast<double>(args.g_scale), pc, nc);
-    // low parts of the outer point's coordinates (x = hi + lo)
     const float xl = static_cast<float>(gx - static_cast<double>(pc[0]));
     const float yl = static_cast<float>(gy - static_cast<double>(pc[1]));
     const float zl = static_cast<float>(gz - static_cast<double>(pc[2]));
-    const int wgroup = warp - 2;
+    uint32_t row_off[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) row_off[x] = sw64_offset(x * TP + pt, c);
 
-    for (int kb = kb0; kb < kb1; ++kb) {
-      const int it = kb - kb0, s = it % STAGES, n = it / STAGES;
-      const bool got = n == 0 || mbar_wait(&empty[s], (n - 1) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF);
-      if (!__all_sync(0xffffffffu, got)) break;  // warp-uniform decision
+    for (int it = group; it < n_it; it += 2) {
+      const int s = it % STAGES, n = it / STAGES;
+      bool got = n == 0 || mbar_wait(&empty[s], (n - 1) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF);
+      got = got && mbar_wait(&tma_full[s], n & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF);
+      if (!__all_sync(0xffffffffu, got)) break;
       const uint32_t sa = smem_base + s * Cfg::STAGE_BYTES;
+      const uint32_t jt = sa + Cfg::A_BYTES + Cfg::B_BYTES + c * 8 * 48;
+      float gv[3][8];
 #pragma unroll
-      for (int grp = 0; grp < 2; ++grp) {
-        const int64_t jbase = static_cast<int64_t>(kb) * VF_BK + jh * 16 + grp * 8;
-        float gv[3][8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const float* jp = args.jtab + (jbase + u) * JS;
-          const float4 p0 = __ldg(reinterpret_cast<const float4*>(jp));
-          const float4 p1 = __ldg(reinterpret_cast<const float4*>(jp + 4));
-          float aj[NNUC];
-          aj[0] = p0.w;
-          if (NNUC > 1) aj[NNUC > 1 ? 1 : 0] = p1.w;
-          if (NNUC > 2) {
-            const float4 p2 = __ldg(reinterpret_cast<const float4*>(jp + 8));
-            aj[NNUC > 2 ? 2 : 0] = p2.x;
-            if (NNUC > 3) aj[NNUC > 3 ? 3 : 0] = p2.y;
-          }
-          // (hi_i - hi_j) is exact for nearby points; the low parts restore the rest
-          const float dx = (pc[0] - p0.x) + (xl - p1.x);
-          const float dy = (pc[1] - p0.y) + (yl - p1.y);
-          const float dz = (pc[2] - p0.z) + (zl - p1.z);
-          const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          const float rinv = rsqrt_approx(fmaxf(r2, 1e-30f));
-          const float r = r2 * rinv;
-          const float q = rcp_approx(1.0f + r);
-          const float b = r * q;
-          const float sfac = r2 > 0.0f ? q * q * rinv : 0.0f;
-          float ex = fmaf(b, fmaf(b, pc[9], pc[6]), pc[3]);
-          float ey = fmaf(b, fmaf(b, pc[10], pc[7]), pc[4]);
-          float ez = fmaf(b, fmaf(b, pc[11], pc[8]), pc[5]);
-          float h1 = pc[12], h2 = pc[13];
-#pragma unroll
-          for (int I = 0; I < NNUC; ++I) {
-            const float* c = nc + I * NUC_COEF;
-            const float a = aj[I];
-            const float t = fmaf(b, fmaf(b, fmaf(a, c[8], c[7]), fmaf(a, c[6], c[5])), fmaf(a, c[4], c[3]));
-            const float at = a * t;
-            ex = fmaf(at, c[0], ex);
-            ey = fmaf(at, c[1], ey);
-            ez = fmaf(at, c[2], ez);
-            h1 = fmaf(a, fmaf(a, c[10], c[9]), h1);
-            h2 = fmaf(a, fmaf(a, c[12], c[11]), h2);
-          }
-          const float hs = fmaf(b, h2, h1) * sfac;
-          gv[0][u] = fmaf(hs, dx, ex);
-          gv[1][u] = fmaf(hs, dy, ey);
-          gv[2][u] = fmaf(hs, dz, ez);
+      for (int v = 0; v < 8; ++v) {
+        const float4 p0 = ld_shared_f4(jt + v * 48);
+        const float4 p1 = ld_shared_f4(jt + v * 48 + 16);
+        float aj[NNUC];
+        aj[0] = p0.w;
+        if (NNUC > 1) aj[NNUC > 1 ? 1 : 0] = p1.w;
+        if (NNUC > 2) {
+          const float4 p2 = ld_shared_f4(jt + v * 48 + 32);
+          aj[NNUC > 2 ? 2 : 0] = p2.x;
+          if (NNUC > 3) aj[NNUC > 3 ? 3 : 0] = p2.y;
         }
-        const uint32_t off = sw64_offset(row, jh * 2 + grp);
+        // (hi_i - hi_j) is exact for nearby points; the low parts restore the rest
+        const float dx = (pc[0] - p0.x) + (xl - p1.x);
+        const float dy = (pc[1] - p0.y) + (yl - p1.y);
+        const float dz = (pc[2] - p0.z) + (zl - p1.z);
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float rinv = rsqrt_approx(fmaxf(r2, 1e-30f));
+        const float rr = r2 * rinv;
+        const float q = rcp_approx(1.0f + rr);
+        const float b = rr * q;
+        const float sfac = r2 > 0.0f ? q * q * rinv : 0.0f;
+        float ex = fmaf(b, fmaf(b, pc[9], pc[6]), pc[3]);
+        float ey = fmaf(b, fmaf(b, pc[10], pc[7]), pc[4]);
+        float ez = fmaf(b, fmaf(b, pc[11], pc[8]), pc[5]);
+        float h1 = pc[12], h2 = pc[13];
 #pragma unroll
-        for (int x = 0; x < 3; ++x) {
-          uint32_t w[4][PARTS];
-#pragma unroll
-          for (int h = 0; h < 4; ++h) split_pair<BF16>(gv[x][2 * h], gv[x][2 * h + 1], w[h], PARTS);
-#pragma unroll
-          for (int p = 0; p < PARTS; ++p)
-            st_shared_v4(sa + (x * PARTS + p) * A_TILE + off, w[0][p], w[1][p], w[2][p], w[3][p]);
+        for (int I = 0; I < NNUC; ++I) {
+          const float* cf = nc + I * NUC_COEF;
+          const float a = aj[I];
+          const float t = fmaf(b, fmaf(b, fmaf(a, cf[8], cf[7]), fmaf(a, cf[6], cf[5])), fmaf(a, cf[4], cf[3]));
+          const float at = a * t;
+          ex = fmaf(at, cf[0], ex);
+          ey = fmaf(at, cf[1], ey);
+          ez = fmaf(at, cf[2], ez);
+          h1 = fmaf(a, fmaf(a, cf[10], cf[9]), h1);
+          h2 = fmaf(a, fmaf(a, cf[12], cf[11]), h2);
         }
+        const float hs = fmaf(b, h2, h1) * sfac;
+        gv[0][v] = fmaf(hs, dx, ex);
+        gv[1][v] = fmaf(hs, dy, ey);
+        gv[2][v] = fmaf(hs, dz, ez);
+      }
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        uint32_t w[4][PARTS];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) split_pair<BF16>(gv[x][2 * h], gv[x][2 * h + 1], w[h]);
+#pragma unroll
+        for (int p = 0; p < PARTS; ++p) st_shared_v4(sa + p * A_TILE + row_off[x], w[0][p], w[1][p], w[2][p], w[3][p]);
       }
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&g_full[s]);
     }
-
-    // ------------------------------------------------------------------ epilogue (warps 2..5)
-    if (wgroup < 4) {
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(acc_bar, 0, abort_flag, args.err, DEV_ERR_TIMEOUT_VF));
+  } else {
+    // ------------------------------------------------------------------ range drains and epilogue
+    const int quarter = warp & 3;
+    const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
+    bool ok = true;
+    for (int r = 0; r < n_ranges && ok; ++r) {
+      const int b = r & 1, u = r >> 1;
+      ok = __all_sync(0xffffffffu, mbar_wait(&d_full[b], u & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF));
       __syncwarp();
+      if (!ok) break;
       tc_fence_after();
-      const int quarter = warp & 3;
-      const int erow = quarter * 32 + lane;
-      const int64_t eil = static_cast<int64_t>(m_tile) * VF_BM + erow;
-      const bool valid = ok && !*abort_flag && eil < args.n_i;
-      float* Vz = args.V + static_cast<int64_t>(split) * args.n_pair * 3 * args.gcp;
 #pragma unroll 1
-      for (int x = 0; x < 3; ++x) {
-#pragma unroll 1
-        for (int c0 = 0; c0 < VF_BN; c0 += 32) {
-          uint32_t r[32];
-          tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + x * VF_BN + c0, r);
-          tmem_wait_ld();
-          if (valid) {
+      for (int c0 = 0; c0 < D_COLS; c0 += 32) {
+        uint32_t d[32], sacc[32];
+        tmem_ld_32x32b_x32(tmem + lane_base + b * D_COLS + c0, d);
+        if (r > 0) tmem_ld_32x32b_x32(tmem + lane_base + S_COL + c0, sacc);
+        tmem_wait_ld();
+        if (r > 0) {
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-              const int pq = n_tile * VF_BN + c0 + k;
-              if (pq < args.n_pair) {
-                const float v = __uint_as_float(r[k]) * args.unscale_g;
-                Vz[(static_cast<int64_t>(pq) * 3 + x) * args.gcp + eil] = ldexpf(v, -__ldg(args.colexp + pq));
-              }
-            }
+          for (int k = 0; k < 32; ++k) d[k] = __float_as_uint(__uint_as_float(sacc[k]) + __uint_as_float(d[k]));
+        }
+        tmem_st_32x32b_x32(tmem + lane_base + S_COL + c0, d);
+      }
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&d_free[b]);
+    }
+    // store the running sum: row x*32 + pt of this tile -> V[split][pq][x][tile*32 + pt]
+    const int row = quarter * 32 + lane;
+    const int64_t il = static_cast<int64_t>(m_tile) * TP + (row & (TP - 1));
+    const bool valid = ok && !*abort_flag && row < 3 * TP && il < args.n_i && n_it > 0;
+    float* Vz = args.V + static_cast<int64_t>(split) * args.n_pair * 3 * args.gcp;
+    const int64_t col_off = static_cast<int64_t>(row >> 5) * args.gcp + il;
+    tc_fence_after();
+#pragma unroll 1
+    for (int c0 = 0; c0 < D_COLS; c0 += 32) {
+      uint32_t sacc[32];
+      tmem_ld_32x32b_x32(tmem + lane_base + S_COL + c0, sacc);
+      tmem_wait_ld();
+      if (valid) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const int pq = n_tile * VF_BN + c0 + k;
+          if (pq < args.n_pair) {
+            const float v = __uint_as_float(sacc[k]) * args.unscale_g;
+            Vz[static_cast<int64_t>(pq) * 3 * args.gcp + col_off] = ldexpf(v, -__ldg(args.colexp + pq));
           }
         }
       }
@@ -310,10 +400,10 @@ void launch_t(const CUtensorMap* tm, const VfieldArgs& a, int splits, cudaStream
   auto kern = vfield_tc_kernel<PARTS, NNUC>;
   constexpr int smem = VfCfg<PARTS>::SMEM;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  const int m_tiles = static_cast<int>((a.n_i + VF_BM - 1) / VF_BM);
+  const int m_tiles = static_cast<int>((a.n_i + TP - 1) / TP);
   const int n_tiles = (a.n_pair + VF_BN - 1) / VF_BN;
   dim3 grid(m_tiles, n_tiles, splits);
-  kern<<<grid, VF_THREADS, smem, st>>>(*tm, a);
+  kern<<<grid, THREADS, smem, st>>>(*tm, a);
 }
 
 }  // namespace

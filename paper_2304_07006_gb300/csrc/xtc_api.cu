@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -70,6 +71,8 @@ struct xtc_ctx {
   double ms[XTC_N_KERNELS] = {0};
   int64_t launches[XTC_N_KERNELS] = {0};
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  int vf_kd = 2;  // K-blocks per tensor-core accumulation range in steps (a)+(b)
+  int as_kd = 2;  // the same for step (d)
 };
 
 namespace {
@@ -293,6 +296,8 @@ int xtc_create(xtc_ctx** out, const xtc_params* p) {
     return XTC_ERR_CUDA;
   }
   ctx->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  if (const char* s = std::getenv("XTC_VF_KD")) ctx->vf_kd = std::max(1, std::atoi(s));
+  if (const char* s = std::getenv("XTC_AS_KD")) ctx->as_kd = std::max(1, std::atoi(s));
   if (!ensure(ctx->jp_dev, sizeof(JastrowParams)) || !ensure(ctx->err_dev, 16) || !ensure(ctx->flag_dev, 16)) {
     xtc_destroy(ctx);
     return XTC_ERR_OOM;
@@ -509,6 +514,7 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   a.js = 12;
   a.n_kb = static_cast<int>(pl.NGp / VF_BK);
   a.kb_per_split = (a.n_kb + pl.splits - 1) / pl.splits;
+  a.kd = std::min(ctx->vf_kd, pl.parts_b == 2 ? 4 : 2);
   int sg = 0;
   if (pl.parts_b == 2 && ctx->g_bound > 0.0) {
     sg = static_cast<int>(std::floor(std::log2(16384.0 / ctx->g_bound)));
@@ -632,7 +638,8 @@ extern "C" int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const dou
           launch_assemble_f64(ctx->L.as<double>(), ctx->R.as<double>(), NP, static_cast<int>(kdim),
                               ctx->M.as<double>(), st);
         else
-          launch_assemble_tc(&tm_L, &tm_R, NP, static_cast<int>(kdim), ctx->M.as<double>(), ctx->err_dev.as<int>(), st);
+          launch_assemble_tc(&tm_L, &tm_R, NP, static_cast<int>(kdim), std::min(ctx->as_kd, 3), ctx->M.as<double>(),
+                             ctx->err_dev.as<int>(), st);
       });
     }
   }

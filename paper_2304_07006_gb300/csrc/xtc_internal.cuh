@@ -29,7 +29,7 @@ constexpr int VF_BM = 128;      // outer points per tile (TMEM lanes)
 constexpr int VF_BN = 160;      // orbital pairs per tile; 3 accumulators of 160 columns
 constexpr int VF_BK = 32;       // inner points per pipeline stage (64-byte rows, SWIZZLE_64B)
 constexpr int AS_BM = 128;      // step (d) tile rows (pairs pq)
-constexpr int AS_BN = 256;      // step (d) tile columns (pairs rs)
+constexpr int AS_BN = 128;      // step (d) tile columns (pairs rs)
 constexpr int AS_BK = 32;
 constexpr int CHUNK_ALIGN = 128;
 
@@ -63,7 +63,7 @@ void launch_transpose_phi(const double* phi, int64_t n_grid, int64_t n_grid_pad,
 // Finite check: sets *flag non-zero if any of n values is NaN/Inf.
 void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t st);
 
-// Steps (a)+(b), tensor cores.  V[z][pq][x][gcp] (FP32) for outer points [i0, i0 + n_i).
+// Steps (a)+(b), tensor cores.  V[z][pq][x][il] (FP32, il = i - i0 < gcp) for outer points [i0, i0 + n_i).
 struct VfieldArgs {
   const double* grid;          // outer-point coordinates (global index space)
   const JastrowParams* jp;
@@ -74,6 +74,7 @@ struct VfieldArgs {
   int64_t gcp;                 // padded chunk length (row stride of V)
   int n_pair, n_nuc, js;
   int kb_per_split, n_kb;      // inner K-blocks per split slice, total K-blocks
+  int kd;                      // K-blocks per TMEM accumulation range (then added to the FP32 running sum)
   float g_scale;               // 2^sG folded into the gradient
   float unscale_g;             // 2^-sG
   int* err;
@@ -82,7 +83,7 @@ bool vfield_tc_supported(int n_nuc);
 void launch_vfield_tc(const CUtensorMap* tm_rho, const VfieldArgs& a, int parts, bool bf16, int splits,
                       cudaStream_t st);
 
-// Steps (a)+(b), FP64 SIMT twin.  V[pq][x][gcp] (FP64).  jtab64[n_grid_pad][3 + n_nuc].
+// Steps (a)+(b), FP64 SIMT twin.  V[pq][x][il] (FP64).  jtab64[n_grid_pad][3 + n_nuc].
 void launch_jtab64(const double* grid, int64_t n_grid, int64_t n_pad, const JastrowParams* jp, int n_nuc,
                    double* jtab, cudaStream_t st);
 void launch_vfield_f64_impl(const double* grid, const JastrowParams* jp, int n_nuc, const double* jtab64,
@@ -115,10 +116,10 @@ struct FieldsArgs {
   int out_parts;               // 0 = FP64 [4*gcp][pq]; 3 = bf16 x3 split [part][pq][4*gcp]
 };
 size_t fields_smem_bytes(int n_orb, int rank, int pts, bool f64);
-void launch_fields(const FieldsArgs& a, bool v_is_f64, cudaStream_t st);
+void launch_fields(const FieldsArgs& a, bool f64, cudaStream_t st);  // f64: FP64 V, compute and output
 
 // Step (d), tensor cores: M[pq][rs] += sum_k L[pq][k] R[rs][k] over k < kdim (FP64 accumulator).
-void launch_assemble_tc(const CUtensorMap* tm_L, const CUtensorMap* tm_R, int n_pair, int kdim, double* M,
+void launch_assemble_tc(const CUtensorMap* tm_L, const CUtensorMap* tm_R, int n_pair, int kdim, int kd, double* M,
                         int* err, cudaStream_t st);
 
 // Step (d), FP64 SIMT twin: M[pq][rs] += sum_k L[k][pq] R[k][rs].
