@@ -157,6 +157,26 @@ enum {
  * count; either pointer may be NULL.  n = array length (>= XTC_N_KERNELS). */
 XTC_API int xtc_get_timings(xtc_ctx* ctx, double* ms, int64_t* launches, int n);
 
+/* Allocation-free variant of xtc_vfield, for callers that must not allocate device memory (for
+ * instance code that runs inside a host framework owning every allocation, or a loop that may
+ * not call cudaMalloc).  The paper has no counterpart; it is a deployment convenience.
+ * Same computation and output as xtc_vfield (steps (a)+(b) in the context's precision), but:
+ *   - grid_xyz, weights, phi and V must be device pointers on the context's device (else
+ *     XTC_ERR_ARG); nothing is staged through host memory;
+ *   - all workspace comes from one fixed device array of XTC_NOALLOC_SCRATCH_MIB MiB built into
+ *     the library (every GPU that loads the library holds it until the process exits); problems
+ *     whose workspace does not fit (about n_grid * n_orb^2 * 4 bytes for the pair tables) are
+ *     rejected with XTC_ERR_ARG before any device work;
+ *   - the call makes no device allocation (no cudaMalloc, cudaFree or allocating library call).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call reuses the same array, which keeps the
+ * last call's contents: calls that overlap on the GPU race with each other, so serialise them.
+ * The call is synchronous with respect to the host, like the others. */
+#define XTC_NOALLOC_SCRATCH_MIB 64
+XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz,
+                               const double* weights, const double* phi, int64_t outer_begin, int64_t outer_end,
+                               double* V);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,212 @@
+// Allocation-free variant of steps (a)+(b) (xtc_vfield) for callers that cannot allocate device
+// memory: code running where the memory is owned by someone else (a host framework with its own
+// pool, a real-time loop that must not call cudaMalloc) can still evaluate the vector pair fields
+// V of small problems.  All workspace lives in one file-scope device array of fixed size; the
+// caller passes device buffers for the inputs and the output.
+//
+// The array's device address is obtained with cudaGetSymbolAddress on the first call on each
+// device (with that device current); that first call should therefore happen before any stream
+// capture.  Every call reuses the same array and it keeps the last call's contents, so calls
+// that overlap on the GPU (other streams, other threads, other contexts of this process on the
+// same device) race with each other and must be serialised by the caller.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "../../include/xtc.h"
+#include "xtc_internal.cuh"
+
+using namespace xtc;
+
+namespace {
+
+constexpr size_t kScratchBytes = static_cast<size_t>(XTC_NOALLOC_SCRATCH_MIB) << 20;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+void* g_scratch_addr[kMaxDevices] = {nullptr};
+
+__global__ void pair_table_kernel(int n_orb, int* pp, int* pq) {
+  const int p = blockIdx.x;
+  const int base = p * n_orb - p * (p - 1) / 2;
+  for (int q = p + threadIdx.x; q < n_orb; q += blockDim.x) {
+    pp[base + q - p] = p;
+    pq[base + q - p] = q;
+  }
+}
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Carves 256-byte aligned pieces out of the scratch array.
+struct Carver {
+  unsigned char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    T* p = reinterpret_cast<T*>(base + off);
+    off += (count * sizeof(T) + 255) / 256 * 256;
+    return p;
+  }
+};
+
+}  // namespace
+
+extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz,
+                                          const double* weights, const double* phi, int64_t outer_begin,
+                                          int64_t outer_end, double* V) {
+  CtxView cv{};
+  if (!xtc_internal_ctx_view(ctx, &cv)) return XTC_ERR_ARG;
+  if (!cv.jastrow_set) return xtc_internal_fail(ctx, XTC_ERR_STATE, "xtc_set_jastrow has not been called");
+  if (n_grid < 1 || n_orb < 1 || n_orb > 320 || outer_begin < 0 || outer_end < outer_begin || outer_end > n_grid)
+    return xtc_internal_fail(ctx, XTC_ERR_ARG, "noalloc: bad sizes or outer range");
+  const bool f64 = cv.precision == XTC_PREC_FP64;
+  if (!f64 && !vfield_tc_supported(cv.n_nuc))
+    return xtc_internal_fail(ctx, XTC_ERR_UNSUPPORTED, "noalloc: the tensor-core path supports 1..4 nuclei");
+  if (cudaSetDevice(cv.device) != cudaSuccess || cv.device < 0 || cv.device >= kMaxDevices)
+    return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: cudaSetDevice failed");
+  if (!on_device(grid_xyz) || !on_device(weights) || !on_device(phi) || !on_device(V))
+    return xtc_internal_fail(ctx, XTC_ERR_ARG, "noalloc: inputs and output must be device pointers");
+
+  // ---- the scratch array's device address, once per device
+  if (!g_scratch_addr[cv.device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: cudaGetSymbolAddress of the scratch array failed");
+    }
+    g_scratch_addr[cv.device] = p;
+  }
+
+  // ---- plan and carve (sizes checked before any device work)
+  const int N = n_orb, NP = N * (N + 1) / 2, n_nuc = cv.n_nuc;
+  const int64_t NGp = round_up(n_grid, 128);
+  const int64_t n_outer = outer_end - outer_begin;
+  const int parts = f64 ? 0 : (cv.precision == XTC_PREC_FP16X2 ? 2 : 3);
+  // bytes the layout below carves for a chunk of gc outer points (same order and rounding)
+  auto need = [&](int64_t gc) {
+    Carver c{nullptr};
+    c.take<int>(4);
+    c.take<int>(NP);
+    c.take<int>(NP);
+    if (f64) {
+      c.take<double>(static_cast<size_t>(NGp) * (3 + n_nuc));
+      c.take<double>(static_cast<size_t>(NGp) * NP);
+      c.take<double>(static_cast<size_t>(NP) * 3 * gc);
+    } else {
+      c.take<double>(static_cast<size_t>(N) * NGp);
+      c.take<float>(static_cast<size_t>(NGp) * 12);
+      c.take<uint16_t>(static_cast<size_t>(parts) * NP * NGp);
+      c.take<unsigned int>(NP);
+      c.take<int>(NP);
+      c.take<float>(static_cast<size_t>(NP) * 3 * gc);
+    }
+    return c.off;
+  };
+  int64_t gc = round_up(std::max<int64_t>(n_outer, 1), 128);
+  while (gc > 128 && need(gc) > kScratchBytes) gc -= 128;
+  if (need(gc) > kScratchBytes) {
+    char msg[200];
+    snprintf(msg, sizeof msg, "noalloc: problem needs %.1f MiB of workspace, the fixed scratch holds %d MiB",
+             need(128) / 1048576.0, XTC_NOALLOC_SCRATCH_MIB);
+    return xtc_internal_fail(ctx, XTC_ERR_ARG, msg);
+  }
+  Carver cz{static_cast<unsigned char*>(g_scratch_addr[cv.device])};
+  int* err = cz.take<int>(4);
+  int* pair_p = cz.take<int>(NP);
+  int* pair_q = cz.take<int>(NP);
+  cudaStream_t st = cv.stream;
+  if (n_outer == 0) return XTC_OK;
+
+  // ---- what must start at zero: the device error word (the column maxima are cleared by their launcher)
+  if (cudaMemsetAsync(err, 0, 16, st) != cudaSuccess)
+    return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: clearing the error word failed");
+  pair_table_kernel<<<N, 128, 0, st>>>(N, pair_p, pair_q);
+
+  CUtensorMap tm{};
+  double* jtab64 = nullptr;
+  double* rho64 = nullptr;
+  float* jtab = nullptr;
+  void* rho = nullptr;
+  int* colexp = nullptr;
+  void* Vbuf = nullptr;
+  if (f64) {
+    jtab64 = cz.take<double>(static_cast<size_t>(NGp) * (3 + n_nuc));
+    rho64 = cz.take<double>(static_cast<size_t>(NGp) * NP);
+    Vbuf = cz.take<double>(static_cast<size_t>(NP) * 3 * gc);
+    launch_jtab64(grid_xyz, n_grid, NGp, cv.jp_dev, n_nuc, jtab64, st);
+    launch_rho_f64(phi, weights, n_grid, NGp, N, pair_p, pair_q, rho64, st);
+  } else {
+    double* phiT = cz.take<double>(static_cast<size_t>(N) * NGp);
+    jtab = cz.take<float>(static_cast<size_t>(NGp) * 12);
+    rho = cz.take<uint16_t>(static_cast<size_t>(parts) * NP * NGp);
+    unsigned int* colmax = cz.take<unsigned int>(NP);
+    colexp = cz.take<int>(NP);
+    Vbuf = cz.take<float>(static_cast<size_t>(NP) * 3 * gc);
+    launch_transpose_phi(phi, n_grid, NGp, N, phiT, st);
+    launch_jtab(grid_xyz, n_grid, NGp, cv.jp_dev, n_nuc, 12, jtab, st);
+    launch_rho_split(phiT, weights, n_grid, NGp, N, parts, parts == 3, parts == 2, pair_p, pair_q, colmax, colexp,
+                     rho, st);
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(NGp), static_cast<cuuint64_t>(NP),
+                                static_cast<cuuint64_t>(parts)};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(NGp) * 2, static_cast<cuuint64_t>(NGp) * NP * 2};
+    const cuuint32_t box[3] = {VF_BK, VF_BN, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(cv.encode_tiled);
+    if (encode(&tm, parts == 3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, rho, dims,
+               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: cuTensorMapEncodeTiled failed");
+  }
+
+  // ---- chunks of outer points: steps (a)+(b), then V -> caller's buffer [k][x][pq] (FP64)
+  const int n_kb = static_cast<int>(NGp / VF_BK);
+  for (int64_t c0 = outer_begin; c0 < outer_end; c0 += gc) {
+    const int64_t n_i = std::min<int64_t>(gc, outer_end - c0);
+    if (f64) {
+      launch_vfield_f64_impl(grid_xyz, cv.jp_dev, n_nuc, jtab64, rho64, NGp, NP, c0, n_i, gc,
+                             static_cast<double*>(Vbuf), st);
+    } else {
+      VfieldArgs a{};
+      a.grid = grid_xyz;
+      a.jp = cv.jp_dev;
+      a.jtab = jtab;
+      a.colexp = colexp;
+      a.V = static_cast<float*>(Vbuf);
+      a.i0 = c0;
+      a.n_i = n_i;
+      a.gcp = gc;
+      a.n_pair = NP;
+      a.n_nuc = n_nuc;
+      a.js = 12;
+      a.n_kb = n_kb;
+      a.kb_per_split = n_kb;
+      a.kd = std::min(cv.vf_kd, parts == 2 ? 4 : 2);
+      int sg = 0;
+      if (parts == 2 && cv.g_bound > 0.0) sg = std::max(-30, std::min(30, static_cast<int>(std::floor(std::log2(16384.0 / cv.g_bound)))));
+      a.g_scale = std::ldexp(1.0f, sg);
+      a.unscale_g = std::ldexp(1.0f, -sg);
+      a.err = err;
+      launch_vfield_tc(&tm, a, parts, parts == 3, 1, st);
+    }
+    launch_vfield_export(Vbuf, f64, 1, NP, n_i, gc, V + (c0 - outer_begin) * 3 * NP, st);
+  }
+  if (cudaGetLastError() != cudaSuccess) return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: kernel launch failed");
+  int h = 0;
+  if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: stream synchronisation failed");
+  if (h) return xtc_internal_fail(ctx, XTC_ERR_TIMEOUT, "noalloc: a device-side wait timed out");
+  return XTC_OK;
+}

@@ -743,3 +743,21 @@ extern "C" int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double*
   finish_timers(ctx);
   return XTC_OK;
 }
+
+// ====================================================================== internal accessors
+bool xtc_internal_ctx_view(const xtc_ctx* ctx, xtc::CtxView* v) {
+  if (!ctx || !v) return false;
+  v->device = ctx->prm.device;
+  v->stream = ctx->st;
+  v->precision = ctx->prm.precision;
+  v->n_sm = ctx->n_sm;
+  v->jastrow_set = ctx->jastrow_set;
+  v->n_nuc = ctx->jp.n_nuc;
+  v->g_bound = ctx->g_bound;
+  v->vf_kd = ctx->vf_kd;
+  v->jp_dev = ctx->jp_dev.as<JastrowParams>();
+  v->encode_tiled = reinterpret_cast<void*>(ctx->encode);
+  return true;
+}
+
+int xtc_internal_fail(xtc_ctx* ctx, int code, const char* msg) { return fail(ctx, code, "%s", msg); }

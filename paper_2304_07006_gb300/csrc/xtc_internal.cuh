@@ -135,4 +135,24 @@ void launch_onebody(const double* M, const double* gamma, int n_orb, int n_pair,
 void launch_vfield_export(const void* V, bool f64, int splits, int n_pair, int64_t n_i, int64_t gcp,
                           double* out, cudaStream_t st);
 
+// Read-only view of a context for entry points implemented outside xtc_api.cu.
+struct CtxView {
+  int device;
+  cudaStream_t stream;
+  int precision;
+  int n_sm;
+  bool jastrow_set;
+  int n_nuc;
+  double g_bound;
+  int vf_kd;
+  const JastrowParams* jp_dev;
+  void* encode_tiled;  // PFN_cuTensorMapEncodeTiled_v12000
+};
+
 }  // namespace xtc
+
+struct xtc_ctx;
+// Fills *v from ctx; false for a null context.
+bool xtc_internal_ctx_view(const xtc_ctx* ctx, xtc::CtxView* v);
+// Records a failure message on ctx and returns code.
+int xtc_internal_fail(xtc_ctx* ctx, int code, const char* msg);

@@ -20,7 +20,7 @@ KERNEL_NAMES = ("prep", "vfield", "fields", "assemble", "final")
 
 EXPORTED = ("xtc_default_params", "xtc_create", "xtc_destroy", "xtc_strerror", "xtc_last_error_detail",
             "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b", "xtc_jastrow_grad", "xtc_vfield",
-            "xtc_get_timings")
+            "xtc_get_timings", "xtc_vfield_noalloc")
 
 
 class XtcParams(ctypes.Structure):
@@ -59,9 +59,10 @@ def load(path: str = LIB_PATH):
     lib.xtc_build_1b2b.argtypes = [P, I64, I, D, D, D, D, D, D, D, D]
     lib.xtc_jastrow_grad.argtypes = [P, I64, D, D, D]
     lib.xtc_vfield.argtypes = [P, I64, I, D, D, D, I64, I64, D]
+    lib.xtc_vfield_noalloc.argtypes = [P, I64, I, D, D, D, I64, I64, D]
     lib.xtc_get_timings.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), I]
     for name in ("xtc_create", "xtc_destroy", "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b",
-                 "xtc_jastrow_grad", "xtc_vfield", "xtc_get_timings"):
+                 "xtc_jastrow_grad", "xtc_vfield", "xtc_get_timings", "xtc_vfield_noalloc"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -174,6 +175,14 @@ class Context:
             out = np.empty((outer_end - outer_begin, 3, n_pair))
         self._check(self._lib.xtc_vfield(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
                                          int(outer_begin), int(outer_end), _ptr(out)))
+        return out
+
+    def vfield_noalloc(self, grid, weights, phi, outer_begin, outer_end, out):
+        """xtc_vfield without device allocation: every argument must be a CUDA tensor (float64);
+        workspace comes from the library's fixed scratch array (small problems only)."""
+        n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+        self._check(self._lib.xtc_vfield_noalloc(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
+                                                 int(outer_begin), int(outer_end), _ptr(out)))
         return out
 
     def timings(self):
