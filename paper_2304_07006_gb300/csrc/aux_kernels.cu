@@ -28,23 +28,23 @@ __global__ void jtab_kernel(const double* __restrict__ grid, int64_t n_grid, int
     y = grid[3 * j + 1];
     z = grid[3 * j + 2];
   }
-  // layout (12 floats): x_hi y_hi z_hi a_0 | x_lo y_lo z_lo a_1 | a_2 a_3 0 0, with x = x_hi + x_lo so that
-  // differences of nearby points keep FP64-level accuracy in FP32 arithmetic
-  float* o = jtab + j * js;
-  for (int k = 0; k < js; ++k) o[k] = 0.0f;
+  // Points j = 2k and 2k+1 share a 24-float record, each field stored as an adjacent (even, odd)
+  // pair so that one 16-byte load yields two packed fields:
+  //   x_hi y_hi | z_hi x_lo | y_lo z_lo | a_0 a_1 | a_2 a_3 | 0 0      (each entry = [j even, j odd])
+  // with x = x_hi + x_lo (differences of nearby points keep FP64-level accuracy in FP32) and
+  // a_I = |r_j - R_I| / (1 + |r_j - R_I|).
+  (void)js;
+  float* o = jtab + (j >> 1) * 24 + (j & 1);
   const float xh = static_cast<float>(x), yh = static_cast<float>(y), zh = static_cast<float>(z);
-  o[0] = xh;
-  o[1] = yh;
-  o[2] = zh;
-  o[4] = static_cast<float>(x - static_cast<double>(xh));
-  o[5] = static_cast<float>(y - static_cast<double>(yh));
-  o[6] = static_cast<float>(z - static_cast<double>(zh));
-  const int slot[4] = {3, 7, 8, 9};
+  float f[12] = {xh, yh, zh, static_cast<float>(x - static_cast<double>(xh)),
+                 static_cast<float>(y - static_cast<double>(yh)), static_cast<float>(z - static_cast<double>(zh)),
+                 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   for (int I = 0; I < n_nuc && I < 4; ++I) {
     const double dx = x - jp->nuc[I][0], dy = y - jp->nuc[I][1], dz = z - jp->nuc[I][2];
     const double d = sqrt(dx * dx + dy * dy + dz * dz);
-    o[slot[I]] = static_cast<float>(d / (1.0 + d));
+    f[6 + I] = static_cast<float>(d / (1.0 + d));
   }
+  for (int k = 0; k < 12; ++k) o[2 * k] = f[k];
 }
 
 __global__ void transpose_phi_kernel(const double* __restrict__ phi, int64_t n_grid, int64_t n_pad, int N,

@@ -108,6 +108,40 @@ __device__ __forceinline__ float4 ld_shared_f4(uint32_t addr) {
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "r"(addr));
   return r;
 }
+// Two FP32 values packed in a 64-bit register, processed by Blackwell's paired FP32 instructions.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void up2(f32x2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ void ld_shared_2x64(uint32_t addr, f32x2& a, f32x2& b) {
+  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
+}
+
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_u32(dst)),
@@ -269,6 +303,17 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t row_off[3];
 #pragma unroll
     for (int x = 0; x < 3; ++x) row_off[x] = sw64_offset(x * TP + pt, c);
+    // the same constants duplicated in both halves of a packed pair (paired FP32 path, <= 2 nuclei)
+    f32x2 PC[NNUC <= 2 ? PT_COEF : 1], NC[NNUC <= 2 ? NNUC * NUC_COEF : 1], XL = 0, YL = 0, ZL = 0;
+    if constexpr (NNUC <= 2) {
+#pragma unroll
+      for (int k = 0; k < PT_COEF; ++k) PC[k] = pk2(pc[k], pc[k]);
+#pragma unroll
+      for (int k = 0; k < NNUC * NUC_COEF; ++k) NC[k] = pk2(nc[k], nc[k]);
+      XL = pk2(xl, xl);
+      YL = pk2(yl, yl);
+      ZL = pk2(zl, zl);
+    }
 
     for (int it = group; it < n_it; it += 2) {
       const int s = it % STAGES, n = it / STAGES;
@@ -276,50 +321,97 @@ __global__ void __launch_bounds__(THREADS, 1)
       got = got && mbar_wait(&tma_full[s], n & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF);
       if (!__all_sync(0xffffffffu, got)) break;
       const uint32_t sa = smem_base + s * Cfg::STAGE_BYTES;
-      const uint32_t jt = sa + Cfg::A_BYTES + Cfg::B_BYTES + c * 8 * 48;
+      const uint32_t jt = sa + Cfg::A_BYTES + Cfg::B_BYTES + c * 4 * 96;
       float gv[3][8];
 #pragma unroll
-      for (int v = 0; v < 8; ++v) {
-        const float4 p0 = ld_shared_f4(jt + v * 48);
-        const float4 p1 = ld_shared_f4(jt + v * 48 + 16);
-        float aj[NNUC];
-        aj[0] = p0.w;
-        if (NNUC > 1) aj[NNUC > 1 ? 1 : 0] = p1.w;
-        if (NNUC > 2) {
-          const float4 p2 = ld_shared_f4(jt + v * 48 + 32);
-          aj[NNUC > 2 ? 2 : 0] = p2.x;
-          if (NNUC > 3) aj[NNUC > 3 ? 3 : 0] = p2.y;
-        }
-        // (hi_i - hi_j) is exact for nearby points; the low parts restore the rest
-        const float dx = (pc[0] - p0.x) + (xl - p1.x);
-        const float dy = (pc[1] - p0.y) + (yl - p1.y);
-        const float dz = (pc[2] - p0.z) + (zl - p1.z);
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const float rinv = rsqrt_approx(fmaxf(r2, 1e-30f));
-        const float rr = r2 * rinv;
-        const float q = rcp_approx(1.0f + rr);
-        const float b = rr * q;
-        const float sfac = r2 > 0.0f ? q * q * rinv : 0.0f;
-        float ex = fmaf(b, fmaf(b, pc[9], pc[6]), pc[3]);
-        float ey = fmaf(b, fmaf(b, pc[10], pc[7]), pc[4]);
-        float ez = fmaf(b, fmaf(b, pc[11], pc[8]), pc[5]);
-        float h1 = pc[12], h2 = pc[13];
+      for (int v2 = 0; v2 < 4; ++v2) {
+        // inner points j = 8c + 2 v2 (even) and + 1 (odd), one 96-byte record
+        const uint32_t rec = jt + v2 * 96;
+        if constexpr (NNUC <= 2) {
+          f32x2 xh, yh, zh, xlo, ylo, zlo, a0, a1;
+          ld_shared_2x64(rec, xh, yh);
+          ld_shared_2x64(rec + 16, zh, xlo);
+          ld_shared_2x64(rec + 32, ylo, zlo);
+          ld_shared_2x64(rec + 48, a0, a1);
+          const f32x2 dx = add2(sub2(PC[0], xh), sub2(XL, xlo));
+          const f32x2 dy = add2(sub2(PC[1], yh), sub2(YL, ylo));
+          const f32x2 dz = add2(sub2(PC[2], zh), sub2(ZL, zlo));
+          const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+          float r2a, r2b;
+          up2(r2, r2a, r2b);
+          // unit vector of r1 - r2 taken as zero below 1e-14 bohr (coincident points)
+          const float ria = r2a > 1e-28f ? rsqrt_approx(r2a) : 0.0f;
+          const float rib = r2b > 1e-28f ? rsqrt_approx(r2b) : 0.0f;
+          const f32x2 rinv = pk2(ria, rib);
+          const f32x2 rr = mul2(r2, rinv);
+          float ra, rb;
+          up2(rr, ra, rb);
+          const f32x2 q = pk2(rcp_approx(1.0f + ra), rcp_approx(1.0f + rb));
+          const f32x2 b = mul2(rr, q);
+          const f32x2 sfac = mul2(mul2(q, q), rinv);
+          f32x2 ex = fma2(b, fma2(b, PC[9], PC[6]), PC[3]);
+          f32x2 ey = fma2(b, fma2(b, PC[10], PC[7]), PC[4]);
+          f32x2 ez = fma2(b, fma2(b, PC[11], PC[8]), PC[5]);
+          f32x2 h1 = PC[12], h2 = PC[13];
 #pragma unroll
-        for (int I = 0; I < NNUC; ++I) {
-          const float* cf = nc + I * NUC_COEF;
-          const float a = aj[I];
-          const float t = fmaf(b, fmaf(b, fmaf(a, cf[8], cf[7]), fmaf(a, cf[6], cf[5])), fmaf(a, cf[4], cf[3]));
-          const float at = a * t;
-          ex = fmaf(at, cf[0], ex);
-          ey = fmaf(at, cf[1], ey);
-          ez = fmaf(at, cf[2], ez);
-          h1 = fmaf(a, fmaf(a, cf[10], cf[9]), h1);
-          h2 = fmaf(a, fmaf(a, cf[12], cf[11]), h2);
+          for (int I = 0; I < NNUC; ++I) {
+            const f32x2* cf = NC + I * NUC_COEF;
+            const f32x2 a = I == 0 ? a0 : a1;
+            const f32x2 t = fma2(b, fma2(b, fma2(a, cf[8], cf[7]), fma2(a, cf[6], cf[5])), fma2(a, cf[4], cf[3]));
+            const f32x2 at = mul2(a, t);
+            ex = fma2(at, cf[0], ex);
+            ey = fma2(at, cf[1], ey);
+            ez = fma2(at, cf[2], ez);
+            h1 = fma2(a, fma2(a, cf[10], cf[9]), h1);
+            h2 = fma2(a, fma2(a, cf[12], cf[11]), h2);
+          }
+          const f32x2 hs = mul2(fma2(b, h2, h1), sfac);
+          up2(fma2(hs, dx, ex), gv[0][2 * v2], gv[0][2 * v2 + 1]);
+          up2(fma2(hs, dy, ey), gv[1][2 * v2], gv[1][2 * v2 + 1]);
+          up2(fma2(hs, dz, ez), gv[2][2 * v2], gv[2][2 * v2 + 1]);
+        } else {
+          const float4 q0 = ld_shared_f4(rec), q1 = ld_shared_f4(rec + 16), q2 = ld_shared_f4(rec + 32);
+          const float4 q3 = ld_shared_f4(rec + 48), q4 = ld_shared_f4(rec + 64);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float xh = h ? q0.y : q0.x, yh = h ? q0.w : q0.z, zh = h ? q1.y : q1.x;
+            const float xlo = h ? q1.w : q1.z, ylo = h ? q2.y : q2.x, zlo = h ? q2.w : q2.z;
+            float aj[NNUC];
+            aj[0] = h ? q3.y : q3.x;
+            aj[NNUC > 1 ? 1 : 0] = h ? q3.w : q3.z;
+            if (NNUC > 2) aj[NNUC > 2 ? 2 : 0] = h ? q4.y : q4.x;
+            if (NNUC > 3) aj[NNUC > 3 ? 3 : 0] = h ? q4.w : q4.z;
+            const float dx = (pc[0] - xh) + (xl - xlo);
+            const float dy = (pc[1] - yh) + (yl - ylo);
+            const float dz = (pc[2] - zh) + (zl - zlo);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float rinv = r2 > 1e-28f ? rsqrt_approx(r2) : 0.0f;
+            const float rr = r2 * rinv;
+            const float q = rcp_approx(1.0f + rr);
+            const float b = rr * q;
+            const float sfac = q * q * rinv;
+            float ex = fmaf(b, fmaf(b, pc[9], pc[6]), pc[3]);
+            float ey = fmaf(b, fmaf(b, pc[10], pc[7]), pc[4]);
+            float ez = fmaf(b, fmaf(b, pc[11], pc[8]), pc[5]);
+            float h1 = pc[12], h2 = pc[13];
+#pragma unroll
+            for (int I = 0; I < NNUC; ++I) {
+              const float* cf = nc + I * NUC_COEF;
+              const float a = aj[I];
+              const float t = fmaf(b, fmaf(b, fmaf(a, cf[8], cf[7]), fmaf(a, cf[6], cf[5])), fmaf(a, cf[4], cf[3]));
+              const float at = a * t;
+              ex = fmaf(at, cf[0], ex);
+              ey = fmaf(at, cf[1], ey);
+              ez = fmaf(at, cf[2], ez);
+              h1 = fmaf(a, fmaf(a, cf[10], cf[9]), h1);
+              h2 = fmaf(a, fmaf(a, cf[12], cf[11]), h2);
+            }
+            const float hs = fmaf(b, h2, h1) * sfac;
+            gv[0][2 * v2 + h] = fmaf(hs, dx, ex);
+            gv[1][2 * v2 + h] = fmaf(hs, dy, ey);
+            gv[2][2 * v2 + h] = fmaf(hs, dz, ez);
+          }
         }
-        const float hs = fmaf(b, h2, h1) * sfac;
-        gv[0][v] = fmaf(hs, dx, ex);
-        gv[1][v] = fmaf(hs, dy, ey);
-        gv[2][v] = fmaf(hs, dz, ez);
       }
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
