@@ -165,6 +165,7 @@ def main():
     import torch
     import synth
     from paper_2304_07006_gb300 import Context
+    from paper_2304_07006_gb300.xtc import KERNEL_NAMES
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -198,8 +199,8 @@ def main():
     torch.cuda.synchronize(dev)
     clocks = Clocks(local)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kern_ms = np.zeros(5)
-    kern_n = np.zeros(5, dtype=np.int64)
+    kern_ms = np.zeros(len(KERNEL_NAMES))
+    kern_n = np.zeros(len(KERNEL_NAMES), dtype=np.int64)
     ev0.record(stream)
     for _ in range(args.steps):
         run()
@@ -220,9 +221,8 @@ def main():
     value = world * F["total"] / (ms_step * 1e-3) / 1e12
 
     # roofline of the dominant kernel: steps (a)+(b), per-launch algorithmic flops / mean launch time
-    names = ["prep", "vfield", "fields", "assemble", "final"]
-    per_kernel = {names[k]: {"ms_per_step": kern_ms[k] / args.steps, "launches_per_step": int(kern_n[k] // args.steps)}
-                  for k in range(5)}
+    per_kernel = {name: {"ms_per_step": kern_ms[k] / args.steps, "launches_per_step": int(kern_n[k] // args.steps)}
+                  for k, name in enumerate(KERNEL_NAMES)}
     n_vf = kern_n[1] / args.steps
     vf_ms = kern_ms[1] / max(kern_n[1], 1)
     vf_flops_launch = F["b"] / n_vf

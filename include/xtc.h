@@ -147,11 +147,12 @@ XTC_API int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* gr
 /* Kernel timers of the last build (requires params.timing != 0).  Kernel ids: */
 enum {
   XTC_K_PREP = 0,     /* per-grid-point tables, orbital transposition, pair products rho (split) */
-  XTC_K_VFIELD = 1,   /* steps (a)+(b) */
+  XTC_K_VFIELD = 1,   /* step (b) GEMM (tensor-core precisions); steps (a)+(b) (XTC_PREC_FP64) */
   XTC_K_FIELDS = 2,   /* step (c) */
   XTC_K_ASSEMBLE = 3, /* step (d): Delta U accumulation */
   XTC_K_FINAL = 4,    /* Delta U unpacking, Delta h, e0 */
-  XTC_N_KERNELS = 5
+  XTC_K_GRAD = 5,     /* step (a) gradient table of the tensor-core precisions */
+  XTC_N_KERNELS = 6
 };
 /* ms[k] = summed device milliseconds of kernel class k over the last build, launches[k] = launch
  * count; either pointer may be NULL.  n = array length (>= XTC_N_KERNELS). */
@@ -165,8 +166,9 @@ XTC_API int xtc_get_timings(xtc_ctx* ctx, double* ms, int64_t* launches, int n);
  *     XTC_ERR_ARG); nothing is staged through host memory;
  *   - all workspace comes from one fixed device array of XTC_NOALLOC_SCRATCH_MIB MiB built into
  *     the library (every GPU that loads the library holds it until the process exits); problems
- *     whose workspace does not fit (about n_grid * n_orb^2 * 4 bytes for the pair tables) are
- *     rejected with XTC_ERR_ARG before any device work;
+ *     whose workspace does not fit (with P = 2 parts for fp16x2, 3 for bf16x3, 4 for FP64:
+ *     about n_grid * P * (n_orb^2 + 800) bytes for the pair and gradient tables) are rejected
+ *     with XTC_ERR_ARG before any device work;
  *   - the call makes no device allocation (no cudaMalloc, cudaFree or allocating library call).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture.  Every call reuses the same array, which keeps the

@@ -1,0 +1,238 @@
+// Step (a) for the tensor-core path: the Jastrow gradient G_x(i, j) = d/dx_i u(r_i, r_j) of every
+// (outer point i, inner point j) pair of a chunk (section "Decomposition of two-body correction",
+// the factor that multiplies rho in V), split into fp16 (2 parts) or bf16 (3 parts) and stored
+// K-major as the A operand of the step (b) GEMM:
+//     G[part][x * gcp + il][j]     (il = i - i0, j contiguous, NGp columns, 64-byte swizzle tiles).
+// Computing G once per chunk, instead of inside every orbital-pair tile of the GEMM, removes the
+// gradient from the GEMM's critical path; the table costs one HBM write and is then read through L2
+// by the GEMM's tiles.
+//
+// One warp owns a unit of 32 outer points (one per lane, its per-point coefficients in registers)
+// and a run of inner-point blocks of 32.  For each block it evaluates the gradient in FP32 (two
+// inner points per packed FP32 instruction for up to two Jastrow centres), splits it, writes the
+// 3 x PARTS tiles of 32 rows x 64 bytes into shared memory in the 64-byte swizzle (conflict-free
+// 16-byte stores) and one lane stores them with TMA.  The gradient is taken with the pair formula
+// of jastrow_coef.cuh: per-point coefficients times polynomials in b = r12 / (1 + r12) and
+// a_jI = |r_j - R_I| / (1 + |r_j - R_I|).
+#include "jastrow_coef.cuh"
+#include "ptx_sm100.cuh"
+#include "simt_pack.cuh"
+#include "xtc_internal.cuh"
+
+namespace xtc {
+namespace {
+
+constexpr int GF_WARPS = 8;
+constexpr int GF_THREADS = GF_WARPS * 32;
+constexpr int GF_TILE = 32 * 64;   // one part tile: 32 rows of 64 bytes
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, uint32_t src, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)),
+               "r"(src), "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Waits until the shared memory of every committed bulk store has been read.
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// Waits until every committed bulk store has completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+template <int PARTS, int NNUC>
+__global__ void __launch_bounds__(GF_THREADS)
+    gfield_kernel(const __grid_constant__ CUtensorMap tm_g, const GfieldArgs args) {
+  constexpr bool BF16 = PARTS == 3;
+  constexpr int WARP_BYTES = 3 * PARTS * GF_TILE;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t unit = static_cast<int64_t>(blockIdx.x) * GF_WARPS + warp;
+  if (unit >= static_cast<int64_t>(args.n_tiles) * args.n_seg) return;  // whole warp; no block barrier below
+  const int tile = static_cast<int>(unit / args.n_seg), seg = static_cast<int>(unit % args.n_seg);
+  const int kb0 = seg * args.kb_per_seg, kb1 = min(args.n_kb, kb0 + args.kb_per_seg);
+  const uint32_t buf = smem_u32(smem) + warp * WARP_BYTES;
+
+  // coefficients of this lane's outer point (rows past the chunk repeat its last point)
+  const int64_t il = static_cast<int64_t>(tile) * 32 + lane;
+  const int64_t ig = args.i0 + (il < args.n_i ? il : args.n_i - 1);
+  float pc[PT_COEF];
+  float nc[NNUC * NUC_COEF];
+  const double gx = args.grid[3 * ig], gy = args.grid[3 * ig + 1], gz = args.grid[3 * ig + 2];
+  point_coefs_fixed<float, NNUC>(*args.jp, gx, gy, gz, static_cast<double>(args.g_scale), pc, nc);
+  // low parts of the outer coordinates (the pair difference is taken in hi/lo FP32)
+  const float xl = static_cast<float>(gx - static_cast<double>(pc[0]));
+  const float yl = static_cast<float>(gy - static_cast<double>(pc[1]));
+  const float zl = static_cast<float>(gz - static_cast<double>(pc[2]));
+  // the same constants duplicated in both halves of a packed pair (paired FP32 path, <= 2 nuclei)
+  f32x2 PC[NNUC <= 2 ? PT_COEF : 1], NC[NNUC <= 2 ? NNUC * NUC_COEF : 1], XL = 0, YL = 0, ZL = 0;
+  if constexpr (NNUC <= 2) {
+#pragma unroll
+    for (int k = 0; k < PT_COEF; ++k) PC[k] = pk2(pc[k], pc[k]);
+#pragma unroll
+    for (int k = 0; k < NNUC * NUC_COEF; ++k) NC[k] = pk2(nc[k], nc[k]);
+    XL = pk2(xl, xl);
+    YL = pk2(yl, yl);
+    ZL = pk2(zl, zl);
+  }
+  const int row0 = tile * 32;
+
+  for (int kb = kb0; kb < kb1; ++kb) {
+    // 16 records of two inner points each (the pair-interleaved table written by launch_jtab)
+    const float* blk = args.jtab + static_cast<int64_t>(kb) * VF_BK * 12;
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+      float gv[3][8];
+#pragma unroll
+      for (int v2 = 0; v2 < 4; ++v2) {
+        const float* rec = blk + (c * 4 + v2) * 24;  // inner points 8c + 2 v2 and + 1
+        if constexpr (NNUC <= 2) {
+          f32x2 xh, yh, zh, xlo, ylo, zlo, a0, a1;
+          ldg_2x64(rec, xh, yh);
+          ldg_2x64(rec + 4, zh, xlo);
+          ldg_2x64(rec + 8, ylo, zlo);
+          ldg_2x64(rec + 12, a0, a1);
+          const f32x2 dx = add2(sub2(PC[0], xh), sub2(XL, xlo));
+          const f32x2 dy = add2(sub2(PC[1], yh), sub2(YL, ylo));
+          const f32x2 dz = add2(sub2(PC[2], zh), sub2(ZL, zlo));
+          const f32x2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+          float r2a, r2b;
+          up2(r2, r2a, r2b);
+          // unit vector of r1 - r2 taken as zero below 1e-14 bohr (coincident points)
+          const float ria = r2a > 1e-28f ? rsqrt_approx(r2a) : 0.0f;
+          const float rib = r2b > 1e-28f ? rsqrt_approx(r2b) : 0.0f;
+          const f32x2 rinv = pk2(ria, rib);
+          const f32x2 rr = mul2(r2, rinv);
+          float ra, rb;
+          up2(rr, ra, rb);
+          const f32x2 q = pk2(rcp_approx(1.0f + ra), rcp_approx(1.0f + rb));
+          const f32x2 b = mul2(rr, q);
+          const f32x2 sfac = mul2(mul2(q, q), rinv);
+          f32x2 ex = fma2(b, fma2(b, PC[9], PC[6]), PC[3]);
+          f32x2 ey = fma2(b, fma2(b, PC[10], PC[7]), PC[4]);
+          f32x2 ez = fma2(b, fma2(b, PC[11], PC[8]), PC[5]);
+          f32x2 h1 = PC[12], h2 = PC[13];
+#pragma unroll
+          for (int I = 0; I < NNUC; ++I) {
+            const f32x2* cf = NC + I * NUC_COEF;
+            const f32x2 a = I == 0 ? a0 : a1;
+            const f32x2 t = fma2(b, fma2(b, fma2(a, cf[8], cf[7]), fma2(a, cf[6], cf[5])), fma2(a, cf[4], cf[3]));
+            const f32x2 at = mul2(a, t);
+            ex = fma2(at, cf[0], ex);
+            ey = fma2(at, cf[1], ey);
+            ez = fma2(at, cf[2], ez);
+            h1 = fma2(a, fma2(a, cf[10], cf[9]), h1);
+            h2 = fma2(a, fma2(a, cf[12], cf[11]), h2);
+          }
+          const f32x2 hs = mul2(fma2(b, h2, h1), sfac);
+          up2(fma2(hs, dx, ex), gv[0][2 * v2], gv[0][2 * v2 + 1]);
+          up2(fma2(hs, dy, ey), gv[1][2 * v2], gv[1][2 * v2 + 1]);
+          up2(fma2(hs, dz, ez), gv[2][2 * v2], gv[2][2 * v2 + 1]);
+        } else {
+          const float4 q0 = ldg_f4(rec), q1 = ldg_f4(rec + 4), q2 = ldg_f4(rec + 8);
+          const float4 q3 = ldg_f4(rec + 12), q4 = ldg_f4(rec + 16);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float xh = h ? q0.y : q0.x, yh = h ? q0.w : q0.z, zh = h ? q1.y : q1.x;
+            const float xlo = h ? q1.w : q1.z, ylo = h ? q2.y : q2.x, zlo = h ? q2.w : q2.z;
+            float aj[NNUC];
+            aj[0] = h ? q3.y : q3.x;
+            aj[NNUC > 1 ? 1 : 0] = h ? q3.w : q3.z;
+            if (NNUC > 2) aj[NNUC > 2 ? 2 : 0] = h ? q4.y : q4.x;
+            if (NNUC > 3) aj[NNUC > 3 ? 3 : 0] = h ? q4.w : q4.z;
+            const float dx = (pc[0] - xh) + (xl - xlo);
+            const float dy = (pc[1] - yh) + (yl - ylo);
+            const float dz = (pc[2] - zh) + (zl - zlo);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float rinv = r2 > 1e-28f ? rsqrt_approx(r2) : 0.0f;
+            const float rr = r2 * rinv;
+            const float q = rcp_approx(1.0f + rr);
+            const float b = rr * q;
+            const float sfac = q * q * rinv;
+            float ex = fmaf(b, fmaf(b, pc[9], pc[6]), pc[3]);
+            float ey = fmaf(b, fmaf(b, pc[10], pc[7]), pc[4]);
+            float ez = fmaf(b, fmaf(b, pc[11], pc[8]), pc[5]);
+            float h1 = pc[12], h2 = pc[13];
+#pragma unroll
+            for (int I = 0; I < NNUC; ++I) {
+              const float* cf = nc + I * NUC_COEF;
+              const float a = aj[I];
+              const float t = fmaf(b, fmaf(b, fmaf(a, cf[8], cf[7]), fmaf(a, cf[6], cf[5])), fmaf(a, cf[4], cf[3]));
+              const float at = a * t;
+              ex = fmaf(at, cf[0], ex);
+              ey = fmaf(at, cf[1], ey);
+              ez = fmaf(at, cf[2], ez);
+              h1 = fmaf(a, fmaf(a, cf[10], cf[9]), h1);
+              h2 = fmaf(a, fmaf(a, cf[12], cf[11]), h2);
+            }
+            const float hs = fmaf(b, h2, h1) * sfac;
+            gv[0][2 * v2 + h] = fmaf(hs, dx, ex);
+            gv[1][2 * v2 + h] = fmaf(hs, dy, ey);
+            gv[2][2 * v2 + h] = fmaf(hs, dz, ez);
+          }
+        }
+      }
+      // the previous block's tiles must have been read by its TMA stores before they are overwritten
+      if (c == 0 && kb > kb0) {
+        if (lane == 0) bulk_wait_read_all();
+        __syncwarp();
+      }
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        uint32_t w[4][PARTS];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) split_pair<BF16>(gv[x][2 * h], gv[x][2 * h + 1], w[h]);
+#pragma unroll
+        for (int p = 0; p < PARTS; ++p)
+          st_shared_v4(buf + (x * PARTS + p) * GF_TILE + sw64_offset(lane, c), w[0][p], w[1][p], w[2][p], w[3][p]);
+      }
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int p = 0; p < PARTS; ++p)
+          tma_store_3d(&tm_g, buf + (x * PARTS + p) * GF_TILE, kb * VF_BK,
+                       static_cast<int>(x * args.gcp) + row0, p);
+      bulk_commit();
+    }
+  }
+  if (lane == 0) bulk_wait_all();
+  __syncwarp();
+}
+
+template <int PARTS, int NNUC>
+void launch_t(const CUtensorMap* tm, const GfieldArgs& a, cudaStream_t st) {
+  auto kern = gfield_kernel<PARTS, NNUC>;
+  constexpr int smem = GF_WARPS * 3 * PARTS * GF_TILE + 1024;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int64_t units = static_cast<int64_t>(a.n_tiles) * a.n_seg;
+  const unsigned blocks = static_cast<unsigned>((units + GF_WARPS - 1) / GF_WARPS);
+  kern<<<blocks, GF_THREADS, smem, st>>>(*tm, a);
+}
+
+}  // namespace
+
+void launch_gfield(const CUtensorMap* tm_g_store, const GfieldArgs& a, int parts, cudaStream_t st) {
+  if (a.n_tiles <= 0 || a.n_seg <= 0) return;
+  if (parts == 2) {
+    switch (a.n_nuc) {
+      case 1: launch_t<2, 1>(tm_g_store, a, st); break;
+      case 2: launch_t<2, 2>(tm_g_store, a, st); break;
+      case 3: launch_t<2, 3>(tm_g_store, a, st); break;
+      default: launch_t<2, 4>(tm_g_store, a, st); break;
+    }
+  } else {
+    switch (a.n_nuc) {
+      case 1: launch_t<3, 1>(tm_g_store, a, st); break;
+      case 2: launch_t<3, 2>(tm_g_store, a, st); break;
+      case 3: launch_t<3, 3>(tm_g_store, a, st); break;
+      default: launch_t<3, 4>(tm_g_store, a, st); break;
+    }
+  }
+}
+
+}  // namespace xtc

@@ -111,6 +111,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
       c.take<unsigned int>(NP);
       c.take<int>(NP);
       c.take<float>(static_cast<size_t>(NP) * 3 * gc);
+      c.take<uint16_t>(static_cast<size_t>(parts) * 3 * gc * NGp);
     }
     return c.off;
   };
@@ -134,7 +135,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: clearing the error word failed");
   pair_table_kernel<<<N, 128, 0, st>>>(N, pair_p, pair_q);
 
-  CUtensorMap tm{};
+  CUtensorMap tm{}, tm_gs{}, tm_gl{};
   double* jtab64 = nullptr;
   double* rho64 = nullptr;
   float* jtab = nullptr;
@@ -154,19 +155,25 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     unsigned int* colmax = cz.take<unsigned int>(NP);
     colexp = cz.take<int>(NP);
     Vbuf = cz.take<float>(static_cast<size_t>(NP) * 3 * gc);
+    void* G = cz.take<uint16_t>(static_cast<size_t>(parts) * 3 * gc * NGp);
     launch_transpose_phi(phi, n_grid, NGp, N, phiT, st);
     launch_jtab(grid_xyz, n_grid, NGp, cv.jp_dev, n_nuc, 12, jtab, st);
     launch_rho_split(phiT, weights, n_grid, NGp, N, parts, parts == 3, parts == 2, pair_p, pair_q, colmax, colexp,
                      rho, st);
-    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(NGp), static_cast<cuuint64_t>(NP),
-                                static_cast<cuuint64_t>(parts)};
-    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(NGp) * 2, static_cast<cuuint64_t>(NGp) * NP * 2};
-    const cuuint32_t box[3] = {VF_BK, VF_BN, 1};
-    const cuuint32_t es[3] = {1, 1, 1};
+    // rho^T [part][pq][j] (box 32 x 160) and the gradient table [part][x * gc + il][j] (boxes 32 x 32
+    // for the step (a) stores and 32 x 128 for the step (b) loads)
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(cv.encode_tiled);
-    if (encode(&tm, parts == 3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, rho, dims,
-               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    auto map = [&](CUtensorMap* m, void* base, int64_t rows, uint32_t box_rows) {
+      const cuuint64_t dims[3] = {static_cast<cuuint64_t>(NGp), static_cast<cuuint64_t>(rows),
+                                  static_cast<cuuint64_t>(parts)};
+      const cuuint64_t strides[2] = {static_cast<cuuint64_t>(NGp) * 2, static_cast<cuuint64_t>(NGp) * rows * 2};
+      const cuuint32_t box[3] = {VF_BK, box_rows, 1};
+      const cuuint32_t es[3] = {1, 1, 1};
+      return encode(m, parts == 3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims,
+                    strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!map(&tm, rho, NP, VF_BN) || !map(&tm_gs, G, 3 * gc, 32) || !map(&tm_gl, G, 3 * gc, VF_BM))
       return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: cuTensorMapEncodeTiled failed");
   }
 
@@ -178,27 +185,38 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
       launch_vfield_f64_impl(grid_xyz, cv.jp_dev, n_nuc, jtab64, rho64, NGp, NP, c0, n_i, gc,
                              static_cast<double*>(Vbuf), st);
     } else {
+      int sg = 0;
+      if (parts == 2 && cv.g_bound > 0.0)
+        sg = std::max(-30, std::min(30, static_cast<int>(std::floor(std::log2(16384.0 / cv.g_bound)))));
+      const int mt_per_x = static_cast<int>((n_i + VF_BM - 1) / VF_BM);
+      GfieldArgs g{};
+      g.grid = grid_xyz;
+      g.jp = cv.jp_dev;
+      g.jtab = jtab;
+      g.i0 = c0;
+      g.n_i = n_i;
+      g.gcp = gc;
+      g.n_tiles = mt_per_x * (VF_BM / 32);
+      g.n_kb = n_kb;
+      g.kb_per_seg = 32;
+      g.n_seg = (n_kb + g.kb_per_seg - 1) / g.kb_per_seg;
+      g.n_nuc = n_nuc;
+      g.g_scale = std::ldexp(1.0f, sg);
+      launch_gfield(&tm_gs, g, parts, st);
       VfieldArgs a{};
-      a.grid = grid_xyz;
-      a.jp = cv.jp_dev;
-      a.jtab = jtab;
       a.colexp = colexp;
       a.V = static_cast<float*>(Vbuf);
-      a.i0 = c0;
       a.n_i = n_i;
       a.gcp = gc;
+      a.mt_per_x = mt_per_x;
+      a.n_tiles = (NP + VF_BN - 1) / VF_BN;
       a.n_pair = NP;
-      a.n_nuc = n_nuc;
-      a.js = 12;
       a.n_kb = n_kb;
       a.kb_per_split = n_kb;
       a.kd = std::min(cv.vf_kd, parts == 2 ? 4 : 2);
-      int sg = 0;
-      if (parts == 2 && cv.g_bound > 0.0) sg = std::max(-30, std::min(30, static_cast<int>(std::floor(std::log2(16384.0 / cv.g_bound)))));
-      a.g_scale = std::ldexp(1.0f, sg);
       a.unscale_g = std::ldexp(1.0f, -sg);
       a.err = err;
-      launch_vfield_tc(&tm, a, parts, parts == 3, 1, st);
+      launch_vfield_tc(&tm_gl, &tm, a, parts, 1, st);
     }
     launch_vfield_export(Vbuf, f64, 1, NP, n_i, gc, V + (c0 - outer_begin) * 3 * NP, st);
   }

@@ -60,7 +60,7 @@ struct xtc_ctx {
   // device workspace
   DBuf jp_dev, err_dev, flag_dev;
   DBuf grid, w, phi, gamma, phiT, pair_p, pair_q;
-  DBuf jtab, jtab64, rho, colmax, colexp;
+  DBuf jtab, jtab64, rho, colmax, colexp, G;
   DBuf V, L, R, M, evec, lam, dU_tmp, dh_tmp, e0_tmp, vout, r1, r2;
   // prepared state key (pair tables)
   int pair_n = -1;
@@ -71,7 +71,7 @@ struct xtc_ctx {
   double ms[XTC_N_KERNELS] = {0};
   int64_t launches[XTC_N_KERNELS] = {0};
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  int vf_kd = 2;  // K-blocks per tensor-core accumulation range in steps (a)+(b)
+  int vf_kd = 2;  // K-blocks per tensor-core accumulation range in step (b)
   int as_kd = 2;  // the same for step (d)
 };
 
@@ -210,12 +210,14 @@ struct Plan {
   bool f64;
 };
 
-int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t n_outer, bool f64) {
-  // memory budget for V and the step (d) operands, then the chunk that fills whole waves best
+int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t NGp, int parts, int64_t n_outer, bool f64) {
+  // memory budgets: 6 GB for V and the step (d) operands, 16 GB for the step (a) gradient table;
+  // then the chunk that fills whole waves of the step (b) GEMM best
   const double vbytes = f64 ? 3.0 * 8 : 3.0 * 4;
   const double lrbytes = f64 ? 2 * 4 * 8.0 : 2 * 3 * 4 * 2.0;
   const double per_point = NP * (vbytes + lrbytes);
   int64_t cap = static_cast<int64_t>(6.0e9 / per_point);
+  if (!f64) cap = std::min<int64_t>(cap, static_cast<int64_t>(16.0e9 / (3.0 * parts * 2.0 * NGp)));
   cap = std::max<int64_t>(128, std::min<int64_t>(cap, 32768) / 128 * 128);
   const int64_t need = round_up(n_outer, 128);
   if (need <= cap) return need;
@@ -223,7 +225,7 @@ int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t n_outer, bool f64) {
   int64_t best = cap;
   double best_eff = 0.0;
   for (int64_t tiles = cap / 128; tiles >= std::max<int64_t>(1, cap / 256); --tiles) {
-    const double ctas = static_cast<double>(tiles) * nt;
+    const double ctas = 3.0 * tiles * nt;
     const double eff = ctas / (std::ceil(ctas / c->n_sm) * c->n_sm);
     if (eff > best_eff + 1e-9) {
       best_eff = eff;
@@ -419,7 +421,8 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
   pl.oe = ctx->outer_end < 0 ? n_grid : std::min<int64_t>(ctx->outer_end, n_grid);
   if (pl.oe < pl.ob) pl.oe = pl.ob;
   const int64_t n_outer = pl.oe - pl.ob;
-  pl.gc = ctx->prm.grid_chunk > 0 ? ctx->prm.grid_chunk : auto_chunk(ctx, pl.NP, std::max<int64_t>(n_outer, 1), f64);
+  pl.gc = ctx->prm.grid_chunk > 0 ? ctx->prm.grid_chunk
+                                   : auto_chunk(ctx, pl.NP, pl.NGp, pl.parts_b, std::max<int64_t>(n_outer, 1), f64);
   const int n_kb = static_cast<int>(pl.NGp / VF_BK);
   pl.splits = ctx->prm.split_k > 0 ? std::min(ctx->prm.split_k, n_kb) : 1;
   if (f64) pl.splits = 1;
@@ -487,11 +490,29 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
   });
   const size_t vbytes = static_cast<size_t>(pl.splits) * pl.NP * 3 * pl.gc * (f64 ? 8 : 4);
   if (!ensure(ctx->V, vbytes)) return fail(ctx, XTC_ERR_OOM, "V chunk (%.2f GB)", vbytes / 1e9);
+  if (!f64) {
+    const size_t gbytes = 2ull * pl.parts_b * 3 * pl.gc * pl.NGp;
+    if (!ensure(ctx->G, gbytes)) return fail(ctx, XTC_ERR_OOM, "gradient table (%.2f GB)", gbytes / 1e9);
+  }
   return XTC_OK;
 }
 
+// Tensor maps of the step (b) operands: rho^T (box 32 x 160) and the gradient table, as stored by
+// step (a) (box 32 x 32) and as loaded by the GEMM (box 32 x 128).
+struct VfMaps {
+  CUtensorMap rho, g_store, g_load;
+};
+int make_vfield_maps(xtc_ctx* ctx, const Plan& pl, VfMaps& m) {
+  if (pl.f64) return XTC_OK;
+  const bool bf = pl.parts_b == 3;
+  int rc;
+  if ((rc = make_tmap_3d(ctx, &m.rho, ctx->rho.p, bf, pl.NGp, pl.NP, pl.parts_b, VF_BK, VF_BN))) return rc;
+  if ((rc = make_tmap_3d(ctx, &m.g_store, ctx->G.p, bf, pl.NGp, 3 * pl.gc, pl.parts_b, VF_BK, 32))) return rc;
+  return make_tmap_3d(ctx, &m.g_load, ctx->G.p, bf, pl.NGp, 3 * pl.gc, pl.parts_b, VF_BK, VF_BM);
+}
+
 // Steps (a)+(b) for outer points [i0, i0 + n_i) into ctx->V.
-int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, int64_t n_i, const CUtensorMap* tm) {
+int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, int64_t n_i, const VfMaps& maps) {
   cudaStream_t st = ctx->st;
   if (pl.f64) {
     timed(ctx, XTC_K_VFIELD, 1, [&] {
@@ -500,31 +521,44 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
     });
     return XTC_OK;
   }
-  VfieldArgs a{};
-  a.grid = d_grid;
-  a.jp = ctx->jp_dev.as<JastrowParams>();
-  a.jtab = ctx->jtab.as<float>();
-  a.colexp = ctx->colexp.as<int>();
-  a.V = ctx->V.as<float>();
-  a.i0 = i0;
-  a.n_i = n_i;
-  a.gcp = pl.gc;
-  a.n_pair = pl.NP;
-  a.n_nuc = ctx->jp.n_nuc;
-  a.js = 12;
-  a.n_kb = static_cast<int>(pl.NGp / VF_BK);
-  a.kb_per_split = (a.n_kb + pl.splits - 1) / pl.splits;
-  a.kd = std::min(ctx->vf_kd, pl.parts_b == 2 ? 4 : 2);
+  const int n_kb = static_cast<int>(pl.NGp / VF_BK);
+  const int mt_per_x = static_cast<int>((n_i + VF_BM - 1) / VF_BM);
+  // fp16 gradient scale 2^sG keeps |G| below 16384 (bf16 needs none)
   int sg = 0;
   if (pl.parts_b == 2 && ctx->g_bound > 0.0) {
     sg = static_cast<int>(std::floor(std::log2(16384.0 / ctx->g_bound)));
     sg = std::max(-30, std::min(30, sg));
   }
-  a.g_scale = std::ldexp(1.0f, sg);
+  GfieldArgs g{};
+  g.grid = d_grid;
+  g.jp = ctx->jp_dev.as<JastrowParams>();
+  g.jtab = ctx->jtab.as<float>();
+  g.i0 = i0;
+  g.n_i = n_i;
+  g.gcp = pl.gc;
+  g.n_tiles = mt_per_x * (VF_BM / 32);
+  g.n_kb = n_kb;
+  g.kb_per_seg = 32;
+  g.n_seg = (n_kb + g.kb_per_seg - 1) / g.kb_per_seg;
+  g.n_nuc = ctx->jp.n_nuc;
+  g.g_scale = std::ldexp(1.0f, sg);
+  timed(ctx, XTC_K_GRAD, 1, [&] { launch_gfield(&maps.g_store, g, pl.parts_b, st); });
+
+  VfieldArgs a{};
+  a.colexp = ctx->colexp.as<int>();
+  a.V = ctx->V.as<float>();
+  a.n_i = n_i;
+  a.gcp = pl.gc;
+  a.mt_per_x = mt_per_x;
+  a.n_tiles = (pl.NP + VF_BN - 1) / VF_BN;
+  a.n_pair = pl.NP;
+  a.n_kb = n_kb;
+  a.kb_per_split = (a.n_kb + pl.splits - 1) / pl.splits;
+  a.kd = std::min(ctx->vf_kd, pl.parts_b == 2 ? 4 : 2);
   a.unscale_g = std::ldexp(1.0f, -sg);
   a.err = ctx->err_dev.as<int>();
   const int splits = (a.n_kb + a.kb_per_split - 1) / a.kb_per_split;  // every slice non-empty
-  timed(ctx, XTC_K_VFIELD, 1, [&] { launch_vfield_tc(tm, a, pl.parts_b, pl.parts_b == 3, splits, st); });
+  timed(ctx, XTC_K_VFIELD, 1, [&] { launch_vfield_tc(&maps.g_load, &maps.rho, a, pl.parts_b, splits, st); });
   return XTC_OK;
 }
 
@@ -590,9 +624,10 @@ extern "C" int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const dou
   const size_t lr_bytes = pl.f64 ? 8ull * kdim * NP : 2ull * 3 * kdim * NP;
   if (!ensure(ctx->L, lr_bytes) || !ensure(ctx->R, lr_bytes))
     return fail(ctx, XTC_ERR_OOM, "step (d) operands (%.2f GB)", 2.0 * lr_bytes / 1e9);
-  CUtensorMap tm_rho{}, tm_L{}, tm_R{};
+  VfMaps maps{};
+  CUtensorMap tm_L{}, tm_R{};
+  if ((rc = make_vfield_maps(ctx, pl, maps))) return rc;
   if (!pl.f64) {
-    if ((rc = make_tmap_3d(ctx, &tm_rho, ctx->rho.p, pl.parts_b == 3, pl.NGp, NP, pl.parts_b, VF_BK, VF_BN))) return rc;
     if ((rc = make_tmap_3d(ctx, &tm_L, ctx->L.p, true, kdim, NP, 3, AS_BK, AS_BM))) return rc;
     if ((rc = make_tmap_3d(ctx, &tm_R, ctx->R.p, true, kdim, NP, 3, AS_BK, AS_BN))) return rc;
   }
@@ -608,7 +643,7 @@ extern "C" int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const dou
   // ---- chunk loop
   for (int64_t c0 = pl.ob; c0 < pl.oe; c0 += pl.gc) {
     const int64_t n_i = std::min<int64_t>(pl.gc, pl.oe - c0);
-    if ((rc = run_vfield(ctx, pl, d_grid, c0, n_i, &tm_rho))) return rc;
+    if ((rc = run_vfield(ctx, pl, d_grid, c0, n_i, maps))) return rc;
     for (int gi = 0; gi < groups; ++gi) {
       const int k0 = gi * RANK_GROUP;
       const int rg = std::max(0, std::min(RANK_GROUP, rank - k0));
@@ -718,16 +753,15 @@ extern "C" int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double*
   ctx->outer_end = oe;
   if (rc) return rc;
   cudaStream_t st = ctx->st;
-  CUtensorMap tm_rho{};
-  if (!pl.f64 && (rc = make_tmap_3d(ctx, &tm_rho, ctx->rho.p, pl.parts_b == 3, pl.NGp, pl.NP, pl.parts_b, VF_BK, VF_BN)))
-    return rc;
+  VfMaps maps{};
+  if ((rc = make_vfield_maps(ctx, pl, maps))) return rc;
   const bool out_dev = is_device_ptr(V);
   const size_t per_point = static_cast<size_t>(3) * pl.NP;
   const int64_t n_out = pl.oe - pl.ob;
   DBuf tmp;
   for (int64_t c0 = pl.ob; c0 < pl.oe; c0 += pl.gc) {
     const int64_t n_i = std::min<int64_t>(pl.gc, pl.oe - c0);
-    if ((rc = run_vfield(ctx, pl, d_grid, c0, n_i, &tm_rho))) return rc;
+    if ((rc = run_vfield(ctx, pl, d_grid, c0, n_i, maps))) return rc;
     double* dst = V + (c0 - pl.ob) * per_point;
     if (!out_dev) {
       if (!ensure(ctx->vout, n_i * per_point * 8)) return fail(ctx, XTC_ERR_OOM, "V staging");

@@ -63,25 +63,40 @@ void launch_transpose_phi(const double* phi, int64_t n_grid, int64_t n_grid_pad,
 // Finite check: sets *flag non-zero if any of n values is NaN/Inf.
 void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t st);
 
-// Steps (a)+(b), tensor cores.  V[z][pq][x][il] (FP32, il = i - i0 < gcp) for outer points [i0, i0 + n_i).
-struct VfieldArgs {
+// Step (a), tensor-core path: the split Jastrow gradient G[part][x * gcp + il][j] (fp16 or bf16,
+// K-major, 64-byte swizzled TMA tiles of 32 rows) for the outer points [i0, i0 + n_i) and every
+// padded inner point.  Rows up to n_tiles * 32 are written (past n_i they repeat the last point).
+struct GfieldArgs {
   const double* grid;          // outer-point coordinates (global index space)
   const JastrowParams* jp;
-  const float* jtab;           // [n_grid_pad][js]
+  const float* jtab;           // pair-interleaved inner-point table (launch_jtab, 12 floats per point)
+  int64_t i0, n_i;             // outer range of this chunk
+  int64_t gcp;                 // padded chunk length (rows per component)
+  int n_tiles;                 // 32-row outer tiles to write (multiple of 4)
+  int n_kb, kb_per_seg, n_seg; // inner K-blocks (32 points), K-blocks per warp unit, units along K
+  int n_nuc;
+  float g_scale;               // 2^sG folded into the gradient
+};
+void launch_gfield(const CUtensorMap* tm_g_store, const GfieldArgs& a, int parts, cudaStream_t st);
+
+// Step (b), tensor cores.  V[z][pq][x][il] (FP32, il = i - i0 < gcp) for the outer points of the
+// chunk, from the G table (tm_g: box 32 x 128) and the split rho^T (tm_rho: box 32 x 160).
+struct VfieldArgs {
   const int* colexp;           // per-pair exponent of the rho scaling (0 when unscaled)
   float* V;                    // output base
-  int64_t i0, n_i;             // outer range of this chunk
-  int64_t gcp;                 // padded chunk length (row stride of V)
-  int n_pair, n_nuc, js;
+  int64_t n_i;                 // outer points of this chunk
+  int64_t gcp;                 // padded chunk length (row stride of V and of G per component)
+  int mt_per_x;                // 128-row tiles per component: ceil(n_i / 128)
+  int n_tiles;                 // 160-column tiles: ceil(n_pair / 160)
+  int n_pair;
   int kb_per_split, n_kb;      // inner K-blocks per split slice, total K-blocks
   int kd;                      // K-blocks per TMEM accumulation range (then added to the FP32 running sum)
-  float g_scale;               // 2^sG folded into the gradient
   float unscale_g;             // 2^-sG
   int* err;
 };
 bool vfield_tc_supported(int n_nuc);
-void launch_vfield_tc(const CUtensorMap* tm_rho, const VfieldArgs& a, int parts, bool bf16, int splits,
-                      cudaStream_t st);
+void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int parts,
+                      int splits, cudaStream_t st);
 
 // Steps (a)+(b), FP64 SIMT twin.  V[pq][x][il] (FP64).  jtab64[n_grid_pad][3 + n_nuc].
 void launch_jtab64(const double* grid, int64_t n_grid, int64_t n_pad, const JastrowParams* jp, int n_nuc,
