@@ -160,7 +160,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     launch_jtab(grid_xyz, n_grid, NGp, cv.jp_dev, n_nuc, 12, jtab, st);
     launch_rho_split(phiT, weights, n_grid, NGp, N, parts, parts == 3, parts == 2, pair_p, pair_q, colmax, colexp,
                      rho, st);
-    // rho^T [part][pq][j] (box 32 x 160) and the gradient table [part][x * gc + il][j] (boxes 32 x 32
+    // rho^T [part][pq][j] (box 32 x vf_bn) and the gradient table [part][x * gc + il][j] (boxes 32 x 32
     // for the step (a) stores and 32 x 128 for the step (b) loads)
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(cv.encode_tiled);
     auto map = [&](CUtensorMap* m, void* base, int64_t rows, uint32_t box_rows) {
@@ -173,7 +173,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
-    if (!map(&tm, rho, NP, VF_BN) || !map(&tm_gs, G, 3 * gc, 32) || !map(&tm_gl, G, 3 * gc, VF_BM))
+    if (!map(&tm, rho, NP, vf_bn(parts)) || !map(&tm_gs, G, 3 * gc, 32) || !map(&tm_gl, G, 3 * gc, VF_BM))
       return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: cuTensorMapEncodeTiled failed");
   }
 
@@ -209,7 +209,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
       a.n_i = n_i;
       a.gcp = gc;
       a.mt_per_x = mt_per_x;
-      a.n_tiles = (NP + VF_BN - 1) / VF_BN;
+      a.n_tiles = (NP + vf_bn(parts) - 1) / vf_bn(parts);
       a.n_pair = NP;
       a.n_kb = n_kb;
       a.kb_per_split = n_kb;

@@ -5,13 +5,15 @@
 // as a split-precision GEMM over the inner points j: A = G (written by gfield.cu, rows x*gcp + il),
 // B = rho^T (written by the rho split kernel), both split into fp16 (2 parts) or bf16 (3 parts).
 //
-// CTA tile: 128 A rows (128 outer points of one component) x 160 orbital pairs, 32 inner points
-// per pipeline stage (64-byte rows, 64-byte swizzle, K-major), all operands loaded by TMA.
+// CTA tile: 128 A rows (128 outer points of one component) x BN orbital pairs (192 with 2 parts,
+// 160 with 3), 32 inner points per pipeline stage (64-byte rows, 64-byte swizzle, K-major), all
+// operands loaded by TMA.
 //   * warp 0 (one lane): TMA loads of the A and B tiles of every part;
 //   * warp 1 (one lane): tcgen05.mma for every split product into one of two TMEM accumulators;
-//   * warps 2..9: every `kd` stages they add the finished accumulator into an FP32 running sum
-//     kept in TMEM (tcgen05.ld / st) while the MMA fills the other accumulator, and at the end
-//     store the sum, unscaled, as V[pq][x][i].
+//   * warps 2..9: every `kd` stages they load the finished accumulator (tcgen05.ld) and add it into
+//     an FP32 running sum held in their registers (two warps per TMEM lane quarter, BN/2 columns
+//     each) while the MMA fills the other accumulator; at the end they store the sum, unscaled,
+//     as V[pq][x][i].
 // The tensor-core accumulator truncates toward zero at each MMA, which biases a long inner sum.
 // Each range is short (default two stages), its MMAs issue the small cross products of all its
 // stages first so that only the hi x hi products meet a large accumulator, and the ranges are
@@ -24,25 +26,26 @@
 namespace xtc {
 namespace {
 
-constexpr int DRAIN_WARPS = 8;       // two per TMEM lane quarter, 80 columns each
+constexpr int DRAIN_WARPS = 8;       // two per TMEM lane quarter, BN/2 columns each
 constexpr int THREADS = (2 + DRAIN_WARPS) * 32;
 constexpr int A_TILE = VF_BM * 64;   // bytes per part tile (128 rows of 64 B)
-constexpr int B_TILE = VF_BN * 64;   // bytes per part tile (160 rows of 64 B)
-constexpr int D_COLS = VF_BN;        // accumulator columns
-constexpr uint32_t S_COL = 2 * D_COLS;  // running-sum columns start
-constexpr int HALF_COLS = D_COLS / 2;
 constexpr int GM = 8;                // row tiles per CTA group (L2 reuse)
 
 template <int PARTS>
 struct VfCfg {
-  static constexpr int STAGES = PARTS == 2 ? 6 : 4;
+  static constexpr int BN = vf_bn(PARTS);
+  static constexpr int B_TILE = BN * 64;   // bytes per part tile (BN rows of 64 B)
+  static constexpr int HC = BN / 2;        // running-sum columns per drain thread
   static constexpr int NPROD = PARTS == 2 ? 3 : 6;
+  static constexpr int STAGES = PARTS == 2 ? 5 : 4;
   static constexpr int A_BYTES = PARTS * A_TILE;
   static constexpr int B_BYTES = PARTS * B_TILE;
   static constexpr int STAGE_BYTES = ((A_BYTES + B_BYTES + 1023) / 1024) * 1024;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 };
 static_assert(VfCfg<2>::SMEM <= 232448 && VfCfg<3>::SMEM <= 232448, "shared memory per CTA");
+static_assert(2 * vf_bn(2) <= 512 && 2 * vf_bn(3) <= 512, "two accumulators in 512 TMEM columns");
+static_assert(vf_bn(2) % 32 == 0 && vf_bn(3) % 32 == 0, "drain chunks of 16 columns, two at a time");
 
 // (A part, B part) of each split product in issue order: the small cross products first and
 // hi x hi last, so that the truncations of the early MMAs act on a small accumulator.
@@ -71,23 +74,13 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr)
       : "memory");
 }
-__device__ __forceinline__ void tmem_st_x16(uint32_t taddr, const uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
-      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
-      : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
 template <int PARTS>
 __global__ void __launch_bounds__(THREADS, 1)
     vfield_tc_kernel(const __grid_constant__ CUtensorMap tm_g, const __grid_constant__ CUtensorMap tm_rho,
                      const VfieldArgs args) {
   using Cfg = VfCfg<PARTS>;
   constexpr bool BF16 = PARTS == 3;
-  constexpr int STAGES = Cfg::STAGES;
+  constexpr int BN = Cfg::BN, HC = Cfg::HC, STAGES = Cfg::STAGES;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -151,11 +144,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int kb = kb0; kb < kb1; ++kb) {
         const int it = kb - kb0, s = it % STAGES, n = it / STAGES;
         if (n > 0 && !mbar_wait(&empty[s], (n - 1) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)) break;
-        mbar_arrive_expect_tx(&tma_full[s], PARTS * (A_TILE + B_TILE));
+        mbar_arrive_expect_tx(&tma_full[s], PARTS * (A_TILE + Cfg::B_TILE));
         uint8_t* st = smem + s * Cfg::STAGE_BYTES;
         for (int p = 0; p < PARTS; ++p) {
           tma_load_3d(st + p * A_TILE, &tm_g, &tma_full[s], kb * VF_BK, row0, p);
-          tma_load_3d(st + Cfg::A_BYTES + p * B_TILE, &tm_rho, &tma_full[s], kb * VF_BK, n_tile * VF_BN, p);
+          tma_load_3d(st + Cfg::A_BYTES + p * Cfg::B_TILE, &tm_rho, &tma_full[s], kb * VF_BK, n_tile * BN, p);
         }
         issued_end = kb + 1;
       }
@@ -170,37 +163,43 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------------------------------------------------------- MMA issuer
-      // A range of kd stages goes into one TMEM accumulator: first every cross product of all its
-      // stages (the accumulator is still small), then every hi x hi product.
-      constexpr uint32_t idesc = idesc_f16(VF_BM, VF_BN, BF16);
+      // A range of kd stages goes into one TMEM accumulator: first the cross products of each
+      // stage as it lands (the accumulator is still small), then the hi x hi product of every
+      // stage, after which that stage is released.
+      constexpr uint32_t idesc = idesc_f16(VF_BM, BN, BF16);
       bool alive = true;
       for (int r = 0; r < n_ranges && alive; ++r) {
         const int it0 = r * kd, it1 = min(n_it, it0 + kd);
         const int b = r & 1, u = r >> 1;
+        const uint32_t d_tmem = tmem + b * BN;
         if (u >= 1 && !mbar_wait(&d_free[b], (u - 1) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)) break;
-        for (int it = it0; it < it1 && alive; ++it)
-          alive = mbar_wait(&tma_full[it % STAGES], (it / STAGES) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF);
-        if (!alive) break;
-        tc_fence_after();
-        for (int pass = 0; pass < 2; ++pass) {
-          for (int it = it0; it < it1; ++it) {
-            const uint32_t sa = smem_base + (it % STAGES) * Cfg::STAGE_BYTES;
-            const uint32_t sb = sa + Cfg::A_BYTES;
+        for (int it = it0; it < it1; ++it) {
+          if (!(alive = mbar_wait(&tma_full[it % STAGES], (it / STAGES) & 1, abort_flag, args.err,
+                                  DEV_ERR_TIMEOUT_VF)))
+            break;
+          tc_fence_after();
+          const uint32_t sa = smem_base + (it % STAGES) * Cfg::STAGE_BYTES;
+          const uint32_t sb = sa + Cfg::A_BYTES;
 #pragma unroll
-            for (int p = 0; p < Cfg::NPROD; ++p) {
-              if ((p == Cfg::NPROD - 1) != (pass == 1)) continue;
-              int pa, pb;
-              prod_parts<PARTS>(p, pa, pb);
+          for (int p = 0; p < Cfg::NPROD - 1; ++p) {
+            int pa, pb;
+            prod_parts<PARTS>(p, pa, pb);
 #pragma unroll
-              for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t ad = sdesc_kmajor_sw64(sa + pa * A_TILE + ks * 32);
-                const uint64_t bd = sdesc_kmajor_sw64(sb + pb * B_TILE + ks * 32);
-                tc_mma_f16(tmem + b * D_COLS, ad, bd, idesc, (it == it0 && p == 0 && ks == 0) ? 0u : 1u);
-              }
-            }
+            for (int ks = 0; ks < 2; ++ks)
+              tc_mma_f16(d_tmem, sdesc_kmajor_sw64(sa + pa * A_TILE + ks * 32),
+                         sdesc_kmajor_sw64(sb + pb * Cfg::B_TILE + ks * 32), idesc,
+                         (it == it0 && p == 0 && ks == 0) ? 0u : 1u);
           }
         }
-        for (int it = it0; it < it1; ++it) tc_commit(&empty[it % STAGES]);
+        if (!alive) break;
+        for (int it = it0; it < it1; ++it) {
+          const uint32_t sa = smem_base + (it % STAGES) * Cfg::STAGE_BYTES;
+          const uint32_t sb = sa + Cfg::A_BYTES;
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks)
+            tc_mma_f16(d_tmem, sdesc_kmajor_sw64(sa + ks * 32), sdesc_kmajor_sw64(sb + ks * 32), idesc, 1u);
+          tc_commit(&empty[it % STAGES]);
+        }
         tc_commit(&d_full[b]);
       }
       // every MMA issued by this thread has completed once fin_bar fires
@@ -211,9 +210,12 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {
     // ------------------------------------------------------------------ range drains and epilogue
     const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31 (hardware rule)
-    const int half = (warp - 2) >> 2;           // columns 80*half .. +79
+    const int half = (warp - 2) >> 2;           // columns HC*half .. +HC-1
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
-    const uint32_t c_base = static_cast<uint32_t>(half * HALF_COLS);
+    const uint32_t c_base = static_cast<uint32_t>(half * HC);
+    float S[HC];
+#pragma unroll
+    for (int k = 0; k < HC; ++k) S[k] = 0.0f;
     bool ok = true;
     for (int r = 0; r < n_ranges && ok; ++r) {
       const int b = r & 1, u = r >> 1;
@@ -221,19 +223,19 @@ __global__ void __launch_bounds__(THREADS, 1)
       __syncwarp();
       if (!ok) break;
       tc_fence_after();
-#pragma unroll 1
-      for (int c0 = 0; c0 < HALF_COLS; c0 += 16) {
-        uint32_t d[16], sacc[16];
-        tmem_ld_x16(tmem + lane_base + b * D_COLS + c_base + c0, d);
-        if (r > 0) tmem_ld_x16(tmem + lane_base + S_COL + c_base + c0, sacc);
-        tmem_wait_ld();
-        if (r > 0) {
+      const uint32_t src = tmem + lane_base + b * BN + c_base;
 #pragma unroll
-          for (int k = 0; k < 16; ++k) d[k] = __float_as_uint(__uint_as_float(sacc[k]) + __uint_as_float(d[k]));
+      for (int c = 0; c < HC; c += 32) {
+        uint32_t d0[16], d1[16];
+        tmem_ld_x16(src + c, d0);
+        tmem_ld_x16(src + c + 16, d1);
+        tmem_wait_ld();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          S[c + k] += __uint_as_float(d0[k]);
+          S[c + 16 + k] += __uint_as_float(d1[k]);
         }
-        tmem_st_x16(tmem + lane_base + S_COL + c_base + c0, d);
       }
-      tmem_wait_st();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&d_free[b]);
@@ -242,23 +244,16 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int row = quarter * 32 + lane;
     const int64_t il = static_cast<int64_t>(ib) + row;
     const bool valid = ok && !*abort_flag && il < args.n_i && n_it > 0;
-    float* Vz = args.V + static_cast<int64_t>(split) * args.n_pair * 3 * args.gcp;
-    const int64_t col_off = static_cast<int64_t>(x) * args.gcp + il;
-    tc_fence_after();
-#pragma unroll 1
-    for (int c0 = 0; c0 < HALF_COLS; c0 += 16) {
-      uint32_t sacc[16];
-      tmem_ld_x16(tmem + lane_base + S_COL + c_base + c0, sacc);
-      tmem_wait_ld();
-      if (valid) {
+    if (valid) {
+      float* Vz = args.V + static_cast<int64_t>(split) * args.n_pair * 3 * args.gcp;
+      const int64_t col_off = static_cast<int64_t>(x) * args.gcp + il;
+      const int pq0 = n_tile * BN + static_cast<int>(c_base);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const int pq = n_tile * VF_BN + static_cast<int>(c_base) + c0 + k;
-          if (pq < args.n_pair) {
-            const float v = __uint_as_float(sacc[k]) * args.unscale_g;
-            Vz[static_cast<int64_t>(pq) * 3 * args.gcp + col_off] = ldexpf(v, -__ldg(args.colexp + pq));
-          }
-        }
+      for (int k = 0; k < HC; ++k) {
+        const int pq = pq0 + k;
+        if (pq < args.n_pair)
+          Vz[static_cast<int64_t>(pq) * 3 * args.gcp + col_off] =
+              ldexpf(S[k] * args.unscale_g, -__ldg(args.colexp + pq));
       }
     }
   }

@@ -221,7 +221,7 @@ int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t NGp, int parts, int64_t n_o
   cap = std::max<int64_t>(128, std::min<int64_t>(cap, 32768) / 128 * 128);
   const int64_t need = round_up(n_outer, 128);
   if (need <= cap) return need;
-  const int nt = (NP + VF_BN - 1) / VF_BN;
+  const int nt = f64 ? 1 : (NP + vf_bn(parts) - 1) / vf_bn(parts);
   int64_t best = cap;
   double best_eff = 0.0;
   for (int64_t tiles = cap / 128; tiles >= std::max<int64_t>(1, cap / 256); --tiles) {
@@ -497,7 +497,7 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
   return XTC_OK;
 }
 
-// Tensor maps of the step (b) operands: rho^T (box 32 x 160) and the gradient table, as stored by
+// Tensor maps of the step (b) operands: rho^T (box 32 x vf_bn) and the gradient table, as stored by
 // step (a) (box 32 x 32) and as loaded by the GEMM (box 32 x 128).
 struct VfMaps {
   CUtensorMap rho, g_store, g_load;
@@ -506,7 +506,7 @@ int make_vfield_maps(xtc_ctx* ctx, const Plan& pl, VfMaps& m) {
   if (pl.f64) return XTC_OK;
   const bool bf = pl.parts_b == 3;
   int rc;
-  if ((rc = make_tmap_3d(ctx, &m.rho, ctx->rho.p, bf, pl.NGp, pl.NP, pl.parts_b, VF_BK, VF_BN))) return rc;
+  if ((rc = make_tmap_3d(ctx, &m.rho, ctx->rho.p, bf, pl.NGp, pl.NP, pl.parts_b, VF_BK, vf_bn(pl.parts_b)))) return rc;
   if ((rc = make_tmap_3d(ctx, &m.g_store, ctx->G.p, bf, pl.NGp, 3 * pl.gc, pl.parts_b, VF_BK, 32))) return rc;
   return make_tmap_3d(ctx, &m.g_load, ctx->G.p, bf, pl.NGp, 3 * pl.gc, pl.parts_b, VF_BK, VF_BM);
 }
@@ -550,7 +550,7 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   a.n_i = n_i;
   a.gcp = pl.gc;
   a.mt_per_x = mt_per_x;
-  a.n_tiles = (pl.NP + VF_BN - 1) / VF_BN;
+  a.n_tiles = (pl.NP + vf_bn(pl.parts_b) - 1) / vf_bn(pl.parts_b);
   a.n_pair = pl.NP;
   a.n_kb = n_kb;
   a.kb_per_split = (a.n_kb + pl.splits - 1) / pl.splits;

@@ -26,7 +26,10 @@ constexpr int PT_COEF = 14;     // x y z, K0[3] K1[3] K2[3], Hc1 Hc2
 
 // Tile shapes of the tensor-core kernels.
 constexpr int VF_BM = 128;      // outer points per tile (TMEM lanes)
-constexpr int VF_BN = 160;      // orbital pairs per tile; 3 accumulators of 160 columns
+// orbital pairs per step (b) tile: two TMEM accumulators of vf_bn columns, a running sum of vf_bn / 2
+// columns in the registers of each drain thread; 5 pipeline stages of the split operands fit in
+// shared memory with 2 parts (40 KB per stage), 4 with 3 parts (54 KB)
+__host__ __device__ constexpr int vf_bn(int parts) { return parts == 2 ? 192 : 160; }
 constexpr int VF_BK = 32;       // inner points per pipeline stage (64-byte rows, SWIZZLE_64B)
 constexpr int AS_BM = 128;      // step (d) tile rows (pairs pq)
 constexpr int AS_BN = 128;      // step (d) tile columns (pairs rs)
@@ -80,14 +83,14 @@ struct GfieldArgs {
 void launch_gfield(const CUtensorMap* tm_g_store, const GfieldArgs& a, int parts, cudaStream_t st);
 
 // Step (b), tensor cores.  V[z][pq][x][il] (FP32, il = i - i0 < gcp) for the outer points of the
-// chunk, from the G table (tm_g: box 32 x 128) and the split rho^T (tm_rho: box 32 x 160).
+// chunk, from the G table (tm_g: box 32 x 128) and the split rho^T (tm_rho: box 32 x vf_bn(parts)).
 struct VfieldArgs {
   const int* colexp;           // per-pair exponent of the rho scaling (0 when unscaled)
   float* V;                    // output base
   int64_t n_i;                 // outer points of this chunk
   int64_t gcp;                 // padded chunk length (row stride of V and of G per component)
   int mt_per_x;                // 128-row tiles per component: ceil(n_i / 128)
-  int n_tiles;                 // 160-column tiles: ceil(n_pair / 160)
+  int n_tiles;                 // column tiles: ceil(n_pair / vf_bn(parts))
   int n_pair;
   int kb_per_split, n_kb;      // inner K-blocks per split slice, total K-blocks
   int kd;                      // K-blocks per TMEM accumulation range (then added to the FP32 running sum)
