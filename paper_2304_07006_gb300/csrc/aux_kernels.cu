@@ -115,13 +115,16 @@ __global__ void rho_split_kernel(const double* __restrict__ phiT, const double* 
     const int p = pp[pq], q = pq_[pq];
     double v = j < n_grid ? w[j] * phiT[p * n_pad + j] * phiT[q * n_pad + j] : 0.0;
     v = ldexp(v, e);
-    const int64_t o = static_cast<int64_t>(pq) * n_pad + j;
     if (!BF16) {
+      // the two parts of a 32-point block share one 128-byte row: [pq][j / 32][part][j % 32]
+      const int64_t o = static_cast<int64_t>(pq) * 2 * n_pad + (j >> 5) * 64 + (j & 31);
       const __half h = __double2half(v);
       const __half l = __double2half(v - static_cast<double>(__half2float(h)));
       out[o] = __half_as_ushort(h);
-      out[part_stride + o] = __half_as_ushort(l);
+      out[o + 32] = __half_as_ushort(l);
     } else {
+      // one plane per part: [part][pq][j]
+      const int64_t o = static_cast<int64_t>(pq) * n_pad + j;
       const __nv_bfloat16 h = __double2bfloat16(v);
       const double r1 = v - static_cast<double>(__bfloat162float(h));
       const __nv_bfloat16 m = __double2bfloat16(r1);

@@ -1,8 +1,10 @@
 // Step (a) for the tensor-core path: the Jastrow gradient G_x(i, j) = d/dx_i u(r_i, r_j) of every
 // (outer point i, inner point j) pair of a chunk (section "Decomposition of two-body correction",
 // the factor that multiplies rho in V), split into fp16 (2 parts) or bf16 (3 parts) and stored
-// K-major as the A operand of the step (b) GEMM:
-//     G[part][x * gcp + il][j]     (il = i - i0, j contiguous, NGp columns, 64-byte swizzle tiles).
+// K-major as the A operand of the step (b) GEMM, row x * gcp + il (il = i - i0):
+//     fp16: G[row][j / 32][part][j % 32]  (both parts of a 32-point block in one 128-byte row,
+//           128-byte swizzle tiles, so that one TMA row request moves 128 bytes);
+//     bf16: G[part][row][j]               (one plane per part, 64-byte swizzle tiles).
 // Computing G once per chunk, instead of inside every orbital-pair tile of the GEMM, removes the
 // gradient from the GEMM's critical path; the table costs one HBM write and is then read through L2
 // by the GEMM's tiles.
@@ -10,10 +12,10 @@
 // One warp owns a unit of 32 outer points (one per lane, its per-point coefficients in registers)
 // and a run of inner-point blocks of 32.  For each block it evaluates the gradient in FP32 (two
 // inner points per packed FP32 instruction for up to two Jastrow centres), splits it, writes the
-// 3 x PARTS tiles of 32 rows x 64 bytes into shared memory in the 64-byte swizzle (conflict-free
-// 16-byte stores) and one lane stores them with TMA.  The gradient is taken with the pair formula
-// of jastrow_coef.cuh: per-point coefficients times polynomials in b = r12 / (1 + r12) and
-// a_jI = |r_j - R_I| / (1 + |r_j - R_I|).
+// tiles of the three components (32 rows x 128 bytes, or 3 parts x 32 rows x 64 bytes) into
+// shared memory in their swizzle (conflict-free 16-byte stores) and one lane stores them with TMA.
+// The gradient is taken with the pair formula of jastrow_coef.cuh: per-point coefficients times
+// polynomials in b = r12 / (1 + r12) and a_jI = |r_j - R_I| / (1 + |r_j - R_I|).
 #include "jastrow_coef.cuh"
 #include "ptx_sm100.cuh"
 #include "simt_pack.cuh"
@@ -24,7 +26,7 @@ namespace {
 
 constexpr int GF_WARPS = 8;
 constexpr int GF_THREADS = GF_WARPS * 32;
-constexpr int GF_TILE = 32 * 64;   // one part tile: 32 rows of 64 bytes
+constexpr int GF_TILE = 32 * 64;   // one part's share of a component tile: 32 rows of 64 bytes
 
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, uint32_t src, int c0, int c1, int c2) {
   asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
@@ -184,19 +186,27 @@ __global__ void __launch_bounds__(GF_THREADS)
 #pragma unroll
         for (int h = 0; h < 4; ++h) split_pair<BF16>(gv[x][2 * h], gv[x][2 * h + 1], w[h]);
 #pragma unroll
-        for (int p = 0; p < PARTS; ++p)
-          st_shared_v4(buf + (x * PARTS + p) * GF_TILE + sw64_offset(lane, c), w[0][p], w[1][p], w[2][p], w[3][p]);
+        for (int p = 0; p < PARTS; ++p) {
+          // fp16: component tile x of 32 rows x 128 bytes, part p in chunks 4p .. 4p + 3
+          const uint32_t off = PARTS == 2 ? x * 2 * GF_TILE + sw128_offset(lane, p * 4 + c)
+                                          : (x * PARTS + p) * GF_TILE + sw64_offset(lane, c);
+          st_shared_v4(buf + off, w[0][p], w[1][p], w[2][p], w[3][p]);
+        }
       }
     }
     fence_proxy_async_smem();
     __syncwarp();
     if (lane == 0) {
 #pragma unroll
-      for (int x = 0; x < 3; ++x)
+      for (int x = 0; x < 3; ++x) {
+        if (PARTS == 2) {
+          tma_store_3d(&tm_g, buf + x * 2 * GF_TILE, kb * 2 * VF_BK, static_cast<int>(x * args.gcp) + row0, 0);
+        } else {
 #pragma unroll
-        for (int p = 0; p < PARTS; ++p)
-          tma_store_3d(&tm_g, buf + (x * PARTS + p) * GF_TILE, kb * VF_BK,
-                       static_cast<int>(x * args.gcp) + row0, p);
+          for (int p = 0; p < PARTS; ++p)
+            tma_store_3d(&tm_g, buf + (x * PARTS + p) * GF_TILE, kb * VF_BK, static_cast<int>(x * args.gcp) + row0, p);
+        }
+      }
       bulk_commit();
     }
   }

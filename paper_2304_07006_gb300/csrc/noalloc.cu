@@ -163,14 +163,18 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     // rho^T [part][pq][j] (box 32 x vf_bn) and the gradient table [part][x * gc + il][j] (boxes 32 x 32
     // for the step (a) stores and 32 x 128 for the step (b) loads)
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(cv.encode_tiled);
+    // (fp16: both parts of a 32-point block in one 128-byte row; bf16: one plane per part)
+    const bool wide = parts == 2;
+    const int64_t cols = wide ? 2 * NGp : NGp, planes = wide ? 1 : parts;
     auto map = [&](CUtensorMap* m, void* base, int64_t rows, uint32_t box_rows) {
-      const cuuint64_t dims[3] = {static_cast<cuuint64_t>(NGp), static_cast<cuuint64_t>(rows),
-                                  static_cast<cuuint64_t>(parts)};
-      const cuuint64_t strides[2] = {static_cast<cuuint64_t>(NGp) * 2, static_cast<cuuint64_t>(NGp) * rows * 2};
-      const cuuint32_t box[3] = {VF_BK, box_rows, 1};
+      const cuuint64_t dims[3] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows),
+                                  static_cast<cuuint64_t>(planes)};
+      const cuuint64_t strides[2] = {static_cast<cuuint64_t>(cols) * 2, static_cast<cuuint64_t>(cols) * rows * 2};
+      const cuuint32_t box[3] = {static_cast<cuuint32_t>(wide ? 2 * VF_BK : VF_BK), box_rows, 1};
       const cuuint32_t es[3] = {1, 1, 1};
       return encode(m, parts == 3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims,
-                    strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                    strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    wide ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
     if (!map(&tm, rho, NP, vf_bn(parts)) || !map(&tm_gs, G, 3 * gc, 32) || !map(&tm_gl, G, 3 * gc, VF_BM))
@@ -214,6 +218,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
       a.n_kb = n_kb;
       a.kb_per_split = n_kb;
       a.kd = std::min(cv.vf_kd, parts == 2 ? 4 : 2);
+      a.cluster = cv.vf_cluster;
       a.unscale_g = std::ldexp(1.0f, -sg);
       a.err = err;
       launch_vfield_tc(&tm_gl, &tm, a, parts, 1, st);

@@ -144,6 +144,18 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
   return d;
 }
 
+// The same for 128-byte rows in the 128-byte swizzle (8-row groups of 1024 bytes), layout
+// SWIZZLE_128B.  K steps inside a row advance the start address by 32 bytes (16 fp16 values).
+__device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1u) << 16;
+  d |= static_cast<uint64_t>(1024u >> 4) << 32;
+  d |= static_cast<uint64_t>(1u) << 46;
+  d |= static_cast<uint64_t>(2u) << 61;
+  return d;
+}
+
 // Instruction descriptor for kind::f16: FP32 accumulator, A and B both fp16 or both bf16,
 // both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
@@ -154,6 +166,10 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool bf16) {
 // Byte offset of the 16-byte chunk `chunk` (0..3) of row `row` in a 64-byte-swizzled K-major tile.
 __device__ __forceinline__ uint32_t sw64_offset(int row, int chunk) {
   return static_cast<uint32_t>(row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4));
+}
+// Byte offset of the 16-byte chunk `chunk` (0..7) of row `row` in a 128-byte-swizzled K-major tile.
+__device__ __forceinline__ uint32_t sw128_offset(int row, int chunk) {
+  return static_cast<uint32_t>(row * 128 + ((chunk ^ (row & 7)) << 4));
 }
 
 }  // namespace xtc

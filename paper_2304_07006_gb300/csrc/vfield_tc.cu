@@ -6,8 +6,10 @@
 // B = rho^T (written by the rho split kernel), both split into fp16 (2 parts) or bf16 (3 parts).
 //
 // CTA tile: 128 A rows (128 outer points of one component) x BN orbital pairs (192 with 2 parts,
-// 160 with 3), 32 inner points per pipeline stage (64-byte rows, 64-byte swizzle, K-major), all
-// operands loaded by TMA.
+// 160 with 3), 32 inner points per pipeline stage, K-major, all operands loaded by TMA.  With 2
+// parts both parts of a row share one 128-byte row (128-byte swizzle; one TMA box per operand and
+// stage); with 3 parts every part is a plane of 64-byte rows (64-byte swizzle).  The TMA engine's
+// rate is set by its row requests, so the wide rows move twice the bytes per request.
 //   * warp 0 (one lane): TMA loads of the A and B tiles of every part;
 //   * warp 1 (one lane): tcgen05.mma for every split product into one of two TMEM accumulators;
 //   * warps 2..9: every `kd` stages they load the finished accumulator (tcgen05.ld) and add it into
@@ -18,8 +20,13 @@
 // Each range is short (default two stages), its MMAs issue the small cross products of all its
 // stages first so that only the hi x hi products meet a large accumulator, and the ranges are
 // summed with round-to-nearest FP32 adds.
-// CTAs are ordered in groups of GM row tiles so that the CTAs resident at one time share their A
-// and B panels in L2.
+// The kernel is bound by the L2 -> shared memory traffic of its operand tiles, so CTAs run in
+// clusters of CM x CN tiles: each A tile is fetched once from L2 and multicast by TMA to the CN
+// CTAs of its tile row, each B tile to the CM CTAs of its tile column (CTA (i, j) of a cluster
+// issues the parts p of its A tile with p % CN == j and those of its B tile with p % CM == i).
+// A stage slot is refilled only after every CTA of the cluster has released it (the MMA commits
+// are multicast to all of them).  Clusters are ordered in groups of GM row tiles so that the
+// clusters resident at one time also share their panels in L2.
 #include "ptx_sm100.cuh"
 #include "xtc_internal.cuh"
 
@@ -29,7 +36,7 @@ namespace {
 constexpr int DRAIN_WARPS = 8;       // two per TMEM lane quarter, BN/2 columns each
 constexpr int THREADS = (2 + DRAIN_WARPS) * 32;
 constexpr int A_TILE = VF_BM * 64;   // bytes per part tile (128 rows of 64 B)
-constexpr int GM = 8;                // row tiles per CTA group (L2 reuse)
+constexpr int GM = 8;                // row tiles per cluster group (L2 reuse)
 
 template <int PARTS>
 struct VfCfg {
@@ -46,6 +53,13 @@ struct VfCfg {
 static_assert(VfCfg<2>::SMEM <= 232448 && VfCfg<3>::SMEM <= 232448, "shared memory per CTA");
 static_assert(2 * vf_bn(2) <= 512 && 2 * vf_bn(3) <= 512, "two accumulators in 512 TMEM columns");
 static_assert(vf_bn(2) % 32 == 0 && vf_bn(3) % 32 == 0, "drain chunks of 16 columns, two at a time");
+
+// Shared-memory descriptor of part p, K step ks (16 values) of an operand tile at `base`.
+template <int PARTS>
+__device__ __forceinline__ uint64_t op_desc(uint32_t base, int tile_bytes, int p, int ks) {
+  if (PARTS == 2) return sdesc_kmajor_sw128(base + p * 64 + ks * 32);
+  return sdesc_kmajor_sw64(base + p * tile_bytes + ks * 32);
+}
 
 // (A part, B part) of each split product in issue order: the small cross products first and
 // hi x hi last, so that the truncations of the early MMAs act on a small accumulator.
@@ -64,6 +78,34 @@ __device__ __forceinline__ void prod_parts(int p, int& pa, int& pb) {
   }
 }
 
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// All threads of every CTA of the cluster (release / acquire at cluster scope).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// TMA tile load written to the same shared-memory offset of every CTA in `mask`, each of which
+// receives the complete_tx on its own mbarrier at the offset of `bar`.
+__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* tm, uint64_t* bar, int c0, int c1,
+                                               int c2, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
+      : "memory");
+}
+// Arrives on the mbarrier at the offset of `bar` in every CTA of `mask` once this thread's MMAs
+// have completed.
+__device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
+                   "r"(smem_u32(bar)),
+               "h"(mask)
+               : "memory");
+}
+
 // 32 lanes x 16 consecutive 32-bit columns: thread t of the warp receives lane (base + t).
 __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
@@ -74,13 +116,14 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr)
       : "memory");
 }
-template <int PARTS>
+template <int PARTS, int CM, int CN>
 __global__ void __launch_bounds__(THREADS, 1)
     vfield_tc_kernel(const __grid_constant__ CUtensorMap tm_g, const __grid_constant__ CUtensorMap tm_rho,
                      const VfieldArgs args) {
   using Cfg = VfCfg<PARTS>;
   constexpr bool BF16 = PARTS == 3;
   constexpr int BN = Cfg::BN, HC = Cfg::HC, STAGES = Cfg::STAGES;
+  constexpr int CS = CM * CN;  // CTAs per cluster
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -94,14 +137,22 @@ __global__ void __launch_bounds__(THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // grouped tile order: GM row tiles x every column tile, row tile fastest
+  // this CTA's place (ci, cj) in its cluster and the cluster's tile block, in grouped order:
+  // GMC cluster rows x every cluster column, cluster row fastest
+  const int rank = CS > 1 ? static_cast<int>(cluster_ctarank()) : 0;
+  const int ci = rank % CM, cj = rank / CM;
   const int m_tiles = 3 * args.mt_per_x;
-  const int L = blockIdx.x;
-  const int group = L / (GM * args.n_tiles);
-  const int first_m = group * GM;
-  const int gm = min(GM, m_tiles - first_m);
-  const int rem = L - group * GM * args.n_tiles;
-  const int m_tile = first_m + rem % gm, n_tile = rem / gm;
+  const int MC = (m_tiles + CM - 1) / CM, NC = (args.n_tiles + CN - 1) / CN;
+  constexpr int GMC = GM / CM > 0 ? GM / CM : 1;
+  const int cid = blockIdx.x / CS;
+  const int group = cid / (GMC * NC);
+  const int first_mc = group * GMC;
+  const int gmc = min(GMC, MC - first_mc);
+  const int rem = cid - group * GMC * NC;
+  const int m_tile = (first_mc + rem % gmc) * CM + ci, n_tile = (rem / gmc) * CN + cj;
+  // tiles past the matrix (when the tile counts are not multiples of the cluster shape) load
+  // zero-filled operands, take part in the cluster's pipeline and store nothing
+  const bool ghost = m_tile >= m_tiles || n_tile >= args.n_tiles;
   const int x = m_tile / args.mt_per_x;
   const int ib = (m_tile - x * args.mt_per_x) * VF_BM;  // first outer point (chunk-local) of the tile
   const int row0 = static_cast<int>(x * args.gcp) + ib;
@@ -115,7 +166,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&tma_full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CS);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&d_full[b], 1);
@@ -133,6 +184,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if (CS > 1) cluster_sync_all();  // every barrier of the cluster is initialised before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t smem_base = smem_u32(smem);
@@ -140,15 +192,38 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------------------------------------------------------- TMA producer
+      uint16_t row_mask = 0, col_mask = 0;  // CTAs of this tile row / tile column
+      for (int q = 0; q < CN; ++q) row_mask |= static_cast<uint16_t>(1u << (ci + CM * q));
+      for (int q = 0; q < CM; ++q) col_mask |= static_cast<uint16_t>(1u << (q + CM * cj));
       int issued_end = kb0;
       for (int kb = kb0; kb < kb1; ++kb) {
         const int it = kb - kb0, s = it % STAGES, n = it / STAGES;
         if (n > 0 && !mbar_wait(&empty[s], (n - 1) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)) break;
         mbar_arrive_expect_tx(&tma_full[s], PARTS * (A_TILE + Cfg::B_TILE));
         uint8_t* st = smem + s * Cfg::STAGE_BYTES;
+        if (PARTS == 2) {
+          // one 128-byte-row box per operand holds both parts
+          if (CN == 1)
+            tma_load_3d(st, &tm_g, &tma_full[s], kb * 2 * VF_BK, row0, 0);
+          else if (cj == 0)
+            tma_load_3d_mc(st, &tm_g, &tma_full[s], kb * 2 * VF_BK, row0, 0, row_mask);
+          if (CM == 1)
+            tma_load_3d(st + Cfg::A_BYTES, &tm_rho, &tma_full[s], kb * 2 * VF_BK, n_tile * BN, 0);
+          else if (ci == 0)
+            tma_load_3d_mc(st + Cfg::A_BYTES, &tm_rho, &tma_full[s], kb * 2 * VF_BK, n_tile * BN, 0, col_mask);
+          issued_end = kb + 1;
+          continue;
+        }
         for (int p = 0; p < PARTS; ++p) {
-          tma_load_3d(st + p * A_TILE, &tm_g, &tma_full[s], kb * VF_BK, row0, p);
-          tma_load_3d(st + Cfg::A_BYTES + p * Cfg::B_TILE, &tm_rho, &tma_full[s], kb * VF_BK, n_tile * BN, p);
+          if (CN == 1)
+            tma_load_3d(st + p * A_TILE, &tm_g, &tma_full[s], kb * VF_BK, row0, p);
+          else if (p % CN == cj)
+            tma_load_3d_mc(st + p * A_TILE, &tm_g, &tma_full[s], kb * VF_BK, row0, p, row_mask);
+          if (CM == 1)
+            tma_load_3d(st + Cfg::A_BYTES + p * Cfg::B_TILE, &tm_rho, &tma_full[s], kb * VF_BK, n_tile * BN, p);
+          else if (p % CM == ci)
+            tma_load_3d_mc(st + Cfg::A_BYTES + p * Cfg::B_TILE, &tm_rho, &tma_full[s], kb * VF_BK, n_tile * BN, p,
+                           col_mask);
         }
         issued_end = kb + 1;
       }
@@ -159,6 +234,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         mbar_wait(&tma_full[it % STAGES], (it / STAGES) & 1, reinterpret_cast<volatile int*>(&zero), args.err,
                   DEV_ERR_TIMEOUT_VF);
       }
+      // so do the releases that the other CTAs of the cluster multicast to this CTA's slots
+      if (CS > 1)
+        for (int s = 0; s < STAGES && s < n_it; ++s) {
+          const int last = s + ((n_it - 1 - s) / STAGES) * STAGES;
+          mbar_wait(&empty[s], (last / STAGES) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF);
+        }
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -186,8 +267,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             prod_parts<PARTS>(p, pa, pb);
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks)
-              tc_mma_f16(d_tmem, sdesc_kmajor_sw64(sa + pa * A_TILE + ks * 32),
-                         sdesc_kmajor_sw64(sb + pb * Cfg::B_TILE + ks * 32), idesc,
+              tc_mma_f16(d_tmem, op_desc<PARTS>(sa, A_TILE, pa, ks), op_desc<PARTS>(sb, Cfg::B_TILE, pb, ks), idesc,
                          (it == it0 && p == 0 && ks == 0) ? 0u : 1u);
           }
         }
@@ -197,8 +277,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t sb = sa + Cfg::A_BYTES;
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks)
-            tc_mma_f16(d_tmem, sdesc_kmajor_sw64(sa + ks * 32), sdesc_kmajor_sw64(sb + ks * 32), idesc, 1u);
-          tc_commit(&empty[it % STAGES]);
+            tc_mma_f16(d_tmem, op_desc<PARTS>(sa, A_TILE, 0, ks), op_desc<PARTS>(sb, Cfg::B_TILE, 0, ks), idesc, 1u);
+          if (CS > 1)
+            tc_commit_mc(&empty[it % STAGES], static_cast<uint16_t>((1u << CS) - 1));
+          else
+            tc_commit(&empty[it % STAGES]);
         }
         tc_commit(&d_full[b]);
       }
@@ -243,7 +326,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // store the running sum: row = outer point ib + row of component x -> V[split][pq][x][il]
     const int row = quarter * 32 + lane;
     const int64_t il = static_cast<int64_t>(ib) + row;
-    const bool valid = ok && !*abort_flag && il < args.n_i && n_it > 0;
+    const bool valid = ok && !*abort_flag && !ghost && il < args.n_i && n_it > 0;
     if (valid) {
       float* Vz = args.V + static_cast<int64_t>(split) * args.n_pair * 3 * args.gcp;
       const int64_t col_off = static_cast<int64_t>(x) * args.gcp + il;
@@ -260,6 +343,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   tc_fence_before();
   __syncthreads();
+  if (CS > 1) cluster_sync_all();  // no CTA leaves while the others may still signal it
   if (warp == 0) {
     __syncwarp();
     tc_fence_after();
@@ -267,27 +351,52 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-template <int PARTS>
+template <int PARTS, int CM, int CN>
 void launch_t(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int splits,
               cudaStream_t st) {
-  auto kern = vfield_tc_kernel<PARTS>;
+  auto kern = vfield_tc_kernel<PARTS, CM, CN>;
   constexpr int smem = VfCfg<PARTS>::SMEM;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  dim3 grid(3 * a.mt_per_x * a.n_tiles, splits);
-  kern<<<grid, THREADS, smem, st>>>(*tm_g, *tm_rho, a);
+  const int MC = (3 * a.mt_per_x + CM - 1) / CM, NC = (a.n_tiles + CN - 1) / CN;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(MC * NC * CM * CN), static_cast<unsigned>(splits), 1);
+  cfg.blockDim = dim3(THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CM * CN;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, *tm_g, *tm_rho, a);
+}
+
+template <int PARTS>
+void launch_p(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int splits, cudaStream_t st) {
+  switch (a.cluster) {
+    case 11: launch_t<PARTS, 1, 1>(tm_g, tm_rho, a, splits, st); break;
+    case 21: launch_t<PARTS, 2, 1>(tm_g, tm_rho, a, splits, st); break;
+    case 12: launch_t<PARTS, 1, 2>(tm_g, tm_rho, a, splits, st); break;
+    case 41: launch_t<PARTS, 4, 1>(tm_g, tm_rho, a, splits, st); break;
+    case 42: launch_t<PARTS, 4, 2>(tm_g, tm_rho, a, splits, st); break;
+    default: launch_t<PARTS, 2, 2>(tm_g, tm_rho, a, splits, st); break;
+  }
 }
 
 }  // namespace
 
 bool vfield_tc_supported(int n_nuc) { return n_nuc >= 1 && n_nuc <= 4; }
+bool vfield_cluster_valid(int c) { return c == 11 || c == 21 || c == 12 || c == 22 || c == 41 || c == 42; }
 
 void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int parts,
                       int splits, cudaStream_t st) {
   if (a.mt_per_x <= 0 || a.n_tiles <= 0 || splits <= 0) return;
   if (parts == 2)
-    launch_t<2>(tm_g, tm_rho, a, splits, st);
+    launch_p<2>(tm_g, tm_rho, a, splits, st);
   else
-    launch_t<3>(tm_g, tm_rho, a, splits, st);
+    launch_p<3>(tm_g, tm_rho, a, splits, st);
 }
 
 }  // namespace xtc

@@ -72,6 +72,7 @@ struct xtc_ctx {
   int64_t launches[XTC_N_KERNELS] = {0};
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   int vf_kd = 2;  // K-blocks per tensor-core accumulation range in step (b)
+  int vf_cluster = 11;  // step (b) cluster shape 10 * CM + CN (1 x 1: no multicast)
   int as_kd = 2;  // the same for step (d)
 };
 
@@ -176,13 +177,14 @@ void jacobi_eigen(std::vector<double>& a, std::vector<double>& v, int n) {
 }
 
 int make_tmap_3d(xtc_ctx* ctx, CUtensorMap* tm, void* base, bool bf16, uint64_t d0, uint64_t d1, uint64_t d2,
-                 uint32_t b0, uint32_t b1) {
+                 uint32_t b0, uint32_t b1, bool sw128 = false) {
   const cuuint64_t dims[3] = {d0, d1, d2};
   const cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};
   const cuuint32_t box[3] = {b0, b1, 1};
   const cuuint32_t es[3] = {1, 1, 1};
   CUresult r = ctx->encode(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims,
-                           strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                           strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           sw128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(ctx, XTC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
   return XTC_OK;
@@ -299,6 +301,8 @@ int xtc_create(xtc_ctx** out, const xtc_params* p) {
   }
   ctx->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   if (const char* s = std::getenv("XTC_VF_KD")) ctx->vf_kd = std::max(1, std::atoi(s));
+  if (const char* s = std::getenv("XTC_VF_CLUSTER"))
+    if (vfield_cluster_valid(std::atoi(s))) ctx->vf_cluster = std::atoi(s);
   if (const char* s = std::getenv("XTC_AS_KD")) ctx->as_kd = std::max(1, std::atoi(s));
   if (!ensure(ctx->jp_dev, sizeof(JastrowParams)) || !ensure(ctx->err_dev, 16) || !ensure(ctx->flag_dev, 16)) {
     xtc_destroy(ctx);
@@ -497,18 +501,22 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
   return XTC_OK;
 }
 
-// Tensor maps of the step (b) operands: rho^T (box 32 x vf_bn) and the gradient table, as stored by
-// step (a) (box 32 x 32) and as loaded by the GEMM (box 32 x 128).
+// Tensor maps of the step (b) operands: rho^T (box rows vf_bn) and the gradient table, as stored by
+// step (a) (box rows 32) and as loaded by the GEMM (box rows 128).  fp16: both parts of a 32-point
+// block in one 128-byte row (rows of 2 NGp values, boxes 64 wide, 128-byte swizzle); bf16: one
+// plane per part (rows of NGp values, boxes 32 wide, 64-byte swizzle).
 struct VfMaps {
   CUtensorMap rho, g_store, g_load;
 };
 int make_vfield_maps(xtc_ctx* ctx, const Plan& pl, VfMaps& m) {
   if (pl.f64) return XTC_OK;
-  const bool bf = pl.parts_b == 3;
+  const bool bf = pl.parts_b == 3, wide = pl.parts_b == 2;
+  const uint64_t cols = wide ? 2 * pl.NGp : pl.NGp, planes = wide ? 1 : pl.parts_b;
+  const uint32_t bk = wide ? 2 * VF_BK : VF_BK;
   int rc;
-  if ((rc = make_tmap_3d(ctx, &m.rho, ctx->rho.p, bf, pl.NGp, pl.NP, pl.parts_b, VF_BK, vf_bn(pl.parts_b)))) return rc;
-  if ((rc = make_tmap_3d(ctx, &m.g_store, ctx->G.p, bf, pl.NGp, 3 * pl.gc, pl.parts_b, VF_BK, 32))) return rc;
-  return make_tmap_3d(ctx, &m.g_load, ctx->G.p, bf, pl.NGp, 3 * pl.gc, pl.parts_b, VF_BK, VF_BM);
+  if ((rc = make_tmap_3d(ctx, &m.rho, ctx->rho.p, bf, cols, pl.NP, planes, bk, vf_bn(pl.parts_b), wide))) return rc;
+  if ((rc = make_tmap_3d(ctx, &m.g_store, ctx->G.p, bf, cols, 3 * pl.gc, planes, bk, 32, wide))) return rc;
+  return make_tmap_3d(ctx, &m.g_load, ctx->G.p, bf, cols, 3 * pl.gc, planes, bk, VF_BM, wide);
 }
 
 // Steps (a)+(b) for outer points [i0, i0 + n_i) into ctx->V.
@@ -555,6 +563,7 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   a.n_kb = n_kb;
   a.kb_per_split = (a.n_kb + pl.splits - 1) / pl.splits;
   a.kd = std::min(ctx->vf_kd, pl.parts_b == 2 ? 4 : 2);
+  a.cluster = ctx->vf_cluster;
   a.unscale_g = std::ldexp(1.0f, -sg);
   a.err = ctx->err_dev.as<int>();
   const int splits = (a.n_kb + a.kb_per_split - 1) / a.kb_per_split;  // every slice non-empty
@@ -789,6 +798,7 @@ bool xtc_internal_ctx_view(const xtc_ctx* ctx, xtc::CtxView* v) {
   v->n_nuc = ctx->jp.n_nuc;
   v->g_bound = ctx->g_bound;
   v->vf_kd = ctx->vf_kd;
+  v->vf_cluster = ctx->vf_cluster;
   v->jp_dev = ctx->jp_dev.as<JastrowParams>();
   v->encode_tiled = reinterpret_cast<void*>(ctx->encode);
   return true;

@@ -50,7 +50,9 @@ void launch_jtab(const double* grid, int64_t n_grid, int64_t n_grid_pad, const J
                  int n_nuc, int js, float* jtab, cudaStream_t st);
 
 // Pair products rho^T[pq][j] = w_j phi_p(j) phi_q(j) split into parts (fp16 or bf16), with
-// per-pair power-of-2 scale (fp16).  colexp[pq] receives the exponent used.
+// per-pair power-of-2 scale (fp16).  colexp[pq] receives the exponent used.  Layout: fp16 (2 parts)
+// [pq][j / 32][part][j % 32] (both parts of a 32-point block in one 128-byte row); bf16 (3 parts)
+// [part][pq][j].
 void launch_rho_split(const double* phiT, const double* w, int64_t n_grid, int64_t n_grid_pad, int n_orb,
                       int parts, bool bf16, bool scale, const int* pair_p, const int* pair_q,
                       unsigned int* colmax_bits, int* colexp, void* out, cudaStream_t st);
@@ -66,9 +68,10 @@ void launch_transpose_phi(const double* phi, int64_t n_grid, int64_t n_grid_pad,
 // Finite check: sets *flag non-zero if any of n values is NaN/Inf.
 void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t st);
 
-// Step (a), tensor-core path: the split Jastrow gradient G[part][x * gcp + il][j] (fp16 or bf16,
-// K-major, 64-byte swizzled TMA tiles of 32 rows) for the outer points [i0, i0 + n_i) and every
-// padded inner point.  Rows up to n_tiles * 32 are written (past n_i they repeat the last point).
+// Step (a), tensor-core path: the split Jastrow gradient of the outer points [i0, i0 + n_i) and every
+// padded inner point, K-major, row x * gcp + il: fp16 (2 parts) G[row][j / 32][part][j % 32] stored
+// as 128-byte-swizzled TMA tiles (box 64 x 32); bf16 (3 parts) G[part][row][j] as 64-byte-swizzled
+// tiles (box 32 x 32).  Rows up to n_tiles * 32 are written (past n_i they repeat the last point).
 struct GfieldArgs {
   const double* grid;          // outer-point coordinates (global index space)
   const JastrowParams* jp;
@@ -95,9 +98,12 @@ struct VfieldArgs {
   int kb_per_split, n_kb;      // inner K-blocks per split slice, total K-blocks
   int kd;                      // K-blocks per TMEM accumulation range (then added to the FP32 running sum)
   float unscale_g;             // 2^-sG
+  int cluster;                 // cluster shape 10 * CM + CN (11, 21, 12, 22, 41, 42); CM tiles along
+                               // the rows share B tiles, CN along the columns share A tiles
   int* err;
 };
 bool vfield_tc_supported(int n_nuc);
+bool vfield_cluster_valid(int cluster);
 void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int parts,
                       int splits, cudaStream_t st);
 
@@ -163,6 +169,7 @@ struct CtxView {
   int n_nuc;
   double g_bound;
   int vf_kd;
+  int vf_cluster;
   const JastrowParams* jp_dev;
   void* encode_tiled;  // PFN_cuTensorMapEncodeTiled_v12000
 };
