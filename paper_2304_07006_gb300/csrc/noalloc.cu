@@ -160,7 +160,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     launch_jtab(grid_xyz, n_grid, NGp, cv.jp_dev, n_nuc, 12, jtab, st);
     launch_rho_split(phiT, weights, n_grid, NGp, N, parts, parts == 3, parts == 2, pair_p, pair_q, colmax, colexp,
                      rho, st);
-    // rho^T [part][pq][j] (box 32 x vf_bn) and the gradient table [part][x * gc + il][j] (boxes 32 x 32
+    // rho^T (box rows vf_bn) and the gradient table [part][x * gc + il][j] (boxes 32 x 32
     // for the step (a) stores and 32 x 128 for the step (b) loads)
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(cv.encode_tiled);
     // (fp16: both parts of a 32-point block in one 128-byte row; bf16: one plane per part)
@@ -218,7 +218,6 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
       a.n_kb = n_kb;
       a.kb_per_split = n_kb;
       a.kd = std::min(cv.vf_kd, parts == 2 ? 4 : 2);
-      a.cluster = cv.vf_cluster;
       a.unscale_g = std::ldexp(1.0f, -sg);
       a.err = err;
       launch_vfield_tc(&tm_gl, &tm, a, parts, 1, st);

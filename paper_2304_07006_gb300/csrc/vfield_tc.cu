@@ -5,28 +5,29 @@
 // as a split-precision GEMM over the inner points j: A = G (written by gfield.cu, rows x*gcp + il),
 // B = rho^T (written by the rho split kernel), both split into fp16 (2 parts) or bf16 (3 parts).
 //
-// CTA tile: 128 A rows (128 outer points of one component) x BN orbital pairs (192 with 2 parts,
-// 160 with 3), 32 inner points per pipeline stage, K-major, all operands loaded by TMA.  With 2
-// parts both parts of a row share one 128-byte row (128-byte swizzle; one TMA box per operand and
-// stage); with 3 parts every part is a plane of 64-byte rows (64-byte swizzle).  The TMA engine's
-// rate is set by its row requests, so the wide rows move twice the bytes per request.
-//   * warp 0 (one lane): TMA loads of the A and B tiles of every part;
-//   * warp 1 (one lane): tcgen05.mma for every split product into one of two TMEM accumulators;
+// Tile: 128 A rows per CTA (128 outer points of one component) x BN orbital pairs (192 with 2
+// parts, 160 with 3), 32 inner points per pipeline stage, K-major, all operands loaded by TMA.
+// With 2 parts both parts of a row share one 128-byte row (128-byte swizzle; one TMA box per
+// operand and stage); with 3 parts every part is a plane of 64-byte rows (64-byte swizzle).
+//
+// Every tcgen05.commit stalls the tensor pipe for a few hundred cycles (measured: a group of g
+// back-to-back MMAs plus its commit takes about g x 96 + 300 cycles at N = 192), so the kernel
+// commits once per accumulation range: that single arrival releases the range's stage slots to the
+// TMA producer (which counts finished ranges in order) and hands the accumulator to the drains.
+//
+// Warp roles:
+//   * warp 0 (one lane): TMA loads of the A and B tiles;
+//   * warp 1 (one lane): MMA issuer;
 //   * warps 2..9: every `kd` stages they load the finished accumulator (tcgen05.ld) and add it into
 //     an FP32 running sum held in their registers (two warps per TMEM lane quarter, BN/2 columns
-//     each) while the MMA fills the other accumulator; at the end they store the sum, unscaled,
-//     as V[pq][x][i].
+//     each) while the MMA fills the other accumulator; at the end they store the sum, unscaled, as
+//     V[pq][x][i].
 // The tensor-core accumulator truncates toward zero at each MMA, which biases a long inner sum.
 // Each range is short (default two stages), its MMAs issue the small cross products of all its
 // stages first so that only the hi x hi products meet a large accumulator, and the ranges are
 // summed with round-to-nearest FP32 adds.
-// The kernel is bound by the L2 -> shared memory traffic of its operand tiles, so CTAs run in
-// clusters of CM x CN tiles: each A tile is fetched once from L2 and multicast by TMA to the CN
-// CTAs of its tile row, each B tile to the CM CTAs of its tile column (CTA (i, j) of a cluster
-// issues the parts p of its A tile with p % CN == j and those of its B tile with p % CM == i).
-// A stage slot is refilled only after every CTA of the cluster has released it (the MMA commits
-// are multicast to all of them).  Clusters are ordered in groups of GM row tiles so that the
-// clusters resident at one time also share their panels in L2.
+// Tiles are ordered in groups of GM row tiles so that the CTAs resident at one time share their A
+// and B panels in L2.
 #include "ptx_sm100.cuh"
 #include "xtc_internal.cuh"
 
@@ -35,24 +36,30 @@ namespace {
 
 constexpr int DRAIN_WARPS = 8;       // two per TMEM lane quarter, BN/2 columns each
 constexpr int THREADS = (2 + DRAIN_WARPS) * 32;
-constexpr int A_TILE = VF_BM * 64;   // bytes per part tile (128 rows of 64 B)
-constexpr int GM = 8;                // row tiles per cluster group (L2 reuse)
+constexpr int A_TILE = VF_BM * 64;   // bytes per part of an A tile (128 rows of 64 B)
+constexpr int GM = 8;                // row tiles per group (L2 reuse)
+
+constexpr int NRB = 8;               // range barriers (range r uses r % NRB)
 
 template <int PARTS>
 struct VfCfg {
-  static constexpr int BN = vf_bn(PARTS);
-  static constexpr int B_TILE = BN * 64;   // bytes per part tile (BN rows of 64 B)
-  static constexpr int HC = BN / 2;        // running-sum columns per drain thread
+  static constexpr int BN = vf_bn(PARTS);   // columns of the tile (TMEM accumulator width)
+  static constexpr int B_TILE = BN * 64;    // bytes per part of a B tile
+  static constexpr int HC = BN / 2;         // running-sum columns per drain thread
   static constexpr int NPROD = PARTS == 2 ? 3 : 6;
-  static constexpr int STAGES = PARTS == 2 ? 5 : 4;
   static constexpr int A_BYTES = PARTS * A_TILE;
   static constexpr int B_BYTES = PARTS * B_TILE;
   static constexpr int STAGE_BYTES = ((A_BYTES + B_BYTES + 1023) / 1024) * 1024;
+  static constexpr int STAGES = (220 * 1024) / STAGE_BYTES < 8 ? (220 * 1024) / STAGE_BYTES : 8;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 };
 static_assert(VfCfg<2>::SMEM <= 232448 && VfCfg<3>::SMEM <= 232448, "shared memory per CTA");
+static_assert(VfCfg<2>::STAGES >= 4 && VfCfg<3>::STAGES >= 4, "pipeline depth");
+// a wait for range r must not alias range r + NRB: the producer waits for the range of stage
+// k - STAGES before loading stage k, and range r + NRB starts past stage k when NRB > STAGES
+static_assert(NRB > VfCfg<2>::STAGES && NRB > VfCfg<3>::STAGES, "range barriers");
 static_assert(2 * vf_bn(2) <= 512 && 2 * vf_bn(3) <= 512, "two accumulators in 512 TMEM columns");
-static_assert(vf_bn(2) % 32 == 0 && vf_bn(3) % 32 == 0, "drain chunks of 16 columns, two at a time");
+static_assert(vf_bn(2) % 32 == 0 && vf_bn(3) % 32 == 0, "drain halves of whole 16-column chunks");
 
 // Shared-memory descriptor of part p, K step ks (16 values) of an operand tile at `base`.
 template <int PARTS>
@@ -78,34 +85,6 @@ __device__ __forceinline__ void prod_parts(int p, int& pa, int& pb) {
   }
 }
 
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// All threads of every CTA of the cluster (release / acquire at cluster scope).
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// TMA tile load written to the same shared-memory offset of every CTA in `mask`, each of which
-// receives the complete_tx on its own mbarrier at the offset of `bar`.
-__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* tm, uint64_t* bar, int c0, int c1,
-                                               int c2, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
-      : "memory");
-}
-// Arrives on the mbarrier at the offset of `bar` in every CTA of `mask` once this thread's MMAs
-// have completed.
-__device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
-                   "r"(smem_u32(bar)),
-               "h"(mask)
-               : "memory");
-}
-
 // 32 lanes x 16 consecutive 32-bit columns: thread t of the warp receives lane (base + t).
 __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
@@ -116,43 +95,34 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr)
       : "memory");
 }
-template <int PARTS, int CM, int CN>
+
+template <int PARTS>
 __global__ void __launch_bounds__(THREADS, 1)
     vfield_tc_kernel(const __grid_constant__ CUtensorMap tm_g, const __grid_constant__ CUtensorMap tm_rho,
                      const VfieldArgs args) {
   using Cfg = VfCfg<PARTS>;
   constexpr bool BF16 = PARTS == 3;
   constexpr int BN = Cfg::BN, HC = Cfg::HC, STAGES = Cfg::STAGES;
-  constexpr int CS = CM * CN;  // CTAs per cluster
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
-  uint64_t* tma_full = bars;                 // [STAGES]
-  uint64_t* empty = bars + STAGES;           // [STAGES]
-  uint64_t* d_full = bars + 2 * STAGES;      // [2]
-  uint64_t* d_free = bars + 2 * STAGES + 2;  // [2]
-  uint64_t* fin_bar = bars + 2 * STAGES + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  uint64_t* tma_full = bars;                  // [STAGES] the stage's loads landed
+  uint64_t* rdone = bars + STAGES;            // [NRB] the MMAs of range r (r % NRB) completed
+  uint64_t* d_free = bars + STAGES + NRB;     // [2] the drains released accumulator b
+  uint64_t* fin_bar = bars + STAGES + NRB + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + STAGES + NRB + 3);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // this CTA's place (ci, cj) in its cluster and the cluster's tile block, in grouped order:
-  // GMC cluster rows x every cluster column, cluster row fastest
-  const int rank = CS > 1 ? static_cast<int>(cluster_ctarank()) : 0;
-  const int ci = rank % CM, cj = rank / CM;
+  // grouped tile order: GM row tiles x every column tile, row tile fastest
   const int m_tiles = 3 * args.mt_per_x;
-  const int MC = (m_tiles + CM - 1) / CM, NC = (args.n_tiles + CN - 1) / CN;
-  constexpr int GMC = GM / CM > 0 ? GM / CM : 1;
-  const int cid = blockIdx.x / CS;
-  const int group = cid / (GMC * NC);
-  const int first_mc = group * GMC;
-  const int gmc = min(GMC, MC - first_mc);
-  const int rem = cid - group * GMC * NC;
-  const int m_tile = (first_mc + rem % gmc) * CM + ci, n_tile = (rem / gmc) * CN + cj;
-  // tiles past the matrix (when the tile counts are not multiples of the cluster shape) load
-  // zero-filled operands, take part in the cluster's pipeline and store nothing
-  const bool ghost = m_tile >= m_tiles || n_tile >= args.n_tiles;
+  const int L = blockIdx.x;
+  const int group = L / (GM * args.n_tiles);
+  const int first_m = group * GM;
+  const int gm = min(GM, m_tiles - first_m);
+  const int rem = L - group * GM * args.n_tiles;
+  const int m_tile = first_m + rem % gm, n_tile = rem / gm;
   const int x = m_tile / args.mt_per_x;
   const int ib = (m_tile - x * args.mt_per_x) * VF_BM;  // first outer point (chunk-local) of the tile
   const int row0 = static_cast<int>(x * args.gcp) + ib;
@@ -164,14 +134,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int n_ranges = (n_it + kd - 1) / kd;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&tma_full[s], 1);
-      mbar_init(&empty[s], CS);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&d_full[b], 1);
-      mbar_init(&d_free[b], DRAIN_WARPS);
-    }
+    for (int s = 0; s < STAGES; ++s) mbar_init(&tma_full[s], 1);
+    for (int r = 0; r < NRB; ++r) mbar_init(&rdone[r], 1);
+    for (int b = 0; b < 2; ++b) mbar_init(&d_free[b], DRAIN_WARPS);
     mbar_init(fin_bar, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -184,7 +149,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (CS > 1) cluster_sync_all();  // every barrier of the cluster is initialised before any multicast
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t smem_base = smem_u32(smem);
@@ -192,38 +156,28 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------------------------------------------------------- TMA producer
-      uint16_t row_mask = 0, col_mask = 0;  // CTAs of this tile row / tile column
-      for (int q = 0; q < CN; ++q) row_mask |= static_cast<uint16_t>(1u << (ci + CM * q));
-      for (int q = 0; q < CM; ++q) col_mask |= static_cast<uint16_t>(1u << (q + CM * cj));
+      int seen = 0;  // ranges known to have completed (their slots are free again)
       int issued_end = kb0;
       for (int kb = kb0; kb < kb1; ++kb) {
-        const int it = kb - kb0, s = it % STAGES, n = it / STAGES;
-        if (n > 0 && !mbar_wait(&empty[s], (n - 1) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)) break;
-        mbar_arrive_expect_tx(&tma_full[s], PARTS * (A_TILE + Cfg::B_TILE));
+        const int it = kb - kb0, s = it % STAGES;
+        if (it >= STAGES) {
+          const int need = (it - STAGES) / kd;  // range holding the slot's previous stage
+          bool ok = true;
+          for (; seen <= need && ok; ++seen)
+            ok = mbar_wait(&rdone[seen % NRB], (seen / NRB) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF);
+          if (!ok) break;
+        }
+        mbar_arrive_expect_tx(&tma_full[s], Cfg::A_BYTES + Cfg::B_BYTES);
         uint8_t* st = smem + s * Cfg::STAGE_BYTES;
         if (PARTS == 2) {
           // one 128-byte-row box per operand holds both parts
-          if (CN == 1)
-            tma_load_3d(st, &tm_g, &tma_full[s], kb * 2 * VF_BK, row0, 0);
-          else if (cj == 0)
-            tma_load_3d_mc(st, &tm_g, &tma_full[s], kb * 2 * VF_BK, row0, 0, row_mask);
-          if (CM == 1)
-            tma_load_3d(st + Cfg::A_BYTES, &tm_rho, &tma_full[s], kb * 2 * VF_BK, n_tile * BN, 0);
-          else if (ci == 0)
-            tma_load_3d_mc(st + Cfg::A_BYTES, &tm_rho, &tma_full[s], kb * 2 * VF_BK, n_tile * BN, 0, col_mask);
-          issued_end = kb + 1;
-          continue;
-        }
-        for (int p = 0; p < PARTS; ++p) {
-          if (CN == 1)
+          tma_load_3d(st, &tm_g, &tma_full[s], kb * 2 * VF_BK, row0, 0);
+          tma_load_3d(st + Cfg::A_BYTES, &tm_rho, &tma_full[s], kb * 2 * VF_BK, n_tile * BN, 0);
+        } else {
+          for (int p = 0; p < PARTS; ++p) {
             tma_load_3d(st + p * A_TILE, &tm_g, &tma_full[s], kb * VF_BK, row0, p);
-          else if (p % CN == cj)
-            tma_load_3d_mc(st + p * A_TILE, &tm_g, &tma_full[s], kb * VF_BK, row0, p, row_mask);
-          if (CM == 1)
             tma_load_3d(st + Cfg::A_BYTES + p * Cfg::B_TILE, &tm_rho, &tma_full[s], kb * VF_BK, n_tile * BN, p);
-          else if (p % CM == ci)
-            tma_load_3d_mc(st + Cfg::A_BYTES + p * Cfg::B_TILE, &tm_rho, &tma_full[s], kb * VF_BK, n_tile * BN, p,
-                           col_mask);
+          }
         }
         issued_end = kb + 1;
       }
@@ -234,19 +188,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         mbar_wait(&tma_full[it % STAGES], (it / STAGES) & 1, reinterpret_cast<volatile int*>(&zero), args.err,
                   DEV_ERR_TIMEOUT_VF);
       }
-      // so do the releases that the other CTAs of the cluster multicast to this CTA's slots
-      if (CS > 1)
-        for (int s = 0; s < STAGES && s < n_it; ++s) {
-          const int last = s + ((n_it - 1 - s) / STAGES) * STAGES;
-          mbar_wait(&empty[s], (last / STAGES) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF);
-        }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------------------------------------------------------- MMA issuer
       // A range of kd stages goes into one TMEM accumulator: first the cross products of each
       // stage as it lands (the accumulator is still small), then the hi x hi product of every
-      // stage, after which that stage is released.
+      // stage; one commit per range.
       constexpr uint32_t idesc = idesc_f16(VF_BM, BN, BF16);
       bool alive = true;
       for (int r = 0; r < n_ranges && alive; ++r) {
@@ -255,11 +203,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t d_tmem = tmem + b * BN;
         if (u >= 1 && !mbar_wait(&d_free[b], (u - 1) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)) break;
         for (int it = it0; it < it1; ++it) {
-          if (!(alive = mbar_wait(&tma_full[it % STAGES], (it / STAGES) & 1, abort_flag, args.err,
-                                  DEV_ERR_TIMEOUT_VF)))
-            break;
+          const int s = it % STAGES;
+          if (!(alive = mbar_wait(&tma_full[s], (it / STAGES) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF))) break;
           tc_fence_after();
-          const uint32_t sa = smem_base + (it % STAGES) * Cfg::STAGE_BYTES;
+          const uint32_t sa = smem_base + s * Cfg::STAGE_BYTES;
           const uint32_t sb = sa + Cfg::A_BYTES;
 #pragma unroll
           for (int p = 0; p < Cfg::NPROD - 1; ++p) {
@@ -278,12 +225,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks)
             tc_mma_f16(d_tmem, op_desc<PARTS>(sa, A_TILE, 0, ks), op_desc<PARTS>(sb, Cfg::B_TILE, 0, ks), idesc, 1u);
-          if (CS > 1)
-            tc_commit_mc(&empty[it % STAGES], static_cast<uint16_t>((1u << CS) - 1));
-          else
-            tc_commit(&empty[it % STAGES]);
         }
-        tc_commit(&d_full[b]);
+        tc_commit(&rdone[r % NRB]);
       }
       // every MMA issued by this thread has completed once fin_bar fires
       tc_commit(fin_bar);
@@ -301,14 +244,15 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int k = 0; k < HC; ++k) S[k] = 0.0f;
     bool ok = true;
     for (int r = 0; r < n_ranges && ok; ++r) {
-      const int b = r & 1, u = r >> 1;
-      ok = __all_sync(0xffffffffu, mbar_wait(&d_full[b], u & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF));
+      const int b = r & 1;
+      ok = __all_sync(0xffffffffu,
+                      mbar_wait(&rdone[r % NRB], (r / NRB) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF));
       __syncwarp();
       if (!ok) break;
       tc_fence_after();
       const uint32_t src = tmem + lane_base + b * BN + c_base;
 #pragma unroll
-      for (int c = 0; c < HC; c += 32) {
+      for (int c = 0; c + 32 <= HC; c += 32) {
         uint32_t d0[16], d1[16];
         tmem_ld_x16(src + c, d0);
         tmem_ld_x16(src + c + 16, d1);
@@ -319,6 +263,14 @@ __global__ void __launch_bounds__(THREADS, 1)
           S[c + 16 + k] += __uint_as_float(d1[k]);
         }
       }
+      if constexpr (HC % 32 != 0) {  // last 16 columns
+        constexpr int c = HC - 16;
+        uint32_t d0[16];
+        tmem_ld_x16(src + c, d0);
+        tmem_wait_ld();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) S[c + k] += __uint_as_float(d0[k]);
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&d_free[b]);
@@ -326,7 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // store the running sum: row = outer point ib + row of component x -> V[split][pq][x][il]
     const int row = quarter * 32 + lane;
     const int64_t il = static_cast<int64_t>(ib) + row;
-    const bool valid = ok && !*abort_flag && !ghost && il < args.n_i && n_it > 0;
+    const bool valid = ok && !*abort_flag && il < args.n_i && n_it > 0;
     if (valid) {
       float* Vz = args.V + static_cast<int64_t>(split) * args.n_pair * 3 * args.gcp;
       const int64_t col_off = static_cast<int64_t>(x) * args.gcp + il;
@@ -343,7 +295,6 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   tc_fence_before();
   __syncthreads();
-  if (CS > 1) cluster_sync_all();  // no CTA leaves while the others may still signal it
   if (warp == 0) {
     __syncwarp();
     tc_fence_after();
@@ -351,52 +302,27 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-template <int PARTS, int CM, int CN>
+template <int PARTS>
 void launch_t(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int splits,
               cudaStream_t st) {
-  auto kern = vfield_tc_kernel<PARTS, CM, CN>;
+  auto kern = vfield_tc_kernel<PARTS>;
   constexpr int smem = VfCfg<PARTS>::SMEM;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  const int MC = (3 * a.mt_per_x + CM - 1) / CM, NC = (a.n_tiles + CN - 1) / CN;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(static_cast<unsigned>(MC * NC * CM * CN), static_cast<unsigned>(splits), 1);
-  cfg.blockDim = dim3(THREADS, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CM * CN;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, *tm_g, *tm_rho, a);
-}
-
-template <int PARTS>
-void launch_p(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int splits, cudaStream_t st) {
-  switch (a.cluster) {
-    case 11: launch_t<PARTS, 1, 1>(tm_g, tm_rho, a, splits, st); break;
-    case 21: launch_t<PARTS, 2, 1>(tm_g, tm_rho, a, splits, st); break;
-    case 12: launch_t<PARTS, 1, 2>(tm_g, tm_rho, a, splits, st); break;
-    case 41: launch_t<PARTS, 4, 1>(tm_g, tm_rho, a, splits, st); break;
-    case 42: launch_t<PARTS, 4, 2>(tm_g, tm_rho, a, splits, st); break;
-    default: launch_t<PARTS, 2, 2>(tm_g, tm_rho, a, splits, st); break;
-  }
+  dim3 grid(static_cast<unsigned>(3 * a.mt_per_x * a.n_tiles), static_cast<unsigned>(splits));
+  kern<<<grid, THREADS, smem, st>>>(*tm_g, *tm_rho, a);
 }
 
 }  // namespace
 
 bool vfield_tc_supported(int n_nuc) { return n_nuc >= 1 && n_nuc <= 4; }
-bool vfield_cluster_valid(int c) { return c == 11 || c == 21 || c == 12 || c == 22 || c == 41 || c == 42; }
 
 void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int parts,
                       int splits, cudaStream_t st) {
   if (a.mt_per_x <= 0 || a.n_tiles <= 0 || splits <= 0) return;
   if (parts == 2)
-    launch_p<2>(tm_g, tm_rho, a, splits, st);
+    launch_t<2>(tm_g, tm_rho, a, splits, st);
   else
-    launch_p<3>(tm_g, tm_rho, a, splits, st);
+    launch_t<3>(tm_g, tm_rho, a, splits, st);
 }
 
 }  // namespace xtc

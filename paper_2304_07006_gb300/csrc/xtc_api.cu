@@ -72,7 +72,6 @@ struct xtc_ctx {
   int64_t launches[XTC_N_KERNELS] = {0};
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   int vf_kd = 2;  // K-blocks per tensor-core accumulation range in step (b)
-  int vf_cluster = 11;  // step (b) cluster shape 10 * CM + CN (1 x 1: no multicast)
   int as_kd = 2;  // the same for step (d)
 };
 
@@ -301,8 +300,6 @@ int xtc_create(xtc_ctx** out, const xtc_params* p) {
   }
   ctx->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   if (const char* s = std::getenv("XTC_VF_KD")) ctx->vf_kd = std::max(1, std::atoi(s));
-  if (const char* s = std::getenv("XTC_VF_CLUSTER"))
-    if (vfield_cluster_valid(std::atoi(s))) ctx->vf_cluster = std::atoi(s);
   if (const char* s = std::getenv("XTC_AS_KD")) ctx->as_kd = std::max(1, std::atoi(s));
   if (!ensure(ctx->jp_dev, sizeof(JastrowParams)) || !ensure(ctx->err_dev, 16) || !ensure(ctx->flag_dev, 16)) {
     xtc_destroy(ctx);
@@ -563,7 +560,6 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   a.n_kb = n_kb;
   a.kb_per_split = (a.n_kb + pl.splits - 1) / pl.splits;
   a.kd = std::min(ctx->vf_kd, pl.parts_b == 2 ? 4 : 2);
-  a.cluster = ctx->vf_cluster;
   a.unscale_g = std::ldexp(1.0f, -sg);
   a.err = ctx->err_dev.as<int>();
   const int splits = (a.n_kb + a.kb_per_split - 1) / a.kb_per_split;  // every slice non-empty
@@ -798,7 +794,6 @@ bool xtc_internal_ctx_view(const xtc_ctx* ctx, xtc::CtxView* v) {
   v->n_nuc = ctx->jp.n_nuc;
   v->g_bound = ctx->g_bound;
   v->vf_kd = ctx->vf_kd;
-  v->vf_cluster = ctx->vf_cluster;
   v->jp_dev = ctx->jp_dev.as<JastrowParams>();
   v->encode_tiled = reinterpret_cast<void*>(ctx->encode);
   return true;

@@ -86,7 +86,7 @@ struct GfieldArgs {
 void launch_gfield(const CUtensorMap* tm_g_store, const GfieldArgs& a, int parts, cudaStream_t st);
 
 // Step (b), tensor cores.  V[z][pq][x][il] (FP32, il = i - i0 < gcp) for the outer points of the
-// chunk, from the G table (tm_g: box 32 x 128) and the split rho^T (tm_rho: box 32 x vf_bn(parts)).
+// chunk, from the G table (tm_g: box rows 128) and the split rho^T (tm_rho: box rows vf_bn(parts)).
 struct VfieldArgs {
   const int* colexp;           // per-pair exponent of the rho scaling (0 when unscaled)
   float* V;                    // output base
@@ -98,12 +98,9 @@ struct VfieldArgs {
   int kb_per_split, n_kb;      // inner K-blocks per split slice, total K-blocks
   int kd;                      // K-blocks per TMEM accumulation range (then added to the FP32 running sum)
   float unscale_g;             // 2^-sG
-  int cluster;                 // cluster shape 10 * CM + CN (11, 21, 12, 22, 41, 42); CM tiles along
-                               // the rows share B tiles, CN along the columns share A tiles
   int* err;
 };
 bool vfield_tc_supported(int n_nuc);
-bool vfield_cluster_valid(int cluster);
 void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int parts,
                       int splits, cudaStream_t st);
 
@@ -169,7 +166,6 @@ struct CtxView {
   int n_nuc;
   double g_bound;
   int vf_kd;
-  int vf_cluster;
   const JastrowParams* jp_dev;
   void* encode_tiled;  // PFN_cuTensorMapEncodeTiled_v12000
 };
