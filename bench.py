@@ -146,6 +146,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ncu_case(args):
+    """A small, quick build (same workload, outer sum restricted to P points) for kernel captures."""
+    import synth
+    from paper_2304_07006_gb300 import Context
+
+    p = synth.make_config(WORKLOAD)
+    with Context(args.precision) as c:
+        c.set_jastrow(p.nuc_xyz, p.nuc_set, p.terms, p.coef)
+        c.set_outer_range(0, args.ncu_case)
+        for _ in range(2):
+            out = c.build(p.grid, p.weights, p.phi, p.gamma, want_dU=False)
+    print(f"ncu case: {WORKLOAD}, {args.precision}, outer points [0, {args.ncu_case}), e0 {float(out['e0'][0]):.12e}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -156,10 +170,16 @@ def main():
     ap.add_argument("--fp64-sample", type=int, default=512, help="outer points for the FP64 GPU comparison")
     ap.add_argument("--cpu-sample", type=int, default=4, help="outer points for the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--ncu-case", type=int, default=0, metavar="P",
+                    help="profiling aid: run one warm-up and one build of the workload restricted to the first P "
+                         "outer points, print a one-line summary and exit (no benchmark line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.ncu_case > 0:
+        run_ncu_case(args)
         return
 
     import torch
