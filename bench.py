@@ -10,7 +10,7 @@ divided by the device time of one build (inputs resident in HBM).  The per-step 
 (pair-product tables of several GB) is far larger than L2, so no flush is needed between steps.
 
 Also reported: the same metric end to end through the C ABI with host buffers (``e2e``), the
-roofline of the dominant kernel (steps a+b on the tensor cores), the FP64 GPU path timed on
+roofline of the dominant kernel (step b on the tensor cores), the FP64 GPU path timed on
 sampled outer points (time is linear in the outer sum) with the mixed/FP64 speed ratio, the
 mixed-vs-FP64 error in Hartree on those points, and the CPU oracle timed on a bounded sample.
 
@@ -96,6 +96,12 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one vfield_tc_kernel<2> launch on the first 1184
+# outer points of the workload (profiles/vfield_tc_n2.md); valid for that kernel version only
+VFIELD_DRAM_BYTES_CAPTURED = 15.914727e9 + 0.100698e9
+VFIELD_CAPTURE_OUTER = 1184
 
 
 def measured_peaks():
@@ -240,7 +246,7 @@ def main():
     ms_step = ms_total / args.steps
     value = world * F["total"] / (ms_step * 1e-3) / 1e12
 
-    # roofline of the dominant kernel: steps (a)+(b), per-launch algorithmic flops / mean launch time
+    # roofline of the dominant kernel: step (b), per-launch algorithmic flops / mean launch time
     per_kernel = {name: {"ms_per_step": kern_ms[k] / args.steps, "launches_per_step": int(kern_n[k] // args.steps)}
                   for k, name in enumerate(KERNEL_NAMES)}
     n_vf = kern_n[1] / args.steps
@@ -250,9 +256,14 @@ def main():
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     achieved = vf_flops_launch / (vf_ms * 1e-3) / 1e12
     issued_factor = 3 if args.precision == "fp16x2" else 6
-    roofline = {"kernel": "vfield (steps a+b, tcgen05 split-precision GEMM with fused Jastrow gradient)",
+    # DRAM bytes of the step (b) kernel from the ncu capture in profiles/vfield_tc_n2.md (fp16x2,
+    # 1184 outer points), scaled by the outer points of a launch (traffic grows with the row tiles)
+    traffic = None
+    if args.precision == "fp16x2":
+        traffic = VFIELD_DRAM_BYTES_CAPTURED * (NG / n_vf) / VFIELD_CAPTURE_OUTER
+    roofline = {"kernel": "vfield_tc (step b: tcgen05 split-fp16 GEMM V = G rho^T)",
                 "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{peak_src} bf16 dense sustained (fp16 nominal ratio 1:1)",
                 "issued_tflops": achieved * issued_factor,
                 "issued_frac": achieved * issued_factor / peak,

@@ -4,12 +4,15 @@
 // k = (outer point, component); Delta U = -(M + M^T) is formed by the final kernels.
 //
 // CTA tile 128 x 128, 32-element K stages with both operands TMA-loaded in the 64-byte swizzle,
-// three bf16 parts per operand and six split products (i + j <= 2, smallest first).  Warp 0 issues the TMA
-// loads, warp 1 the MMAs into one of two TMEM accumulators; every `kd` stages warps 2..5 add the
-// finished accumulator into a compensated FP32 running sum (sum and error term, Knuth's TwoSum,
-// both in TMEM) while the MMA fills the other one, which keeps the tensor-core accumulation
-// (truncating at each MMA) to short ranges.  At the end warps 2..5 add sum + error into the
-// FP64 accumulator M in HBM (read-modify-write; every tile of M is owned by exactly one CTA).
+// three bf16 parts per operand and six split products (i + j <= 2, smallest first).  Warp 0 issues
+// the TMA loads, warp 1 the MMAs into one of two TMEM accumulators; every `kd` stages warps 2..5
+// add the finished accumulator into a compensated FP32 running sum (sum and error term, Knuth's
+// TwoSum, both in TMEM) while the MMA fills the other one, which keeps the tensor-core
+// accumulation (truncating at each MMA) to short ranges.  A tcgen05.commit stalls the tensor pipe
+// for a few hundred cycles, so each range ends with one commit, whose arrival both frees the
+// range's stage slots (the TMA producer counts finished ranges in order) and starts the drain.
+// At the end warps 2..5 add sum + error into the FP64 accumulator M in HBM (read-modify-write;
+// every tile of M is owned by exactly one CTA).
 #include "ptx_sm100.cuh"
 #include "xtc_internal.cuh"
 
@@ -27,6 +30,10 @@ constexpr int THREADS = 192;
 constexpr int DRAIN_WARPS = 4;
 constexpr uint32_t S_COL = 2 * AS_BN;  // running sum
 constexpr uint32_t C_COL = 3 * AS_BN;  // its rounding-error term
+constexpr int NRB = 8;                 // range barriers (range r uses r % NRB)
+// a wait for range r must not alias range r + NRB (the producer waits for the range of stage
+// k - STAGES before loading stage k)
+static_assert(NRB > STAGES, "range barriers");
 
 __device__ __forceinline__ void tmem_st_32x32b_x32(uint32_t taddr, const uint32_t (&r)[32]) {
   asm volatile(
@@ -47,12 +54,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  uint64_t* full = bars;                     // [STAGES]
-  uint64_t* empty = bars + STAGES;           // [STAGES]
-  uint64_t* d_full = bars + 2 * STAGES;      // [2]
-  uint64_t* d_free = bars + 2 * STAGES + 2;  // [2]
-  uint64_t* fin_bar = bars + 2 * STAGES + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  uint64_t* full = bars;                     // [STAGES] the stage's loads landed
+  uint64_t* rdone = bars + STAGES;           // [NRB] the MMAs of range r (r % NRB) completed
+  uint64_t* d_free = bars + STAGES + NRB;    // [2] the drains released accumulator b
+  uint64_t* fin_bar = bars + STAGES + NRB + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + STAGES + NRB + 3);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -60,14 +66,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int n_ranges = (n_kb + kd - 1) / kd;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&d_full[b], 1);
-      mbar_init(&d_free[b], DRAIN_WARPS);
-    }
+    for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+    for (int r = 0; r < NRB; ++r) mbar_init(&rdone[r], 1);
+    for (int b = 0; b < 2; ++b) mbar_init(&d_free[b], DRAIN_WARPS);
     mbar_init(fin_bar, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -86,10 +87,17 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
+      int seen = 0;  // ranges known to have completed (their slots are free again)
       int issued_end = 0;
       for (int kb = 0; kb < n_kb; ++kb) {
-        const int s = kb % STAGES, n = kb / STAGES;
-        if (n > 0 && !mbar_wait(&empty[s], (n - 1) & 1, abort_flag, err, DEV_ERR_TIMEOUT_AS)) break;
+        const int s = kb % STAGES;
+        if (kb >= STAGES) {
+          const int need = (kb - STAGES) / kd;  // range holding the slot's previous stage
+          bool ok = true;
+          for (; seen <= need && ok; ++seen)
+            ok = mbar_wait(&rdone[seen % NRB], (seen / NRB) & 1, abort_flag, err, DEV_ERR_TIMEOUT_AS);
+          if (!ok) break;
+        }
         mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
         uint8_t* st = smem + s * STAGE_BYTES;
         for (int p = 0; p < PARTS; ++p) {
@@ -115,12 +123,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int kb0 = r * kd, kb1 = min(n_kb, kb0 + kd);
         const int b = r & 1, u = r >> 1;
         if (u >= 1 && !mbar_wait(&d_free[b], (u - 1) & 1, abort_flag, err, DEV_ERR_TIMEOUT_AS)) break;
-        for (int kb = kb0; kb < kb1 && alive; ++kb)
-          alive = mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, abort_flag, err, DEV_ERR_TIMEOUT_AS);
-        if (!alive) break;
-        tc_fence_after();
-        for (int pass = 0; pass < 2; ++pass) {
+        // cross products of each stage as it lands, then the hi x hi products of the range
+        for (int pass = 0; pass < 2 && alive; ++pass) {
           for (int kb = kb0; kb < kb1; ++kb) {
+            if (pass == 0) {
+              if (!(alive = mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, abort_flag, err, DEV_ERR_TIMEOUT_AS)))
+                break;
+              tc_fence_after();
+            }
             const uint32_t sa = smem_base + (kb % STAGES) * STAGE_BYTES;
             const uint32_t sb = sa + PARTS * A_TILE;
 #pragma unroll
@@ -135,8 +145,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
           }
         }
-        for (int kb = kb0; kb < kb1; ++kb) tc_commit(&empty[kb % STAGES]);
-        tc_commit(&d_full[b]);
+        if (!alive) break;
+        tc_commit(&rdone[r % NRB]);
       }
       tc_commit(fin_bar);
       int zero = 0;
@@ -147,8 +157,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
     bool ok = true;
     for (int r = 0; r < n_ranges && ok; ++r) {
-      const int b = r & 1, u = r >> 1;
-      ok = __all_sync(0xffffffffu, mbar_wait(&d_full[b], u & 1, abort_flag, err, DEV_ERR_TIMEOUT_AS));
+      const int b = r & 1;
+      ok = __all_sync(0xffffffffu, mbar_wait(&rdone[r % NRB], (r / NRB) & 1, abort_flag, err, DEV_ERR_TIMEOUT_AS));
       __syncwarp();
       if (!ok) break;
       tc_fence_after();
