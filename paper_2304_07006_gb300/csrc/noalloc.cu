@@ -210,6 +210,8 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
       VfieldArgs a{};
       a.colexp = colexp;
       a.V = static_cast<float*>(Vbuf);
+      a.Vacc = nullptr;
+      a.flush = 0;  // FP32 running sums only: the fixed scratch has no room for FP64 tiles
       a.n_i = n_i;
       a.gcp = gc;
       a.mt_per_x = mt_per_x;

@@ -25,7 +25,10 @@
 // The tensor-core accumulator truncates toward zero at each MMA, which biases a long inner sum.
 // Each range is short (default two stages), its MMAs issue the small cross products of all its
 // stages first so that only the hi x hi products meet a large accumulator, and the ranges are
-// summed with round-to-nearest FP32 adds.
+// summed with round-to-nearest FP32 adds.  Rounding of that FP32 sum grows with the number of
+// ranges, so every `flush` ranges the drains add their FP32 partial sums into an FP64 accumulator
+// in HBM, private to the CTA and column-major in its tile (each element belongs to one thread:
+// plain read-modify-write, coalesced over the 32 rows of a warp); the final sum is written as V.
 // Tiles are ordered in groups of GM row tiles so that the CTAs resident at one time share their A
 // and B panels in L2.
 #include "ptx_sm100.cuh"
@@ -83,6 +86,10 @@ __device__ __forceinline__ void prod_parts(int p, int& pa, int& pb) {
     pa = a[p];
     pb = b[p];
   }
+}
+
+__device__ __forceinline__ void red_add_f64(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
 
 // 32 lanes x 16 consecutive 32-bit columns: thread t of the warp receives lane (base + t).
@@ -242,6 +249,25 @@ __global__ void __launch_bounds__(THREADS, 1)
     float S[HC];
 #pragma unroll
     for (int k = 0; k < HC; ++k) S[k] = 0.0f;
+    // Adds the running sums into this thread's elements of the CTA-private FP64 accumulator,
+    // column-major in the tile: Vacc[(split * gridDim.x + tile) * 128 * BN + column * 128 + row],
+    // column = c_base + k (a store the first time, then fire-and-forget reductions, which need
+    // no result registers), and clears them.
+    int nflush = 0;
+    auto flush_sums = [&]() {
+      double* acc = args.Vacc + (static_cast<int64_t>(split) * gridDim.x + blockIdx.x) * VF_BM * BN +
+                    static_cast<int64_t>(c_base) * VF_BM + quarter * 32 + lane;
+      if (nflush == 0) {
+#pragma unroll
+        for (int k = 0; k < HC; ++k) acc[k * VF_BM] = static_cast<double>(S[k]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < HC; ++k) red_add_f64(acc + k * VF_BM, static_cast<double>(S[k]));
+      }
+#pragma unroll
+      for (int k = 0; k < HC; ++k) S[k] = 0.0f;
+      ++nflush;
+    };
     bool ok = true;
     for (int r = 0; r < n_ranges && ok; ++r) {
       const int b = r & 1;
@@ -252,19 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       tc_fence_after();
       const uint32_t src = tmem + lane_base + b * BN + c_base;
 #pragma unroll
-      for (int c = 0; c + 32 <= HC; c += 32) {
-        uint32_t d0[16], d1[16];
-        tmem_ld_x16(src + c, d0);
-        tmem_ld_x16(src + c + 16, d1);
-        tmem_wait_ld();
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          S[c + k] += __uint_as_float(d0[k]);
-          S[c + 16 + k] += __uint_as_float(d1[k]);
-        }
-      }
-      if constexpr (HC % 32 != 0) {  // last 16 columns
-        constexpr int c = HC - 16;
+      for (int c = 0; c < HC; c += 16) {
         uint32_t d0[16];
         tmem_ld_x16(src + c, d0);
         tmem_wait_ld();
@@ -274,21 +288,27 @@ __global__ void __launch_bounds__(THREADS, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&d_free[b]);
+      // FP64 flush of the partial sums (the accumulator is already handed back to the MMA)
+      if (args.flush > 0 && (r + 1) % args.flush == 0) flush_sums();
     }
-    // store the running sum: row = outer point ib + row of component x -> V[split][pq][x][il]
-    const int row = quarter * 32 + lane;
-    const int64_t il = static_cast<int64_t>(ib) + row;
-    const bool valid = ok && !*abort_flag && il < args.n_i && n_it > 0;
-    if (valid) {
-      float* Vz = args.V + static_cast<int64_t>(split) * args.n_pair * 3 * args.gcp;
+    if (args.flush > 0) {
+      // the remaining sums join the FP64 accumulator; vfield_finalize_kernel writes V from it
+      if (ok && n_ranges % args.flush != 0) flush_sums();
+    } else {
+      // FP32 sums straight to V: row = outer point ib + row of component x -> V[split][pq][x][il]
+      const int row = quarter * 32 + lane;
+      const int64_t il = static_cast<int64_t>(ib) + row;
       const int64_t col_off = static_cast<int64_t>(x) * args.gcp + il;
       const int pq0 = n_tile * BN + static_cast<int>(c_base);
+      if (ok && !*abort_flag && il < args.n_i && n_it > 0) {
+        float* Vz = args.V + static_cast<int64_t>(split) * args.n_pair * 3 * args.gcp;
 #pragma unroll
-      for (int k = 0; k < HC; ++k) {
-        const int pq = pq0 + k;
-        if (pq < args.n_pair)
-          Vz[static_cast<int64_t>(pq) * 3 * args.gcp + col_off] =
-              ldexpf(S[k] * args.unscale_g, -__ldg(args.colexp + pq));
+        for (int k = 0; k < HC; ++k) {
+          const int pq = pq0 + k;
+          if (pq < args.n_pair)
+            Vz[static_cast<int64_t>(pq) * 3 * args.gcp + col_off] =
+                ldexpf(S[k] * args.unscale_g, -__ldg(args.colexp + pq));
+        }
       }
     }
   }
@@ -302,6 +322,31 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// V from the FP64 accumulator of the GEMM: one CTA per (tile, split), thread = tile row; the tile
+// order is the GEMM's grouped order.
+template <int BN>
+__global__ void __launch_bounds__(VF_BM) vfield_finalize_kernel(const VfieldArgs args) {
+  const int m_tiles = 3 * args.mt_per_x;
+  const int L = blockIdx.x;
+  const int group = L / (GM * args.n_tiles);
+  const int first_m = group * GM;
+  const int gm = min(GM, m_tiles - first_m);
+  const int rem = L - group * GM * args.n_tiles;
+  const int m_tile = first_m + rem % gm, n_tile = rem / gm;
+  const int x = m_tile / args.mt_per_x;
+  const int row = threadIdx.x;
+  const int64_t il = static_cast<int64_t>(m_tile - x * args.mt_per_x) * VF_BM + row;
+  if (il >= args.n_i) return;
+  const double* acc = args.Vacc + (static_cast<int64_t>(blockIdx.y) * gridDim.x + L) * VF_BM * BN + row;
+  float* v = args.V + static_cast<int64_t>(blockIdx.y) * args.n_pair * 3 * args.gcp + x * args.gcp + il;
+  const int ncol = min(BN, args.n_pair - n_tile * BN);
+  for (int c = 0; c < ncol; ++c) {
+    const int pq = n_tile * BN + c;
+    v[static_cast<int64_t>(pq) * 3 * args.gcp] =
+        ldexpf(static_cast<float>(acc[static_cast<int64_t>(c) * VF_BM]) * args.unscale_g, -__ldg(args.colexp + pq));
+  }
+}
+
 template <int PARTS>
 void launch_t(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int splits,
               cudaStream_t st) {
@@ -310,6 +355,7 @@ void launch_t(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldAr
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   dim3 grid(static_cast<unsigned>(3 * a.mt_per_x * a.n_tiles), static_cast<unsigned>(splits));
   kern<<<grid, THREADS, smem, st>>>(*tm_g, *tm_rho, a);
+  if (a.flush > 0) vfield_finalize_kernel<VfCfg<PARTS>::BN><<<grid, VF_BM, 0, st>>>(a);
 }
 
 }  // namespace

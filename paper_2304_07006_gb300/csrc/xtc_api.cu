@@ -61,7 +61,7 @@ struct xtc_ctx {
   DBuf jp_dev, err_dev, flag_dev;
   DBuf grid, w, phi, gamma, phiT, pair_p, pair_q;
   DBuf jtab, jtab64, rho, colmax, colexp, G;
-  DBuf V, L, R, M, evec, lam, dU_tmp, dh_tmp, e0_tmp, vout, r1, r2;
+  DBuf V, Vacc, L, R, M, evec, lam, dU_tmp, dh_tmp, e0_tmp, vout, r1, r2;
   // prepared state key (pair tables)
   int pair_n = -1;
   // timers
@@ -72,6 +72,7 @@ struct xtc_ctx {
   int64_t launches[XTC_N_KERNELS] = {0};
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   int vf_kd = 2;  // K-blocks per tensor-core accumulation range in step (b)
+  int vf_flush = 128;  // step (b) ranges between FP64 flushes of the running sums (0: FP32 only)
   int as_kd = 2;  // the same for step (d)
 };
 
@@ -301,6 +302,7 @@ int xtc_create(xtc_ctx** out, const xtc_params* p) {
   ctx->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   if (const char* s = std::getenv("XTC_VF_KD")) ctx->vf_kd = std::max(1, std::atoi(s));
   if (const char* s = std::getenv("XTC_AS_KD")) ctx->as_kd = std::max(1, std::atoi(s));
+  if (const char* s = std::getenv("XTC_VF_FLUSH")) ctx->vf_flush = std::max(0, std::atoi(s));
   if (!ensure(ctx->jp_dev, sizeof(JastrowParams)) || !ensure(ctx->err_dev, 16) || !ensure(ctx->flag_dev, 16)) {
     xtc_destroy(ctx);
     return XTC_ERR_OOM;
@@ -494,6 +496,11 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
   if (!f64) {
     const size_t gbytes = 2ull * pl.parts_b * 3 * pl.gc * pl.NGp;
     if (!ensure(ctx->G, gbytes)) return fail(ctx, XTC_ERR_OOM, "gradient table (%.2f GB)", gbytes / 1e9);
+    // FP64 partial sums of step (b): one 128 x vf_bn tile per CTA and split slice
+    const int bn = vf_bn(pl.parts_b);
+    const size_t tiles = 3ull * ((pl.gc + VF_BM - 1) / VF_BM) * ((pl.NP + bn - 1) / bn);
+    const size_t abytes = ctx->vf_flush > 0 ? 8ull * pl.splits * tiles * VF_BM * bn : 0;
+    if (!ensure(ctx->Vacc, abytes)) return fail(ctx, XTC_ERR_OOM, "step (b) FP64 sums (%.2f GB)", abytes / 1e9);
   }
   return XTC_OK;
 }
@@ -552,6 +559,8 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   VfieldArgs a{};
   a.colexp = ctx->colexp.as<int>();
   a.V = ctx->V.as<float>();
+  a.Vacc = ctx->Vacc.as<double>();
+  a.flush = ctx->vf_flush;
   a.n_i = n_i;
   a.gcp = pl.gc;
   a.mt_per_x = mt_per_x;
@@ -563,7 +572,9 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   a.unscale_g = std::ldexp(1.0f, -sg);
   a.err = ctx->err_dev.as<int>();
   const int splits = (a.n_kb + a.kb_per_split - 1) / a.kb_per_split;  // every slice non-empty
-  timed(ctx, XTC_K_VFIELD, 1, [&] { launch_vfield_tc(&maps.g_load, &maps.rho, a, pl.parts_b, splits, st); });
+  // the GEMM, then (FP64 flushes) the kernel that writes V from the FP64 sums
+  timed(ctx, XTC_K_VFIELD, a.flush > 0 ? 2 : 1,
+        [&] { launch_vfield_tc(&maps.g_load, &maps.rho, a, pl.parts_b, splits, st); });
   return XTC_OK;
 }
 

@@ -90,6 +90,8 @@ void launch_gfield(const CUtensorMap* tm_g_store, const GfieldArgs& a, int parts
 struct VfieldArgs {
   const int* colexp;           // per-pair exponent of the rho scaling (0 when unscaled)
   float* V;                    // output base
+  double* Vacc;                // FP64 partial sums, [splits][grid CTAs][BN][128] (used when flush > 0)
+  int flush;                   // ranges summed in FP32 registers between FP64 flushes (0: no flush)
   int64_t n_i;                 // outer points of this chunk
   int64_t gcp;                 // padded chunk length (row stride of V and of G per component)
   int mt_per_x;                // 128-row tiles per component: ceil(n_i / 128)
@@ -101,6 +103,7 @@ struct VfieldArgs {
   int* err;
 };
 bool vfield_tc_supported(int n_nuc);
+// Launches the GEMM and, when a.flush > 0, the kernel that writes V from the FP64 sums.
 void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int parts,
                       int splits, cudaStream_t st);
 
