@@ -100,7 +100,7 @@ class Clocks:
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one vfield_tc_kernel<2> launch on the first 1184
 # outer points of the workload (profiles/vfield_tc_n2.md); valid for that kernel version only
-VFIELD_DRAM_BYTES_CAPTURED = 15.914727e9 + 0.100698e9
+VFIELD_DRAM_BYTES_CAPTURED = None  # re-captured after the FP64-flush change
 VFIELD_CAPTURE_OUTER = 1184
 
 
@@ -249,8 +249,10 @@ def main():
     # roofline of the dominant kernel: step (b), per-launch algorithmic flops / mean launch time
     per_kernel = {name: {"ms_per_step": kern_ms[k] / args.steps, "launches_per_step": int(kern_n[k] // args.steps)}
                   for k, name in enumerate(KERNEL_NAMES)}
-    n_vf = kern_n[1] / args.steps
-    vf_ms = kern_ms[1] / max(kern_n[1], 1)
+    # one gradient-table launch per chunk; step (b) = GEMM (+ the kernel writing V from the FP64
+    # sums), step (d) = row splits + GEMM + the kernel adding into M (fp16x2) or one GEMM (bf16x3)
+    n_vf = kern_n[KERNEL_NAMES.index("grad")] / args.steps
+    vf_ms = kern_ms[1] / args.steps / n_vf
     vf_flops_launch = F["b"] / n_vf
     peaks, peak_src = measured_peaks()
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
@@ -259,7 +261,7 @@ def main():
     # DRAM bytes of the step (b) kernel from the ncu capture in profiles/vfield_tc_n2.md (fp16x2,
     # 1184 outer points), scaled by the outer points of a launch (traffic grows with the row tiles)
     traffic = None
-    if args.precision == "fp16x2":
+    if args.precision == "fp16x2" and VFIELD_DRAM_BYTES_CAPTURED:
         traffic = VFIELD_DRAM_BYTES_CAPTURED * (NG / n_vf) / VFIELD_CAPTURE_OUTER
     roofline = {"kernel": "vfield_tc (step b: tcgen05 split-fp16 GEMM V = G rho^T)",
                 "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -267,17 +269,19 @@ def main():
                 "peak_source": f"{peak_src} bf16 dense sustained (fp16 nominal ratio 1:1)",
                 "issued_tflops": achieved * issued_factor,
                 "issued_frac": achieved * issued_factor / peak,
-                "launch_ms": vf_ms, "algorithmic_flops_per_launch": vf_flops_launch}
-    asm_ms = kern_ms[3] / max(kern_n[3], 1)
-    asm_ach = F["d"] / (kern_n[3] / args.steps) / (asm_ms * 1e-3) / 1e12
-    assemble = {"bound": "tensor", "achieved": asm_ach, "issued_tflops": asm_ach * 6, "frac": asm_ach / peak,
-                "issued_frac": asm_ach * 6 / peak, "launch_ms": asm_ms}
+                "ms_per_chunk": vf_ms, "algorithmic_flops_per_chunk": vf_flops_launch}
+    asm_ms = kern_ms[3] / args.steps / n_vf
+    asm_ach = F["d"] / n_vf / (asm_ms * 1e-3) / 1e12
+    asm_factor = 3 if args.precision == "fp16x2" else 6
+    assemble = {"kernel": "step d per chunk (fp16x2: row splits + vfield_tc GEMM in mode 1 + add into M)",
+                "bound": "tensor", "achieved": asm_ach, "issued_tflops": asm_ach * asm_factor,
+                "frac": asm_ach / peak, "issued_frac": asm_ach * asm_factor / peak, "ms_per_chunk": asm_ms}
 
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "seconds_per_build": ms_step / 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16x2 split (steps a+b) / bf16x3 split (step d), f32 tensor accumulate, f64 chunk sums"
-            if args.precision == "fp16x2" else "bf16x3 split, f32 tensor accumulate, f64 chunk sums",
+            "dtype": "f16x2 split (steps b and d), f32 tensor accumulate, f64 flushes and chunk sums"
+            if args.precision == "fp16x2" else "bf16x3 split (steps b and d), f32 tensor accumulate, f64 sums",
             "data": "synthetic", "config": config_dict(p, args.precision),
             "parallelism": "replicas" if world > 1 else "single GPU",
             "algorithmic_flops_per_build": F, "roofline": roofline, "assemble_roofline": assemble,

@@ -236,8 +236,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 void launch_assemble_tc(const CUtensorMap* tm_L, const CUtensorMap* tm_R, int n_pair, int kdim, int kd, double* M,
                         int* err, cudaStream_t st) {
-  // M has row stride ldm = round_up(n_pair, AS_BN) so every 32-column group of a tile is in bounds
-  const int ldm = static_cast<int>(round_up(n_pair, AS_BN));
+  // M has row stride m_stride(n_pair) so every 32-column group of a tile is in bounds
+  const int ldm = static_cast<int>(m_stride(n_pair));
   cudaFuncSetAttribute(assemble_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
   dim3 grid((n_pair + AS_BM - 1) / AS_BM, (n_pair + AS_BN - 1) / AS_BN);
   assemble_tc_kernel<<<grid, THREADS, SMEM, st>>>(*tm_L, *tm_R, n_pair, ldm, kdim / AS_BK, kd, M, err);

@@ -136,6 +136,43 @@ __global__ void rho_split_kernel(const double* __restrict__ phiT, const double* 
   }
 }
 
+// One CTA per row of a step (d) operand: the row maximum sets a power-of-2 scale, then the scaled
+// row is split into fp16 hi + lo (see launch_lr_split).
+__global__ void __launch_bounds__(256) lr_split_kernel(const float* __restrict__ src, int64_t kdim,
+                                                       uint16_t* __restrict__ dst, int* __restrict__ exps) {
+  __shared__ float red[8];
+  const int64_t r = blockIdx.x;
+  const float* s = src + r * kdim;
+  float m = 0.0f;
+  for (int64_t k = threadIdx.x * 4; k < kdim; k += blockDim.x * 4) {
+    const float4 v = *reinterpret_cast<const float4*>(s + k);
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = red[0];
+  for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+  int e = 0;
+  if (m > 0.0f) {
+    int em;
+    frexpf(m, &em);  // m = f * 2^em, f in [0.5, 1)
+    e = min(max(14 - em, -100), 100);
+  }
+  if (threadIdx.x == 0) exps[r] = e;
+  uint16_t* d = dst + r * 2 * kdim;
+  for (int64_t k = threadIdx.x * 2; k < kdim; k += blockDim.x * 2) {
+    const float2 v = *reinterpret_cast<const float2*>(s + k);
+    const float a = ldexpf(v.x, e), b = ldexpf(v.y, e);
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    const int64_t o = (k >> 5) * 64 + (k & 31);
+    *reinterpret_cast<__half2*>(d + o) = h;
+    *reinterpret_cast<__half2*>(d + o + 32) = l;
+  }
+}
+
 __global__ void rho_f64_kernel(const double* __restrict__ phi, const double* __restrict__ w, int64_t n_grid,
                                int64_t n_pad, int N, int n_pair, const int* __restrict__ pp,
                                const int* __restrict__ pq_, double* __restrict__ rho) {
@@ -449,6 +486,11 @@ void launch_rho_split(const double* phiT, const double* w, int64_t n_grid, int64
   (void)bf16;
 }
 
+void launch_lr_split(const float* src, int rows, int64_t kdim, uint16_t* dst, int* exps, cudaStream_t st) {
+  if (rows <= 0) return;
+  lr_split_kernel<<<rows, 256, 0, st>>>(src, kdim, dst, exps);
+}
+
 void launch_rho_f64(const double* phi, const double* w, int64_t n_grid, int64_t n_pad, int n_orb, const int* pp,
                     const int* pq, double* rho, cudaStream_t st) {
   const int n_pair = n_orb * (n_orb + 1) / 2;
@@ -476,13 +518,13 @@ void launch_vfield_f64_impl(const double* grid, const JastrowParams* jp, int n_n
 }
 
 void launch_assemble_f64(const double* L, const double* R, int n_pair, int kdim, double* M, cudaStream_t st) {
-  const int ldm = static_cast<int>(round_up(n_pair, AS_BN));
+  const int ldm = static_cast<int>(m_stride(n_pair));
   dim3 g(blocks_for(n_pair, 64), blocks_for(n_pair, 64));
   assemble_f64_kernel<<<g, 256, 0, st>>>(L, R, n_pair, kdim, ldm, M);
 }
 
 void launch_unpack(const double* M, int n_orb, int n_pair, double* dU, float* dU32, cudaStream_t st) {
-  const int ldm = static_cast<int>(round_up(n_pair, AS_BN));
+  const int ldm = static_cast<int>(m_stride(n_pair));
   if (dU || dU32) {
     dim3 g(static_cast<unsigned int>(n_orb) * n_orb, blocks_for(static_cast<int64_t>(n_orb) * n_orb, 256));
     unpack_kernel<<<g, 256, 0, st>>>(M, n_orb, ldm, dU, dU32);
@@ -490,14 +532,14 @@ void launch_unpack(const double* M, int n_orb, int n_pair, double* dU, float* dU
 }
 
 void launch_symmetrize(double* M, int n_pair, cudaStream_t st) {
-  const int ldm = static_cast<int>(round_up(n_pair, AS_BN));
+  const int ldm = static_cast<int>(m_stride(n_pair));
   dim3 g(blocks_for(n_pair, 32), blocks_for(n_pair, 32));
   symmetrize_kernel<<<g, dim3(32, 8), 0, st>>>(M, n_pair, ldm);
 }
 
 void launch_onebody(const double* M, const double* gamma, int n_orb, int n_pair, double* dh, double* e0,
                     cudaStream_t st) {
-  const int ldm = static_cast<int>(round_up(n_pair, AS_BN));
+  const int ldm = static_cast<int>(m_stride(n_pair));
   onebody_kernel<<<dim3(n_orb, n_orb), 256, 0, st>>>(M, gamma, n_orb, ldm, dh);
   constant_kernel<<<1, 256, 0, st>>>(dh, gamma, n_orb * n_orb, e0);
 }

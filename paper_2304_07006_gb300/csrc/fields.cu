@@ -82,6 +82,11 @@ __device__ __forceinline__ void write4(void* base, int64_t n_pair, int64_t gcp, 
     double* o = static_cast<double*>(base);
 #pragma unroll
     for (int c = 0; c < 4; ++c) o[(4 * il + c) * n_pair + q] = static_cast<double>(v[c]);
+  } else if (OUT_PARTS == 1) {
+    // FP32 rows [pq][4*gcp] (split afterwards with a per-row scale)
+    float* o = static_cast<float*>(base) + static_cast<int64_t>(q) * 4 * gcp + 4 * il;
+    *reinterpret_cast<float4*>(o) = make_float4(static_cast<float>(v[0]), static_cast<float>(v[1]),
+                                                static_cast<float>(v[2]), static_cast<float>(v[3]));
   } else {
     __nv_bfloat16* o = static_cast<__nv_bfloat16*>(base);
     __nv_bfloat16 h[4], m[4], l[4];
@@ -248,6 +253,8 @@ size_t fields_smem_bytes(int n_orb, int rank, int pts, bool f64) {
 void launch_fields(const FieldsArgs& a, bool f64, cudaStream_t st) {
   if (f64)
     launch_t<double, double, 0>(a, st);
+  else if (a.out_parts == 1)
+    launch_t<float, float, 1>(a, st);
   else
     launch_t<float, float, 3>(a, st);
 }

@@ -31,6 +31,11 @@
 // plain read-modify-write, coalesced over the 32 rows of a warp); the final sum is written as V.
 // Tiles are ordered in groups of GM row tiles so that the CTAs resident at one time share their A
 // and B panels in L2.
+//
+// The same engine runs step (d) for the fp16 x2 precision (MODE 1): M += L^T R with A = the split
+// rows L[pq] (rho, V) and B = the split rows R[rs] (A, B) of a chunk, K = 4 x chunk points, each
+// row carrying its own power-of-2 scale; its tile-private FP64 sums are then added into M[pq][rs],
+// unscaled, by assemble_finalize_kernel.
 #include "ptx_sm100.cuh"
 #include "xtc_internal.cuh"
 
@@ -103,7 +108,7 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
       : "memory");
 }
 
-template <int PARTS>
+template <int PARTS, int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
     vfield_tc_kernel(const __grid_constant__ CUtensorMap tm_g, const __grid_constant__ CUtensorMap tm_rho,
                      const VfieldArgs args) {
@@ -123,16 +128,17 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // grouped tile order: GM row tiles x every column tile, row tile fastest
-  const int m_tiles = 3 * args.mt_per_x;
+  const int m_tiles = MODE == 0 ? 3 * args.mt_per_x : (args.rows_a + VF_BM - 1) / VF_BM;
   const int L = blockIdx.x;
   const int group = L / (GM * args.n_tiles);
   const int first_m = group * GM;
   const int gm = min(GM, m_tiles - first_m);
   const int rem = L - group * GM * args.n_tiles;
   const int m_tile = first_m + rem % gm, n_tile = rem / gm;
-  const int x = m_tile / args.mt_per_x;
-  const int ib = (m_tile - x * args.mt_per_x) * VF_BM;  // first outer point (chunk-local) of the tile
-  const int row0 = static_cast<int>(x * args.gcp) + ib;
+  // mode 0: rows x * gcp + outer point of component x; mode 1: rows pq
+  const int x = MODE == 0 ? m_tile / args.mt_per_x : 0;
+  const int ib = MODE == 0 ? (m_tile - x * args.mt_per_x) * VF_BM : m_tile * VF_BM;
+  const int row0 = MODE == 0 ? static_cast<int>(x * args.gcp) + ib : ib;
   const int split = blockIdx.y;
   const int kb0 = split * args.kb_per_split;
   const int kb1 = min(args.n_kb, kb0 + args.kb_per_split);
@@ -292,7 +298,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (args.flush > 0 && (r + 1) % args.flush == 0) flush_sums();
     }
     if (args.flush > 0) {
-      // the remaining sums join the FP64 accumulator; vfield_finalize_kernel writes V from it
+      // the remaining sums join the FP64 accumulator; a finalize kernel writes V (mode 0) or adds
+      // the tile into M (mode 1)
       if (ok && n_ranges % args.flush != 0) flush_sums();
     } else {
       // FP32 sums straight to V: row = outer point ib + row of component x -> V[split][pq][x][il]
@@ -347,15 +354,41 @@ __global__ void __launch_bounds__(VF_BM) vfield_finalize_kernel(const VfieldArgs
   }
 }
 
-template <int PARTS>
+// M[pq][rs] += tile sum * 2^-(exp_a[pq] + exp_b[rs]) for one tile of the step (d) GEMM (mode 1);
+// one CTA per tile, thread = row pq, columns in order (coalesced tile reads; each M element is
+// owned by one tile).
+template <int BN>
+__global__ void __launch_bounds__(VF_BM) assemble_finalize_kernel(const VfieldArgs args) {
+  const int m_tiles = (args.rows_a + VF_BM - 1) / VF_BM;
+  const int L = blockIdx.x;
+  const int group = L / (GM * args.n_tiles);
+  const int first_m = group * GM;
+  const int gm = min(GM, m_tiles - first_m);
+  const int rem = L - group * GM * args.n_tiles;
+  const int m_tile = first_m + rem % gm, n_tile = rem / gm;
+  const int pq = m_tile * VF_BM + threadIdx.x;
+  if (pq >= args.rows_a) return;
+  const double* acc = args.Vacc + (static_cast<int64_t>(blockIdx.y) * gridDim.x + L) * VF_BM * BN + threadIdx.x;
+  double* m = args.M + static_cast<int64_t>(pq) * args.ldm + n_tile * BN;
+  const int ea = args.exp_a[pq];
+  const int ncol = min(BN, args.n_pair - n_tile * BN);
+  for (int c = 0; c < ncol; ++c) {
+    const int e = ea + __ldg(args.exp_b + n_tile * BN + c);
+    m[c] += acc[static_cast<int64_t>(c) * VF_BM] * __longlong_as_double(static_cast<long long>(1023 - e) << 52);
+  }
+}
+
+template <int PARTS, int MODE>
 void launch_t(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int splits,
               cudaStream_t st) {
-  auto kern = vfield_tc_kernel<PARTS>;
+  auto kern = vfield_tc_kernel<PARTS, MODE>;
   constexpr int smem = VfCfg<PARTS>::SMEM;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  dim3 grid(static_cast<unsigned>(3 * a.mt_per_x * a.n_tiles), static_cast<unsigned>(splits));
+  const int m_tiles = MODE == 0 ? 3 * a.mt_per_x : (a.rows_a + VF_BM - 1) / VF_BM;
+  dim3 grid(static_cast<unsigned>(m_tiles * a.n_tiles), static_cast<unsigned>(splits));
   kern<<<grid, THREADS, smem, st>>>(*tm_g, *tm_rho, a);
-  if (a.flush > 0) vfield_finalize_kernel<VfCfg<PARTS>::BN><<<grid, VF_BM, 0, st>>>(a);
+  if (MODE == 0 && a.flush > 0) vfield_finalize_kernel<VfCfg<PARTS>::BN><<<grid, VF_BM, 0, st>>>(a);
+  if (MODE == 1) assemble_finalize_kernel<VfCfg<PARTS>::BN><<<grid, VF_BM, 0, st>>>(a);
 }
 
 }  // namespace
@@ -364,11 +397,16 @@ bool vfield_tc_supported(int n_nuc) { return n_nuc >= 1 && n_nuc <= 4; }
 
 void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int parts,
                       int splits, cudaStream_t st) {
-  if (a.mt_per_x <= 0 || a.n_tiles <= 0 || splits <= 0) return;
+  if (a.n_tiles <= 0 || splits <= 0) return;
+  if (a.mode == 1) {
+    if (a.rows_a > 0) launch_t<2, 1>(tm_g, tm_rho, a, splits, st);
+    return;
+  }
+  if (a.mt_per_x <= 0) return;
   if (parts == 2)
-    launch_t<2>(tm_g, tm_rho, a, splits, st);
+    launch_t<2, 0>(tm_g, tm_rho, a, splits, st);
   else
-    launch_t<3>(tm_g, tm_rho, a, splits, st);
+    launch_t<3, 0>(tm_g, tm_rho, a, splits, st);
 }
 
 }  // namespace xtc

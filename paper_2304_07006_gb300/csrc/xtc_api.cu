@@ -61,7 +61,7 @@ struct xtc_ctx {
   DBuf jp_dev, err_dev, flag_dev;
   DBuf grid, w, phi, gamma, phiT, pair_p, pair_q;
   DBuf jtab, jtab64, rho, colmax, colexp, G;
-  DBuf V, Vacc, L, R, M, evec, lam, dU_tmp, dh_tmp, e0_tmp, vout, r1, r2;
+  DBuf V, Vacc, L, R, L32, R32, eL, eR, M, evec, lam, dU_tmp, dh_tmp, e0_tmp, vout, r1, r2;
   // prepared state key (pair tables)
   int pair_n = -1;
   // timers
@@ -213,12 +213,13 @@ struct Plan {
 };
 
 int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t NGp, int parts, int64_t n_outer, bool f64) {
-  // memory budgets: 6 GB for V and the step (d) operands, 16 GB for the step (a) gradient table;
+  // memory budgets: 10 GB for V and the step (d) operands, 16 GB for the step (a) gradient table;
   // then the chunk that fills whole waves of the step (b) GEMM best
   const double vbytes = f64 ? 3.0 * 8 : 3.0 * 4;
-  const double lrbytes = f64 ? 2 * 4 * 8.0 : 2 * 3 * 4 * 2.0;
+  // step (d) operands per pair and outer point: FP64 L, R; bf16 x3 L, R; or FP32 L, R + fp16 x2 split
+  const double lrbytes = f64 ? 2 * 4 * 8.0 : (parts == 2 ? 2 * 4 * (4.0 + 4.0) : 2 * 3 * 4 * 2.0);
   const double per_point = NP * (vbytes + lrbytes);
-  int64_t cap = static_cast<int64_t>(6.0e9 / per_point);
+  int64_t cap = static_cast<int64_t>(10.0e9 / per_point);
   if (!f64) cap = std::min<int64_t>(cap, static_cast<int64_t>(16.0e9 / (3.0 * parts * 2.0 * NGp)));
   cap = std::max<int64_t>(128, std::min<int64_t>(cap, 32768) / 128 * 128);
   const int64_t need = round_up(n_outer, 128);
@@ -622,7 +623,7 @@ extern "C" int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const dou
   int rc = prepare(ctx, pl, n_grid, n_orb, grid_xyz, weights, phi, &d_grid, &d_w, &d_phi);
   if (rc) return rc;
   const int NP = pl.NP;
-  const int ldm = static_cast<int>(round_up(NP, AS_BN));
+  const int ldm = static_cast<int>(m_stride(NP));
 
   // ---- device copies of gamma and its factors
   if (!ensure(ctx->gamma, g.size() * 8) || !ensure(ctx->evec, std::max<size_t>(ev.size(), 1) * 8) ||
@@ -636,14 +637,31 @@ extern "C" int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const dou
   CUDA_OK(cudaMemsetAsync(ctx->M.p, 0, 8ull * NP * ldm, st));
 
   // ---- step (d) operands
+  // fp16 x2: step (c) writes FP32 rows L32 / R32, split per row into fp16 hi + lo (L, R, 128-byte
+  // rows) and multiplied on the step (b) engine; bf16 x3: step (c) writes the three bf16 parts.
   const int64_t kdim = 4 * pl.gc;
-  const size_t lr_bytes = pl.f64 ? 8ull * kdim * NP : 2ull * 3 * kdim * NP;
+  const bool d16 = !pl.f64 && pl.parts_b == 2;
+  const size_t lr_bytes = pl.f64 ? 8ull * kdim * NP : (d16 ? 4ull * kdim * NP : 2ull * 3 * kdim * NP);
   if (!ensure(ctx->L, lr_bytes) || !ensure(ctx->R, lr_bytes))
     return fail(ctx, XTC_ERR_OOM, "step (d) operands (%.2f GB)", 2.0 * lr_bytes / 1e9);
+  if (d16) {
+    const size_t ebytes = 4ull * m_stride(NP);
+    const int bn = vf_bn(2);
+    const size_t tiles = static_cast<size_t>((NP + VF_BM - 1) / VF_BM) * ((NP + bn - 1) / bn);
+    if (!ensure(ctx->L32, 4ull * kdim * NP) || !ensure(ctx->R32, 4ull * kdim * NP) || !ensure(ctx->eL, ebytes) ||
+        !ensure(ctx->eR, ebytes) || !ensure(ctx->Vacc, std::max<size_t>(ctx->Vacc.n, 8ull * tiles * VF_BM * bn)))
+      return fail(ctx, XTC_ERR_OOM, "step (d) FP32 operands (%.2f GB)", 8.0 * kdim * NP / 1e9);
+    // exponents of the padding columns of M stay 0
+    CUDA_OK(cudaMemsetAsync(ctx->eL.p, 0, ebytes, st));
+    CUDA_OK(cudaMemsetAsync(ctx->eR.p, 0, ebytes, st));
+  }
   VfMaps maps{};
   CUtensorMap tm_L{}, tm_R{};
   if ((rc = make_vfield_maps(ctx, pl, maps))) return rc;
-  if (!pl.f64) {
+  if (d16) {
+    if ((rc = make_tmap_3d(ctx, &tm_L, ctx->L.p, false, 2 * kdim, NP, 1, 2 * VF_BK, VF_BM, true))) return rc;
+    if ((rc = make_tmap_3d(ctx, &tm_R, ctx->R.p, false, 2 * kdim, NP, 1, 2 * VF_BK, vf_bn(2), true))) return rc;
+  } else if (!pl.f64) {
     if ((rc = make_tmap_3d(ctx, &tm_L, ctx->L.p, true, kdim, NP, 3, AS_BK, AS_BM))) return rc;
     if ((rc = make_tmap_3d(ctx, &tm_R, ctx->R.p, true, kdim, NP, 3, AS_BK, AS_BN))) return rc;
   }
@@ -680,10 +698,33 @@ extern "C" int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const dou
       fa.pts = pts;
       fa.pair_p = ctx->pair_p.as<int>();
       fa.pair_q = ctx->pair_q.as<int>();
-      fa.L = ctx->L.p;
-      fa.R = ctx->R.p;
-      fa.out_parts = pl.f64 ? 0 : 3;
+      fa.L = d16 ? ctx->L32.p : ctx->L.p;
+      fa.R = d16 ? ctx->R32.p : ctx->R.p;
+      fa.out_parts = pl.f64 ? 0 : (d16 ? 1 : 3);
       timed(ctx, XTC_K_FIELDS, 1, [&] { launch_fields(fa, pl.f64, st); });
+      if (d16) {
+        VfieldArgs da{};
+        da.mode = 1;
+        da.rows_a = NP;
+        da.n_pair = NP;
+        da.n_tiles = (NP + vf_bn(2) - 1) / vf_bn(2);
+        da.n_kb = static_cast<int>(kdim / VF_BK);
+        da.kb_per_split = da.n_kb;
+        da.kd = std::min(ctx->vf_kd, 4);
+        da.flush = ctx->vf_flush > 0 ? ctx->vf_flush : 128;
+        da.Vacc = ctx->Vacc.as<double>();
+        da.M = ctx->M.as<double>();
+        da.ldm = m_stride(NP);
+        da.exp_a = ctx->eL.as<int>();
+        da.exp_b = ctx->eR.as<int>();
+        da.err = ctx->err_dev.as<int>();
+        timed(ctx, XTC_K_ASSEMBLE, 4, [&] {
+          launch_lr_split(ctx->L32.as<float>(), NP, kdim, ctx->L.as<uint16_t>(), ctx->eL.as<int>(), st);
+          launch_lr_split(ctx->R32.as<float>(), NP, kdim, ctx->R.as<uint16_t>(), ctx->eR.as<int>(), st);
+          launch_vfield_tc(&tm_L, &tm_R, da, 2, 1, st);
+        });
+        continue;
+      }
       timed(ctx, XTC_K_ASSEMBLE, 1, [&] {
         if (pl.f64)
           launch_assemble_f64(ctx->L.as<double>(), ctx->R.as<double>(), NP, static_cast<int>(kdim),

@@ -41,6 +41,9 @@ constexpr int DEV_ERR_TIMEOUT_VF = 1;
 constexpr int DEV_ERR_TIMEOUT_AS = 2;
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+// Row stride of the FP64 accumulator M[pq][rs]: whole 128-column (bf16 step d) and 192-column
+// (fp16 step d) tiles fit in a row.
+inline int64_t m_stride(int64_t n_pair) { return round_up(n_pair, 384); }
 
 // ---------------------------------------------------------------- launchers
 
@@ -89,7 +92,7 @@ void launch_gfield(const CUtensorMap* tm_g_store, const GfieldArgs& a, int parts
 // chunk, from the G table (tm_g: box rows 128) and the split rho^T (tm_rho: box rows vf_bn(parts)).
 struct VfieldArgs {
   const int* colexp;           // per-pair exponent of the rho scaling (0 when unscaled)
-  float* V;                    // output base
+  float* V;                    // output base (mode 0)
   double* Vacc;                // FP64 partial sums, [splits][grid CTAs][BN][128] (used when flush > 0)
   int flush;                   // ranges summed in FP32 registers between FP64 flushes (0: no flush)
   int64_t n_i;                 // outer points of this chunk
@@ -101,6 +104,15 @@ struct VfieldArgs {
   int kd;                      // K-blocks per TMEM accumulation range (then added to the FP32 running sum)
   float unscale_g;             // 2^-sG
   int* err;
+  // mode 1 (step d with fp16 x2 operands): A = L split rows (rows_a of them), B = R split rows
+  // (n_pair), K = 32 * n_kb; the tile sums (FP64, Vacc, flush > 0 required) are added, unscaled by
+  // 2^-(exp_a[pq] + exp_b[rs]), into M[pq * ldm + rs]
+  int mode;
+  int rows_a;
+  double* M;
+  int64_t ldm;
+  const int* exp_a;
+  const int* exp_b;
 };
 bool vfield_tc_supported(int n_nuc);
 // Launches the GEMM and, when a.flush > 0, the kernel that writes V from the FP64 sums.
@@ -137,12 +149,17 @@ struct FieldsArgs {
   const int* pair_q;
   void* L;                     // outputs
   void* R;
-  int out_parts;               // 0 = FP64 [4*gcp][pq]; 3 = bf16 x3 split [part][pq][4*gcp]
+  int out_parts;               // 0 = FP64 [4*gcp][pq]; 1 = FP32 [pq][4*gcp]; 3 = bf16 x3 split [part][pq][4*gcp]
 };
 size_t fields_smem_bytes(int n_orb, int rank, int pts, bool f64);
 void launch_fields(const FieldsArgs& a, bool f64, cudaStream_t st);  // f64: FP64 V, compute and output
 
-// Step (d), tensor cores: M[pq][rs] += sum_k L[pq][k] R[rs][k] over k < kdim (FP64 accumulator).
+// Step (d) operands in fp16 x2: each FP32 row src[r][0..kdim) is scaled by 2^exps[r] (largest
+// magnitude in [2^13, 2^14)) and split into hi + lo fp16, both parts of a 32-element block in one
+// 128-byte row: dst[r][k / 32][part][k % 32].
+void launch_lr_split(const float* src, int rows, int64_t kdim, uint16_t* dst, int* exps, cudaStream_t st);
+
+// Step (d), tensor cores, bf16 x3: M[pq][rs] += sum_k L[pq][k] R[rs][k] over k < kdim (FP64 accumulator).
 void launch_assemble_tc(const CUtensorMap* tm_L, const CUtensorMap* tm_R, int n_pair, int kdim, int kd, double* M,
                         int* err, cudaStream_t st);
 
