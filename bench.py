@@ -152,6 +152,50 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batched_measure(args, torch, dev, local):
+    """The batched workload (uneven instances: N in [20, 90], 10k-60k points, 1-4 nuclei): one
+    xtc_build_1b2b_batched call against a loop of xtc_build_1b2b calls on one context, inputs
+    resident on the device, after one warm-up of each.  Delta U is formed (it feeds Delta h and
+    the constant) but not unpacked into dense N^4 outputs."""
+    import synth
+    from paper_2304_07006_gb300 import Context
+
+    probs = synth.make_batched(args.batched)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    inst = [{"nuc_xyz": q.nuc_xyz, "nuc_set": q.nuc_set, "terms": q.terms, "coef": q.coef, "grid": t(q.grid),
+             "weights": t(q.weights), "phi": t(q.phi), "gamma": t(q.gamma),
+             "dh": torch.empty((q.n_orb, q.n_orb), dtype=torch.float64, device=dev),
+             "e0": torch.empty(1, dtype=torch.float64, device=dev)} for q in probs]
+    total = sum(flops(q.n_orb, q.n_grid)["total"] for q in probs)
+
+    def loop(c):
+        for d in inst:
+            c.set_jastrow(d["nuc_xyz"], d["nuc_set"], d["terms"], d["coef"])
+            c.build(d["grid"], d["weights"], d["phi"], d["gamma"], dh=d["dh"], e0=d["e0"], want_dU=False)
+
+    res = {}
+    with Context(args.precision, device=local) as c:
+        loop(c)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        loop(c)
+        torch.cuda.synchronize(dev)
+        res["loop_s"] = time.perf_counter() - t0
+    with Context(args.precision, device=local) as c:
+        c.build_batched(inst, want_dU=False)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        c.build_batched(inst, want_dU=False)
+        torch.cuda.synchronize(dev)
+        res["batched_s"] = time.perf_counter() - t0
+    return {"instances": len(probs), "n_orb_range": [min(q.n_orb for q in probs), max(q.n_orb for q in probs)],
+            "n_grid_range": [min(q.n_grid for q in probs), max(q.n_grid for q in probs)],
+            "algorithmic_flops": total, "loop_s": res["loop_s"], "batched_s": res["batched_s"],
+            "tflops_batched": total / res["batched_s"] / 1e12, "tflops_loop": total / res["loop_s"] / 1e12,
+            "speedup_vs_loop": res["loop_s"] / res["batched_s"], "lanes": 4,
+            "note": "wall time of one call (host + device), inputs on the device, dU not unpacked"}
+
+
 def run_ncu_case(args):
     """A small, quick build (same workload, outer sum restricted to P points) for kernel captures."""
     import synth
@@ -176,6 +220,8 @@ def main():
     ap.add_argument("--fp64-sample", type=int, default=512, help="outer points for the FP64 GPU comparison")
     ap.add_argument("--cpu-sample", type=int, default=4, help="outer points for the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--batched", type=int, default=32, metavar="N",
+                    help="also time the batched workload of N uneven instances (0: skip)")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="P",
                     help="profiling aid: run one warm-up and one build of the workload restricted to the first P "
                          "outer points, print a one-line summary and exit (no benchmark line)")
@@ -333,6 +379,8 @@ def main():
         d2h = sum(int(a.numel()) * 8 for a in (hdU, hdh, he0))
         line["e2e"] = {"value": F["total"] / dt / 1e12, "unit": "TFLOP/s", "seconds_per_build": dt,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        if args.batched:
+            line["batched"] = batched_measure(args, torch, dev, local)
         line["cpu_baseline"] = oracle_sample(p, args.cpu_sample)
         line["cpu_baseline"].pop("seconds", None)
         print(json.dumps(line), flush=True)

@@ -144,6 +144,40 @@ XTC_API int xtc_jastrow_grad(xtc_ctx* ctx, int64_t n, const double* r1, const do
 XTC_API int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
                const double* phi, int64_t outer_begin, int64_t outer_end, double* V);
 
+/* One instance of a batched build: the arguments of xtc_set_jastrow and xtc_build_1b2b, with the
+ * same meanings, layouts and ownership; status receives the instance's own status. */
+typedef struct xtc_instance {
+  int64_t n_grid;
+  int n_orb;
+  const double* grid_xyz;   /* [n_grid][3] bohr */
+  const double* weights;    /* [n_grid] */
+  const double* phi;        /* [n_grid][n_orb] */
+  const double* gamma;      /* [n_orb][n_orb] per spin, symmetric */
+  int n_nuc;
+  const double* nuc_xyz;    /* [n_nuc][3] bohr */
+  const int* nuc_set;       /* [n_nuc] */
+  int n_sets;
+  int n_terms;
+  const int* mno;           /* [n_terms][3] */
+  const double* coef;       /* [n_sets][n_terms] */
+  double* dU;               /* [n_orb]^4 or NULL */
+  float* dU_f32;            /* [n_orb]^4 or NULL */
+  double* dh;               /* [n_orb][n_orb] */
+  double* e0;               /* scalar */
+  int status;               /* out */
+} xtc_instance;
+
+/* Batched build of many molecules (or Jastrow parameter sets) of uneven size: every instance is
+ * computed exactly as by xtc_set_jastrow + xtc_build_1b2b on a context with ctx's parameters (the
+ * results are bitwise identical).  The instances are spread over n_lanes lanes (0 = automatic,
+ * at most 4; at most 16), each a context with its own stream and workspace driven by its own host
+ * thread, largest instances first, so that the kernels of small instances overlap on the GPU.
+ * Lane contexts are kept in ctx for later batches and released by xtc_destroy.  Inputs written
+ * on ctx's stream are waited for first; the call returns when every instance is done (or has
+ * failed: the first failing instance's status is returned and named in xtc_last_error_detail).
+ * Each lane holds the workspace of its largest instance.  The outer range of ctx does not apply. */
+XTC_API int xtc_build_1b2b_batched(xtc_ctx* ctx, int n_inst, xtc_instance* inst, int n_lanes);
+
 /* Kernel timers of the last build (requires params.timing != 0).  Kernel ids: */
 enum {
   XTC_K_PREP = 0,     /* per-grid-point tables, orbital transposition, pair products rho (split) */

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "../../include/xtc.h"
@@ -74,6 +75,9 @@ struct xtc_ctx {
   int vf_kd = 2;  // K-blocks per tensor-core accumulation range in step (b)
   int vf_flush = 128;  // step (b) ranges between FP64 flushes of the running sums (0: FP32 only)
   int as_kd = 2;  // the same for step (d)
+  // batched builds: lane contexts, each with its own stream (created on first use)
+  std::vector<xtc_ctx*> lanes;
+  std::vector<cudaStream_t> lane_streams;
 };
 
 namespace {
@@ -319,10 +323,13 @@ int xtc_destroy(xtc_ctx* ctx) {
   else cudaDeviceSynchronize();
   DBuf* bufs[] = {&ctx->jp_dev, &ctx->err_dev, &ctx->flag_dev, &ctx->grid, &ctx->w, &ctx->phi, &ctx->gamma,
                   &ctx->phiT, &ctx->pair_p, &ctx->pair_q, &ctx->jtab, &ctx->jtab64, &ctx->rho, &ctx->colmax,
-                  &ctx->colexp, &ctx->V, &ctx->L, &ctx->R, &ctx->M, &ctx->evec, &ctx->lam, &ctx->dU_tmp,
+                  &ctx->colexp, &ctx->G, &ctx->V, &ctx->Vacc, &ctx->L, &ctx->R, &ctx->L32, &ctx->R32,
+                  &ctx->eL, &ctx->eR, &ctx->M, &ctx->evec, &ctx->lam, &ctx->dU_tmp,
                   &ctx->dh_tmp, &ctx->e0_tmp, &ctx->vout, &ctx->r1, &ctx->r2};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
+  for (xtc_ctx* lane : ctx->lanes) xtc_destroy(lane);
+  for (cudaStream_t s : ctx->lane_streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   delete ctx;
   return XTC_OK;
@@ -852,3 +859,76 @@ bool xtc_internal_ctx_view(const xtc_ctx* ctx, xtc::CtxView* v) {
 }
 
 int xtc_internal_fail(xtc_ctx* ctx, int code, const char* msg) { return fail(ctx, code, "%s", msg); }
+
+// ====================================================================== batched build
+// Instances are ordered by their step (b) cost (N_g^2 N_pair, largest first) and each goes to the
+// lane with the least work so far; every lane is a context with its own stream and workspace, run
+// by its own host thread, so that the kernels of small instances (which fill little of the GPU)
+// overlap.  Every instance is computed exactly as by xtc_set_jastrow + xtc_build_1b2b on a
+// context of the same parameters.
+extern "C" int xtc_build_1b2b_batched(xtc_ctx* ctx, int n_inst, xtc_instance* inst, int n_lanes) {
+  if (!ctx) return XTC_ERR_ARG;
+  if (n_inst < 0 || (n_inst > 0 && !inst) || n_lanes < 0)
+    return fail(ctx, XTC_ERR_ARG, "bad instance count, instance array or lane count");
+  if (n_inst == 0) return XTC_OK;
+  CUDA_OK(cudaSetDevice(ctx->prm.device));
+  // inputs the caller wrote on its stream are complete before the lanes start
+  if (ctx->st) CUDA_OK(cudaStreamSynchronize(ctx->st));
+  else CUDA_OK(cudaDeviceSynchronize());
+  const int lanes = std::min(n_inst, n_lanes > 0 ? std::min(n_lanes, 16) : 4);
+  while (static_cast<int>(ctx->lanes.size()) < lanes) {
+    cudaStream_t sl = nullptr;
+    CUDA_OK(cudaStreamCreateWithFlags(&sl, cudaStreamNonBlocking));
+    xtc_params lp = ctx->prm;
+    lp.stream = sl;
+    lp.timing = 0;
+    xtc_ctx* lc = nullptr;
+    const int rc = xtc_create(&lc, &lp);
+    if (rc != XTC_OK) {
+      cudaStreamDestroy(sl);
+      return fail(ctx, rc, "creating a batch lane failed");
+    }
+    ctx->lanes.push_back(lc);
+    ctx->lane_streams.push_back(sl);
+  }
+  std::vector<int> order(n_inst);
+  for (int i = 0; i < n_inst; ++i) order[i] = i;
+  auto cost = [&](int i) {
+    const double np = 0.5 * inst[i].n_orb * (inst[i].n_orb + 1.0);
+    return static_cast<double>(inst[i].n_grid) * static_cast<double>(inst[i].n_grid) * np;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  std::vector<std::vector<int>> work(lanes);
+  std::vector<double> load(lanes, 0.0);
+  for (int i : order) {
+    const int l = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+    work[l].push_back(i);
+    load[l] += cost(i);
+  }
+  const int device = ctx->prm.device;
+  auto run_lane = [&](int l) {
+    cudaSetDevice(device);
+    xtc_ctx* lc = ctx->lanes[l];
+    for (int i : work[l]) {
+      xtc_instance& in = inst[i];
+      int rc = xtc_set_jastrow(lc, in.n_nuc, in.nuc_xyz, in.nuc_set, in.n_sets, in.n_terms, in.mno, in.coef);
+      if (rc == XTC_OK) rc = xtc_set_outer_range(lc, 0, -1);
+      if (rc == XTC_OK)
+        rc = xtc_build_1b2b(lc, in.n_grid, in.n_orb, in.grid_xyz, in.weights, in.phi, in.gamma, in.dU, in.dU_f32, in.dh,
+                            in.e0);
+      in.status = rc;
+    }
+  };
+  std::vector<std::thread> threads;
+  for (int l = 1; l < lanes; ++l) threads.emplace_back(run_lane, l);
+  run_lane(0);
+  for (std::thread& t : threads) t.join();
+  for (int i = 0; i < n_inst; ++i)
+    if (inst[i].status != XTC_OK) {
+      const xtc_ctx* lc = nullptr;
+      for (int l = 0; l < lanes; ++l)
+        if (std::find(work[l].begin(), work[l].end(), i) != work[l].end()) lc = ctx->lanes[l];
+      return fail(ctx, inst[i].status, "instance %d: %s", i, lc ? lc->detail : "");
+    }
+  return XTC_OK;
+}

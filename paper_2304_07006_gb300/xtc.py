@@ -20,12 +20,21 @@ KERNEL_NAMES = ("prep", "vfield", "fields", "assemble", "final", "grad")
 
 EXPORTED = ("xtc_default_params", "xtc_create", "xtc_destroy", "xtc_strerror", "xtc_last_error_detail",
             "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b", "xtc_jastrow_grad", "xtc_vfield",
-            "xtc_get_timings", "xtc_vfield_noalloc")
+            "xtc_get_timings", "xtc_vfield_noalloc", "xtc_build_1b2b_batched")
 
 
 class XtcParams(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("grid_chunk", ctypes.c_int64), ("split_k", ctypes.c_int), ("timing", ctypes.c_int)]
+
+
+class XtcInstance(ctypes.Structure):
+    _fields_ = [("n_grid", ctypes.c_int64), ("n_orb", ctypes.c_int), ("grid_xyz", ctypes.c_void_p),
+                ("weights", ctypes.c_void_p), ("phi", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
+                ("n_nuc", ctypes.c_int), ("nuc_xyz", ctypes.c_void_p), ("nuc_set", ctypes.c_void_p),
+                ("n_sets", ctypes.c_int), ("n_terms", ctypes.c_int), ("mno", ctypes.c_void_p),
+                ("coef", ctypes.c_void_p), ("dU", ctypes.c_void_p), ("dU_f32", ctypes.c_void_p),
+                ("dh", ctypes.c_void_p), ("e0", ctypes.c_void_p), ("status", ctypes.c_int)]
 
 
 class XtcError(RuntimeError):
@@ -61,8 +70,10 @@ def load(path: str = LIB_PATH):
     lib.xtc_vfield.argtypes = [P, I64, I, D, D, D, I64, I64, D]
     lib.xtc_vfield_noalloc.argtypes = [P, I64, I, D, D, D, I64, I64, D]
     lib.xtc_get_timings.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), I]
+    lib.xtc_build_1b2b_batched.argtypes = [P, I, ctypes.POINTER(XtcInstance), I]
     for name in ("xtc_create", "xtc_destroy", "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b",
-                 "xtc_jastrow_grad", "xtc_vfield", "xtc_get_timings", "xtc_vfield_noalloc"):
+                 "xtc_jastrow_grad", "xtc_vfield", "xtc_get_timings", "xtc_vfield_noalloc",
+                 "xtc_build_1b2b_batched"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -184,6 +195,36 @@ class Context:
         self._check(self._lib.xtc_vfield_noalloc(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
                                                  int(outer_begin), int(outer_end), _ptr(out)))
         return out
+
+    def build_batched(self, instances, n_lanes=0, want_dU=True):
+        """Batched build.  instances: list of dicts with keys nuc_xyz, nuc_set, terms, coef, grid,
+        weights, phi, gamma (numpy arrays or float64 tensors) and optional outputs dU / dU_f32 / dh /
+        e0; returns the list of output dicts {"dU", "dh", "e0"} in instance order."""
+        n = len(instances)
+        arr = (XtcInstance * max(n, 1))()
+        keep, outs = [], []
+        for k, d in enumerate(instances):
+            grid, w, phi, gamma = _f64(d["grid"]), _f64(d["weights"]), _f64(d["phi"]), _f64(d["gamma"])
+            nuc = np.ascontiguousarray(d["nuc_xyz"], dtype=np.float64)
+            ns = np.ascontiguousarray(d["nuc_set"], dtype=np.int32)
+            tm = np.ascontiguousarray(d["terms"], dtype=np.int32)
+            cf = np.ascontiguousarray(d["coef"], dtype=np.float64)
+            n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+            dU, dU32 = d.get("dU"), d.get("dU_f32")
+            if dU is None and dU32 is None and want_dU:
+                dU = np.empty((n_orb,) * 4)
+            dh = d.get("dh") if d.get("dh") is not None else np.empty((n_orb, n_orb))
+            e0 = d.get("e0") if d.get("e0") is not None else np.empty(1)
+            keep += [grid, w, phi, gamma, nuc, ns, tm, cf, dU, dU32, dh, e0]
+            it = arr[k]
+            it.n_grid, it.n_orb = n_grid, n_orb
+            it.grid_xyz, it.weights, it.phi, it.gamma = _ptr(grid), _ptr(w), _ptr(phi), _ptr(gamma)
+            it.n_nuc, it.nuc_xyz, it.nuc_set = nuc.shape[0], _ptr(nuc), _ptr(ns)
+            it.n_sets, it.n_terms, it.mno, it.coef = cf.shape[0], tm.shape[0], _ptr(tm), _ptr(cf)
+            it.dU, it.dU_f32, it.dh, it.e0 = _ptr(dU), _ptr(dU32), _ptr(dh), _ptr(e0)
+            outs.append({"dU": dU if dU is not None else dU32, "dh": dh, "e0": e0})
+        self._check(self._lib.xtc_build_1b2b_batched(self._h, n, arr, int(n_lanes)))
+        return outs
 
     def timings(self):
         n = len(KERNEL_NAMES)

@@ -8,6 +8,7 @@ the CUDA path can both consume its arrays without sharing any of the method.
 from .molecules import (  # noqa: F401
     Problem,
     CANONICAL_TERMS,
+    make_batched,
     make_config,
     make_small,
     random_density,

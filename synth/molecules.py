@@ -251,6 +251,33 @@ def make_config(name: str) -> Problem:
     raise ValueError(f"unknown config {name!r}")
 
 
+def make_batched(n_inst: int = 32, seed: int = 4, scale: float = 1.0, n_orb_range=(20, 90)) -> list:
+    """Instances of uneven size for the batched build: N uniform in [20, 90] (``n_orb_range``),
+    grid uniform in [10k, 60k] points (times ``scale``; smaller ranges serve quick tests), 1-4
+    nuclei uniformly in a ball of radius
+    3 bohr (the first heavy, the rest H), one Jastrow centre set per nucleus, n_occ = max(1, N/10).
+    Sizes and positions come from default_rng(seed); instance k draws its orbitals and Jastrow
+    coefficients from default_rng(1000 + k)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_inst):
+        n_orb = int(rng.integers(n_orb_range[0], n_orb_range[1] + 1))
+        n_grid = int(rng.integers(10000, 60001) * scale)
+        n_nuc = int(rng.integers(1, 5))
+        centres = []
+        while len(centres) < n_nuc:
+            p = rng.uniform(-3.0, 3.0, size=3)
+            if np.linalg.norm(p) <= 3.0 and all(np.linalg.norm(p - q) > 1.0 for q in centres):
+                centres.append(p)
+        kinds = "X" + "H" * (n_nuc - 1)
+        per_atom = max(n_grid // n_nuc, 200)
+        n_theta, n_phi = 10, 20
+        spec = [(max(per_atom // (n_theta * n_phi), 2), n_theta, n_phi)] * n_nuc
+        out.append(_build(f"batched{k}", centres, kinds, spec, n_orb, max(1, n_orb // 10),
+                          list(range(n_nuc)), n_nuc, 1000 + k))
+    return out
+
+
 def make_small(n_orb: int = 4, n_rad: int = 6, n_theta: int = 3, n_phi: int = 4,
                n_atoms: int = 2, seed: int = 7, n_occ: int = 1, separate_sets: bool = True,
                terms=CANONICAL_TERMS) -> Problem:

@@ -264,3 +264,42 @@ def test_n2_workload_sampled_outer_points(n2_sampled, prec):
         out = c.build(p.grid, p.weights, p.phi, p.gamma, want_dU=True)
     err = max_err(out, ref)
     assert err < TOL[prec], err
+
+
+# ------------------------------------------------------------------ batched build
+
+def _instances(probs, gammas=None):
+    return [{"nuc_xyz": p.nuc_xyz, "nuc_set": p.nuc_set, "terms": p.terms, "coef": p.coef, "grid": p.grid,
+             "weights": p.weights, "phi": p.phi, "gamma": p.gamma if gammas is None else gammas[k]}
+            for k, p in enumerate(probs)]
+
+
+@pytest.mark.parametrize("prec", ["fp16x2", "fp64"])
+def test_batched_build_equals_individual_builds(prec):
+    """Six molecules of uneven size (the batched workload's recipe, shrunk) on three lanes: every
+    instance bitwise equal to its own xtc_build_1b2b, and the first also against the oracle."""
+    from paper_2304_07006_gb300 import Context
+    probs = synth.make_batched(6, seed=11, scale=0.1, n_orb_range=(6, 16))
+    gammas = [synth.random_density(p.n_orb, 20 + k) for k, p in enumerate(probs)]
+    with Context(prec) as c:
+        outs = c.build_batched(_instances(probs, gammas), n_lanes=3)
+    for k, p in enumerate(probs):
+        with ctx_for(p, prec) as c:
+            one = c.build(p.grid, p.weights, p.phi, gammas[k])
+        for key in ("dU", "dh", "e0"):
+            assert np.array_equal(np.asarray(outs[k][key]), np.asarray(one[key])), (k, key)
+    ref = direct.build(probs[0], gammas[0])
+    assert max_err(outs[0], ref) < TOL[prec]
+
+
+def test_batched_build_reports_the_failing_instance():
+    from paper_2304_07006_gb300 import Context, XtcError
+    probs = synth.make_batched(3, seed=12, scale=0.1, n_orb_range=(6, 10))
+    inst = _instances(probs)
+    bad = probs[1].weights.copy()
+    bad[5] = np.nan
+    inst[1]["weights"] = bad
+    with Context("fp16x2") as c:
+        with pytest.raises(XtcError) as e:
+            c.build_batched(inst, n_lanes=2)
+    assert e.value.code == -3 and "instance 1" in str(e.value)
