@@ -75,9 +75,11 @@ typedef enum {
 
 typedef enum {
   XTC_PREC_FP64 = 0,   /* all four steps in FP64 (SIMT) */
-  XTC_PREC_FP16X2 = 1, /* step (b): 2-term FP16 split (3 tensor-core products) with power-of-2 scaling;
-                          step (d): 3-term BF16 split (6 products); FP32 accumulation in TMEM;
-                          FP64 accumulation of Delta U across grid chunks, of Delta h and of e0 */
+  XTC_PREC_FP16X2 = 1, /* steps (b) and (d): 2-term FP16 split (3 tensor-core products) with
+                          power-of-2 scaling (per pair column of rho in step b, per row of L and R
+                          in step d); FP32 accumulation in TMEM over short ranges, FP32 running
+                          sums flushed to FP64 every 128 ranges; FP64 accumulation of Delta U
+                          across grid chunks, of Delta h and of e0 */
   XTC_PREC_BF16X3 = 2  /* steps (b) and (d): 3-term BF16 split (6 products), otherwise as FP16X2 */
 } xtc_precision;
 

@@ -370,7 +370,9 @@ int xtc_set_jastrow(xtc_ctx* ctx, int n_nuc, const double* nuc_xyz, const int* n
     for (int t = 0; t < n_terms; ++t)
       bound += std::fabs(jp.coef[jp.set[I]][t]) * (jp.mno[t][0] + jp.mno[t][1] + 2.0 * jp.mno[t][2]);
   cudaSetDevice(ctx->prm.device);
-  CUDA_OK(cudaMemcpy(ctx->jp_dev.p, &jp, sizeof(jp), cudaMemcpyHostToDevice));
+  // on the context's stream (a plain cudaMemcpy is not ordered with non-blocking streams)
+  CUDA_OK(cudaMemcpyAsync(ctx->jp_dev.p, &jp, sizeof(jp), cudaMemcpyHostToDevice, ctx->st));
+  CUDA_OK(cudaStreamSynchronize(ctx->st));
   ctx->jp = jp;
   ctx->g_bound = bound;
   ctx->jastrow_set = true;
@@ -467,8 +469,9 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
       }
     if (!ensure(ctx->pair_p, pl.NP * sizeof(int)) || !ensure(ctx->pair_q, pl.NP * sizeof(int)))
       return fail(ctx, XTC_ERR_OOM, "pair tables");
-    CUDA_OK(cudaMemcpy(ctx->pair_p.p, pp.data(), pl.NP * sizeof(int), cudaMemcpyHostToDevice));
-    CUDA_OK(cudaMemcpy(ctx->pair_q.p, pq.data(), pl.NP * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_OK(cudaMemcpyAsync(ctx->pair_p.p, pp.data(), pl.NP * sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_OK(cudaMemcpyAsync(ctx->pair_q.p, pq.data(), pl.NP * sizeof(int), cudaMemcpyHostToDevice, st));
+    CUDA_OK(cudaStreamSynchronize(st));  // pp and pq are released on return
     ctx->pair_n = n_orb;
   }
   if (!ensure(ctx->phiT, sizeof(double) * pl.NGp * n_orb)) return fail(ctx, XTC_ERR_OOM, "phiT");
@@ -601,7 +604,10 @@ extern "C" int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const dou
   if (n_orb < 1 || n_orb > MAX_ORB) return fail(ctx, XTC_ERR_ARG, "n_orb=%d out of range", n_orb);
   const int N = n_orb;
   std::vector<double> g(static_cast<size_t>(N) * N);
-  if (is_device_ptr(gamma)) CUDA_OK(cudaMemcpy(g.data(), gamma, g.size() * 8, cudaMemcpyDeviceToHost));
+  if (is_device_ptr(gamma)) {
+    CUDA_OK(cudaMemcpyAsync(g.data(), gamma, g.size() * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaStreamSynchronize(st));
+  }
   else std::memcpy(g.data(), gamma, g.size() * 8);
   double gmax = 0.0, asym = 0.0;
   for (int p = 0; p < N; ++p)
