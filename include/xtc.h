@@ -70,7 +70,7 @@ typedef enum {
   XTC_ERR_CUDA = -5,          /* a CUDA runtime or driver call failed */
   XTC_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up (kernel returned early) */
   XTC_ERR_STATE = -7,         /* xtc_set_jastrow not called, or context unusable */
-  XTC_ERR_UNSUPPORTED = -8    /* device is not sm_103 / sm_100 class */
+  XTC_ERR_UNSUPPORTED = -8    /* device is not sm_103 / sm_100 class, or > 8 nuclei on tensor cores */
 } xtc_status;
 
 typedef enum {
@@ -90,6 +90,11 @@ typedef struct {
   int64_t grid_chunk;  /* outer grid points per chunk (multiple of 128); 0 = automatic */
   int split_k;         /* inner-grid slices of step (b) accumulated separately (1..16); 0 = automatic */
   int timing;          /* non-zero: record CUDA events around every kernel (see xtc_get_timings) */
+  int range_stages;    /* tensor-core precisions: inner-sum stages of 32 points accumulated in the
+                          tensor cores before an exactly rounded FP32 add (1..4; bf16x3 uses at
+                          most 2 in step b and 3 in step d).  The tensor-core FP32 accumulator
+                          truncates, so 1 is the most accurate (Delta h error about half of the
+                          default's at N=120) and about 25% slower; 0 = default (2) */
 } xtc_params;
 
 /* Fills *p with defaults: device 0, default stream, XTC_PREC_FP16X2, automatic chunking. */
@@ -110,7 +115,8 @@ XTC_API const char* xtc_last_error_detail(const xtc_ctx* ctx);
 
 /* Jastrow factor (Results, "Computational details" gives the paper's DTN form; this
  * library takes the polynomial form in the header comment).  Host arrays, copied.
- *   n_nuc    >= 1        nuclei
+ *   n_nuc    >= 1        nuclei (any number for XTC_PREC_FP64; at most 8 for the tensor-core
+ *                        precisions, else xtc_build_1b2b returns XTC_ERR_UNSUPPORTED)
  *   nuc_xyz  [n_nuc][3]  bohr
  *   nuc_set  [n_nuc]     centre-set index of each nucleus, 0 <= nuc_set[I] < n_sets
  *   n_terms  >= 1, mno [n_terms][3] = (m, n, o), each in 0..2

@@ -28,23 +28,23 @@ __global__ void jtab_kernel(const double* __restrict__ grid, int64_t n_grid, int
     y = grid[3 * j + 1];
     z = grid[3 * j + 2];
   }
-  // Points j = 2k and 2k+1 share a 24-float record, each field stored as an adjacent (even, odd)
-  // pair so that one 16-byte load yields two packed fields:
-  //   x_hi y_hi | z_hi x_lo | y_lo z_lo | a_0 a_1 | a_2 a_3 | 0 0      (each entry = [j even, j odd])
+  // Points j = 2k and 2k+1 share a record of 2 js floats, each field stored as an adjacent (even,
+  // odd) pair so that one 16-byte load yields two packed fields:
+  //   x_hi y_hi | z_hi x_lo | y_lo z_lo | a_0 a_1 | a_2 a_3 | ...      (each entry = [j even, j odd])
   // with x = x_hi + x_lo (differences of nearby points keep FP64-level accuracy in FP32) and
-  // a_I = |r_j - R_I| / (1 + |r_j - R_I|).
-  (void)js;
-  float* o = jtab + (j >> 1) * 24 + (j & 1);
+  // a_I = |r_j - R_I| / (1 + |r_j - R_I|); js = 12 holds 4 nuclei, js = 16 holds 8 (+ 2 zero
+  // fields); entries past the last nucleus are zero.
+  float* o = jtab + (j >> 1) * 2 * js + (j & 1);
   const float xh = static_cast<float>(x), yh = static_cast<float>(y), zh = static_cast<float>(z);
-  float f[12] = {xh, yh, zh, static_cast<float>(x - static_cast<double>(xh)),
-                 static_cast<float>(y - static_cast<double>(yh)), static_cast<float>(z - static_cast<double>(zh)),
-                 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-  for (int I = 0; I < n_nuc && I < 4; ++I) {
+  float f[16] = {xh, yh, zh, static_cast<float>(x - static_cast<double>(xh)),
+                 static_cast<float>(y - static_cast<double>(yh)), static_cast<float>(z - static_cast<double>(zh))};
+  for (int k = 6; k < 16; ++k) f[k] = 0.0f;
+  for (int I = 0; I < n_nuc && I < js - 6 && I < 8; ++I) {
     const double dx = x - jp->nuc[I][0], dy = y - jp->nuc[I][1], dz = z - jp->nuc[I][2];
     const double d = sqrt(dx * dx + dy * dy + dz * dz);
     f[6 + I] = static_cast<float>(d / (1.0 + d));
   }
-  for (int k = 0; k < 12; ++k) o[2 * k] = f[k];
+  for (int k = 0; k < js && k < 16; ++k) o[2 * k] = f[k];
 }
 
 __global__ void transpose_phi_kernel(const double* __restrict__ phi, int64_t n_grid, int64_t n_pad, int N,

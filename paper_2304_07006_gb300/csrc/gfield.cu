@@ -46,6 +46,7 @@ template <int PARTS, int NNUC>
 __global__ void __launch_bounds__(GF_THREADS)
     gfield_kernel(const __grid_constant__ CUtensorMap tm_g, const GfieldArgs args) {
   constexpr bool BF16 = PARTS == 3;
+  constexpr int JS = NNUC <= 4 ? 12 : 16;  // floats per inner point in the table (launch_jtab)
   constexpr int WARP_BYTES = 3 * PARTS * GF_TILE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -82,13 +83,13 @@ __global__ void __launch_bounds__(GF_THREADS)
 
   for (int kb = kb0; kb < kb1; ++kb) {
     // 16 records of two inner points each (the pair-interleaved table written by launch_jtab)
-    const float* blk = args.jtab + static_cast<int64_t>(kb) * VF_BK * 12;
+    const float* blk = args.jtab + static_cast<int64_t>(kb) * VF_BK * JS;
 #pragma unroll 1
     for (int c = 0; c < 4; ++c) {
       float gv[3][8];
 #pragma unroll
       for (int v2 = 0; v2 < 4; ++v2) {
-        const float* rec = blk + (c * 4 + v2) * 24;  // inner points 8c + 2 v2 and + 1
+        const float* rec = blk + (c * 4 + v2) * 2 * JS;  // inner points 8c + 2 v2 and + 1
         if constexpr (NNUC <= 2) {
           f32x2 xh, yh, zh, xlo, ylo, zlo, a0, a1;
           ldg_2x64(rec, xh, yh);
@@ -133,16 +134,13 @@ __global__ void __launch_bounds__(GF_THREADS)
           up2(fma2(hs, dz, ez), gv[2][2 * v2], gv[2][2 * v2 + 1]);
         } else {
           const float4 q0 = ldg_f4(rec), q1 = ldg_f4(rec + 4), q2 = ldg_f4(rec + 8);
-          const float4 q3 = ldg_f4(rec + 12), q4 = ldg_f4(rec + 16);
+          float2 ap[NNUC];  // a_jI of both points
+#pragma unroll
+          for (int I = 0; I < NNUC; ++I) ap[I] = __ldg(reinterpret_cast<const float2*>(rec + 12 + 2 * I));
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const float xh = h ? q0.y : q0.x, yh = h ? q0.w : q0.z, zh = h ? q1.y : q1.x;
             const float xlo = h ? q1.w : q1.z, ylo = h ? q2.y : q2.x, zlo = h ? q2.w : q2.z;
-            float aj[NNUC];
-            aj[0] = h ? q3.y : q3.x;
-            aj[NNUC > 1 ? 1 : 0] = h ? q3.w : q3.z;
-            if (NNUC > 2) aj[NNUC > 2 ? 2 : 0] = h ? q4.y : q4.x;
-            if (NNUC > 3) aj[NNUC > 3 ? 3 : 0] = h ? q4.w : q4.z;
             const float dx = (pc[0] - xh) + (xl - xlo);
             const float dy = (pc[1] - yh) + (yl - ylo);
             const float dz = (pc[2] - zh) + (zl - zlo);
@@ -159,7 +157,7 @@ __global__ void __launch_bounds__(GF_THREADS)
 #pragma unroll
             for (int I = 0; I < NNUC; ++I) {
               const float* cf = nc + I * NUC_COEF;
-              const float a = aj[I];
+              const float a = h ? ap[I].y : ap[I].x;
               const float t = fmaf(b, fmaf(b, fmaf(a, cf[8], cf[7]), fmaf(a, cf[6], cf[5])), fmaf(a, cf[4], cf[3]));
               const float at = a * t;
               ex = fmaf(at, cf[0], ex);
@@ -233,14 +231,16 @@ void launch_gfield(const CUtensorMap* tm_g_store, const GfieldArgs& a, int parts
       case 1: launch_t<2, 1>(tm_g_store, a, st); break;
       case 2: launch_t<2, 2>(tm_g_store, a, st); break;
       case 3: launch_t<2, 3>(tm_g_store, a, st); break;
-      default: launch_t<2, 4>(tm_g_store, a, st); break;
+      case 4: launch_t<2, 4>(tm_g_store, a, st); break;
+      default: launch_t<2, 8>(tm_g_store, a, st); break;  // 5..8 nuclei
     }
   } else {
     switch (a.n_nuc) {
       case 1: launch_t<3, 1>(tm_g_store, a, st); break;
       case 2: launch_t<3, 2>(tm_g_store, a, st); break;
       case 3: launch_t<3, 3>(tm_g_store, a, st); break;
-      default: launch_t<3, 4>(tm_g_store, a, st); break;
+      case 4: launch_t<3, 4>(tm_g_store, a, st); break;
+      default: launch_t<3, 8>(tm_g_store, a, st); break;  // 5..8 nuclei
     }
   }
 }

@@ -108,6 +108,12 @@ __device__ inline void point_coefs_fixed(const JastrowParams& jp, double x, doub
   double Hc1 = 0.0, Hc2 = 0.0;
 #pragma unroll
   for (int I = 0; I < NN; ++I) {
+    // an instance with fewer nuclei than NN: the extra slots get zero coefficients
+    if (I >= jp.n_nuc) {
+#pragma unroll
+      for (int k = 0; k < NUC_COEF; ++k) nc[I * NUC_COEF + k] = (T)0;
+      continue;
+    }
     NucTerms t;
     nuc_terms(jp, I, x, y, z, t);
 #pragma unroll

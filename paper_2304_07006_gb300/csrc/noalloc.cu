@@ -72,7 +72,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     return xtc_internal_fail(ctx, XTC_ERR_ARG, "noalloc: bad sizes or outer range");
   const bool f64 = cv.precision == XTC_PREC_FP64;
   if (!f64 && !vfield_tc_supported(cv.n_nuc))
-    return xtc_internal_fail(ctx, XTC_ERR_UNSUPPORTED, "noalloc: the tensor-core path supports 1..4 nuclei");
+    return xtc_internal_fail(ctx, XTC_ERR_UNSUPPORTED, "noalloc: the tensor-core path supports 1..8 nuclei");
   if (cudaSetDevice(cv.device) != cudaSuccess || cv.device < 0 || cv.device >= kMaxDevices)
     return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: cudaSetDevice failed");
   if (!on_device(grid_xyz) || !on_device(weights) || !on_device(phi) || !on_device(V))
@@ -106,7 +106,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
       c.take<double>(static_cast<size_t>(NP) * 3 * gc);
     } else {
       c.take<double>(static_cast<size_t>(N) * NGp);
-      c.take<float>(static_cast<size_t>(NGp) * 12);
+      c.take<float>(static_cast<size_t>(NGp) * jtab_stride(n_nuc));
       c.take<uint16_t>(static_cast<size_t>(parts) * NP * NGp);
       c.take<unsigned int>(NP);
       c.take<int>(NP);
@@ -150,14 +150,14 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     launch_rho_f64(phi, weights, n_grid, NGp, N, pair_p, pair_q, rho64, st);
   } else {
     double* phiT = cz.take<double>(static_cast<size_t>(N) * NGp);
-    jtab = cz.take<float>(static_cast<size_t>(NGp) * 12);
+    jtab = cz.take<float>(static_cast<size_t>(NGp) * jtab_stride(n_nuc));
     rho = cz.take<uint16_t>(static_cast<size_t>(parts) * NP * NGp);
     unsigned int* colmax = cz.take<unsigned int>(NP);
     colexp = cz.take<int>(NP);
     Vbuf = cz.take<float>(static_cast<size_t>(NP) * 3 * gc);
     void* G = cz.take<uint16_t>(static_cast<size_t>(parts) * 3 * gc * NGp);
     launch_transpose_phi(phi, n_grid, NGp, N, phiT, st);
-    launch_jtab(grid_xyz, n_grid, NGp, cv.jp_dev, n_nuc, 12, jtab, st);
+    launch_jtab(grid_xyz, n_grid, NGp, cv.jp_dev, n_nuc, jtab_stride(n_nuc), jtab, st);
     launch_rho_split(phiT, weights, n_grid, NGp, N, parts, parts == 3, parts == 2, pair_p, pair_q, colmax, colexp,
                      rho, st);
     // rho^T (box rows vf_bn) and the gradient table [part][x * gc + il][j] (boxes 32 x 32

@@ -393,7 +393,7 @@ void launch_t(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldAr
 
 }  // namespace
 
-bool vfield_tc_supported(int n_nuc) { return n_nuc >= 1 && n_nuc <= 4; }
+bool vfield_tc_supported(int n_nuc) { return n_nuc >= 1 && n_nuc <= 8; }
 
 void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int parts,
                       int splits, cudaStream_t st) {

@@ -286,6 +286,7 @@ int xtc_create(xtc_ctx** out, const xtc_params* p) {
   *out = nullptr;
   if (p->precision < XTC_PREC_FP64 || p->precision > XTC_PREC_BF16X3) return XTC_ERR_ARG;
   if (p->grid_chunk < 0 || p->grid_chunk % 128 != 0 || p->split_k < 0 || p->split_k > 16) return XTC_ERR_ARG;
+  if (p->range_stages < 0 || p->range_stages > 4) return XTC_ERR_ARG;
   if (cudaSetDevice(p->device) != cudaSuccess) {
     cudaGetLastError();
     return XTC_ERR_CUDA;
@@ -308,6 +309,7 @@ int xtc_create(xtc_ctx** out, const xtc_params* p) {
   if (const char* s = std::getenv("XTC_VF_KD")) ctx->vf_kd = std::max(1, std::atoi(s));
   if (const char* s = std::getenv("XTC_AS_KD")) ctx->as_kd = std::max(1, std::atoi(s));
   if (const char* s = std::getenv("XTC_VF_FLUSH")) ctx->vf_flush = std::max(0, std::atoi(s));
+  if (p->range_stages > 0) ctx->vf_kd = ctx->as_kd = p->range_stages;
   if (!ensure(ctx->jp_dev, sizeof(JastrowParams)) || !ensure(ctx->err_dev, 16) || !ensure(ctx->flag_dev, 16)) {
     xtc_destroy(ctx);
     return XTC_ERR_OOM;
@@ -423,7 +425,7 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
     return fail(ctx, XTC_ERR_ARG, "bad sizes (n_grid=%lld, n_orb=%d) or null input", (long long)n_grid, n_orb);
   const bool f64 = ctx->prm.precision == XTC_PREC_FP64;
   if (!f64 && !vfield_tc_supported(ctx->jp.n_nuc))
-    return fail(ctx, XTC_ERR_UNSUPPORTED, "the tensor-core path supports 1..4 nuclei (got %d)", ctx->jp.n_nuc);
+    return fail(ctx, XTC_ERR_UNSUPPORTED, "the tensor-core path supports 1..8 nuclei (got %d)", ctx->jp.n_nuc);
   pl.N = n_orb;
   pl.NP = n_orb * (n_orb + 1) / 2;
   pl.NG = n_grid;
@@ -481,7 +483,7 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
         !ensure(ctx->rho, sizeof(double) * pl.NGp * pl.NP))
       return fail(ctx, XTC_ERR_OOM, "FP64 grid tables (%.2f GB)", 8.0 * pl.NGp * pl.NP / 1e9);
   } else {
-    const int js = 12;
+    const int js = jtab_stride(n_nuc);
     if (!ensure(ctx->jtab, sizeof(float) * pl.NGp * js) ||
         !ensure(ctx->rho, 2ull * pl.parts_b * pl.NGp * pl.NP) || !ensure(ctx->colmax, 4ull * pl.NP) ||
         !ensure(ctx->colexp, 4ull * pl.NP))
@@ -495,7 +497,7 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
       launch_rho_f64(*d_phi, *d_w, n_grid, pl.NGp, n_orb, ctx->pair_p.as<int>(), ctx->pair_q.as<int>(),
                      ctx->rho.as<double>(), st);
     } else {
-      const int js = 12;
+      const int js = jtab_stride(n_nuc);
       launch_jtab(*d_grid, n_grid, pl.NGp, ctx->jp_dev.as<JastrowParams>(), n_nuc, js, ctx->jtab.as<float>(), st);
       launch_rho_split(ctx->phiT.as<double>(), *d_w, n_grid, pl.NGp, n_orb, pl.parts_b, pl.parts_b == 3,
                        pl.parts_b == 2, ctx->pair_p.as<int>(), ctx->pair_q.as<int>(), ctx->colmax.as<unsigned int>(),

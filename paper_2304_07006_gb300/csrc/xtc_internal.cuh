@@ -45,6 +45,9 @@ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // (fp16 step d) tiles fit in a row.
 inline int64_t m_stride(int64_t n_pair) { return round_up(n_pair, 384); }
 
+// Floats per inner point in the gradient producer's table: 12 for up to 4 nuclei, 16 for 5..8.
+inline int jtab_stride(int n_nuc) { return n_nuc <= 4 ? 12 : 16; }
+
 // ---------------------------------------------------------------- launchers
 
 // Per-inner-point table for the producer: stride js floats per point:

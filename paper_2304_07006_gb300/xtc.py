@@ -25,7 +25,8 @@ EXPORTED = ("xtc_default_params", "xtc_create", "xtc_destroy", "xtc_strerror", "
 
 class XtcParams(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int),
-                ("grid_chunk", ctypes.c_int64), ("split_k", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("grid_chunk", ctypes.c_int64), ("split_k", ctypes.c_int), ("timing", ctypes.c_int),
+                ("range_stages", ctypes.c_int)]
 
 
 class XtcInstance(ctypes.Structure):
@@ -105,7 +106,8 @@ def _f64(a):
 class Context:
     """One library context (one device, one stream, one precision)."""
 
-    def __init__(self, precision="fp16x2", device=0, stream=None, grid_chunk=0, split_k=0, timing=False):
+    def __init__(self, precision="fp16x2", device=0, stream=None, grid_chunk=0, split_k=0, timing=False,
+                 range_stages=0):
         lib = load()
         self._lib = lib
         p = XtcParams()
@@ -116,6 +118,7 @@ class Context:
         p.grid_chunk = grid_chunk
         p.split_k = split_k
         p.timing = 1 if timing else 0
+        p.range_stages = range_stages
         h = ctypes.c_void_p()
         rc = lib.xtc_create(ctypes.byref(h), ctypes.byref(p))
         if rc != 0:

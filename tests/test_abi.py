@@ -47,11 +47,14 @@ def test_strerror_and_defaults_without_gpu():
     assert b"symmetric" in lib.xtc_strerror(-2)
     p = xtc.XtcParams()
     lib.xtc_default_params(ctypes.byref(p))
-    assert p.precision == xtc.PREC_FP16X2 and p.grid_chunk == 0
+    assert p.precision == xtc.PREC_FP16X2 and p.grid_chunk == 0 and p.range_stages == 0
     # argument checks happen before any device call
     h = ctypes.c_void_p()
     assert lib.xtc_create(ctypes.byref(h), None) == -1
     p.grid_chunk = 100  # not a multiple of 128
+    assert lib.xtc_create(ctypes.byref(h), ctypes.byref(p)) == -1
+    p.grid_chunk = 0
+    p.range_stages = 5  # ranges of 1..4 stages
     assert lib.xtc_create(ctypes.byref(h), ctypes.byref(p)) == -1
 
 

@@ -173,26 +173,30 @@ def test_error_statuses(small):
         with pytest.raises(XtcError) as e:
             c.build(p.grid, p.weights, phi, g)
         assert e.value.code == -3                              # non-finite input
-        five = np.vstack([p.nuc_xyz, p.nuc_xyz + 1.0, [[3.0, 0, 0]]])
-        c.set_jastrow(five, [0] * 5, p.terms, p.coef[:1])
+        nine = np.vstack([p.nuc_xyz + 0.7 * k for k in range(4)] + [[[3.0, 0, 0]]])
+        c.set_jastrow(nine, [0] * 9, p.terms, p.coef[:1])
         with pytest.raises(XtcError) as e:
             c.build(p.grid, p.weights, p.phi, g)
-        assert e.value.code == -8                              # > 4 nuclei on tensor cores
+        assert e.value.code == -8                              # > 8 nuclei on tensor cores
         # the context stays usable after errors
         c.set_jastrow(p.nuc_xyz, p.nuc_set, p.terms, p.coef)
         c.build(p.grid, p.weights, p.phi, g)
 
 
-def test_fp64_path_takes_many_nuclei():
+@pytest.mark.parametrize("n_nuc", [5, 7, 8])
+@pytest.mark.parametrize("prec", ["fp64", "fp16x2", "bf16x3"])
+def test_many_nuclei_all_precisions(prec, n_nuc):
+    """5..8 Jastrow centres: the tensor-core producer's wide inner table and its 8-centre
+    template, with unused slots zero for 5 and 7 centres."""
     p = synth.make_small(n_orb=3, n_rad=4, n_theta=3, n_phi=3, n_atoms=2, seed=1)
-    rng = np.random.default_rng(2)
-    nuc = rng.uniform(-2, 2, size=(7, 3))
+    rng = np.random.default_rng(2 + n_nuc)
+    nuc = rng.uniform(-2, 2, size=(n_nuc, 3))
     from dataclasses import replace
-    p = replace(p, nuc_xyz=nuc, nuc_set=np.arange(7) % 2, coef=rng.uniform(-0.1, 0.1, (2, 9)))
-    ref = direct.build(p)
-    with ctx_for(p, "fp64") as c:
-        out = c.build(p.grid, p.weights, p.phi, p.gamma)
-    assert max_err(out, ref) < 1e-12
+    p = replace(p, nuc_xyz=nuc, nuc_set=np.arange(n_nuc) % 2, coef=rng.uniform(-0.1, 0.1, (2, 9)))
+    ref = direct.build(p, synth.random_density(3, n_nuc))
+    with ctx_for(p, prec) as c:
+        out = c.build(p.grid, p.weights, p.phi, synth.random_density(3, n_nuc))
+    assert max_err(out, ref) < (1e-12 if prec == "fp64" else TOL[prec])
 
 
 # ------------------------------------------------------------------ measured workloads
@@ -264,6 +268,46 @@ def test_n2_workload_sampled_outer_points(n2_sampled, prec):
         out = c.build(p.grid, p.weights, p.phi, p.gamma, want_dU=True)
     err = max_err(out, ref)
     assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("stages", [1, 3, 4])
+@pytest.mark.parametrize("prec", MIXED)
+def test_accumulation_range_lengths(small, prec, stages):
+    """Every tensor-core accumulation range length the parameter accepts (2 is the default)."""
+    p, g, ref = small
+    with ctx_for(p, prec, range_stages=stages) as c:
+        out = c.build(p.grid, p.weights, p.phi, g)
+    assert max_err(out, ref) < TOL[prec]
+
+
+def _host_ram_gb():
+    try:
+        import os
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 1e9
+    except (ValueError, OSError, AttributeError):
+        return 0.0
+
+
+@pytest.fixture(scope="module")
+def large_sampled():
+    """The N=200, 200,000-point workload (8 nuclei, two centre sets) on 2 sampled outer points;
+    the oracle's dense N^4 Delta U takes about 13 GB and its assembly several times that."""
+    if _host_ram_gb() < 96:
+        pytest.skip("the N=200 oracle needs about 64 GB of host memory")
+    p = _sampled("large", 2, 14)
+    return p, direct.build(p, outer=np.arange(2))
+
+
+@pytest.mark.parametrize("prec", ["fp16x2", "fp64"])
+def test_large_workload_sampled_outer_points(large_sampled, prec):
+    p, ref = large_sampled
+    with ctx_for(p, prec) as c:
+        c.set_outer_range(0, 2)
+        out = c.build(p.grid, p.weights, p.phi, p.gamma, want_dU=False)
+    ref = {"dh": ref["dh"], "e0": ref["e0"]}
+    errs = [np.abs(np.asarray(out[k], dtype=np.float64).reshape(-1) - np.asarray(ref[k]).reshape(-1)).max()
+            / max(1.0, np.abs(np.asarray(ref[k])).max()) for k in ("dh", "e0")]
+    assert max(errs) < TOL[prec], errs
 
 
 # ------------------------------------------------------------------ batched build
