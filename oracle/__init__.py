@@ -9,10 +9,14 @@ from its equations and sharing nothing with the CUDA library:
                      Appendix B (Delta U, Delta h, <Phi0|L|Phi0>), with the
                      intermediate vector field V of the "Decomposition of two-body
                      correction" section.
+* ``spin``        -- Route 2 for two spin densities: the restricted open-shell
+                     working equations of Appendix A (Delta U^{aa}, ^{ab}, ^{bb},
+                     Delta h^a, Delta h^b, <Psi0|L|Psi0>).
 * ``bruteforce``  -- Route 1: the six-index L from eq. (Ldecomp) or from the
                      literal triple quadrature of its definition, normal-ordered
                      explicitly in spin orbitals with eqs. (dU), (Delta h with the
-                     two-body density), (zero-body) and (1Ddens).
+                     two-body density), (zero-body) and (1Ddens), for one density
+                     or for separate alpha and beta densities.
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU baseline leg of
 ``bench.py`` may import this package; the library never does.

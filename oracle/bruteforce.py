@@ -64,15 +64,19 @@ def L_triple(problem):
     return np.einsum("ijk,ipq,jrs,ktu->prtqsu", F, d, d, d, optimize=True)
 
 
-def spin_orbital(L, gamma):
-    """Spin-orbital L_so[P,R,T,Q,S,U] and gamma_so; P = p + N * sigma."""
+def spin_orbital(L, gamma, gamma_b=None):
+    """Spin-orbital L_so[P,R,T,Q,S,U] and gamma_so; P = p + N * sigma.  gamma is the alpha
+    density and gamma_b the beta one (default: the same, the closed-shell case)."""
     n = gamma.shape[0]
+    gb = gamma if gamma_b is None else np.asarray(gamma_b, dtype=np.float64)
     idx = np.arange(2 * n) % n
     spin = np.arange(2 * n) // n
     D = (spin[:, None] == spin[None, :]).astype(np.float64)
     Lso = L[np.ix_(idx, idx, idx, idx, idx, idx)]
     Lso = Lso * D[:, None, None, :, None, None] * D[None, :, None, None, :, None] * D[None, None, :, None, None, :]
-    gso = gamma[np.ix_(idx, idx)] * D
+    gso = np.zeros((2 * n, 2 * n))
+    gso[:n, :n] = gamma
+    gso[n:, n:] = gb
     return Lso, gso
 
 
@@ -112,6 +116,29 @@ def closed_shell_blocks(res, n):
             "dh": res["dh_from_dU"][np.ix_(a, a)], "dh_general": res["dh_general"][np.ix_(a, a)],
             "dh_beta": res["dh_from_dU"][np.ix_(b, b)],
             "e0": res["e_from_dh"], "e0_rdm": res["e_rdm"]}
+
+
+def spin_blocks(res, n):
+    """Spatial views of the spin blocks: dU_st[p,q,r,s] = Delta U_pr^qs with p, q of spin s and
+    r, s of spin t (s, t in {a, b}), Delta h^a and Delta h^b in both forms, and the constant in
+    both forms."""
+    a = np.arange(n)
+    b = a + n
+    dU = res["dU"]
+    blk = lambda s1, s2: dU[np.ix_(s1, s2, s1, s2)].transpose(0, 2, 1, 3)    # [P,R,Q,S] -> [p,q,r,s]
+    return {"dU_aa": blk(a, a), "dU_ab": blk(a, b), "dU_ba": blk(b, a), "dU_bb": blk(b, b),
+            "dh_a": res["dh_from_dU"][np.ix_(a, a)], "dh_b": res["dh_from_dU"][np.ix_(b, b)],
+            "dh_general_a": res["dh_general"][np.ix_(a, a)], "dh_general_b": res["dh_general"][np.ix_(b, b)],
+            "dh_ab": res["dh_from_dU"][np.ix_(a, b)],
+            "e0": res["e_from_dh"], "e0_rdm": res["e_rdm"]}
+
+
+def build_spin(problem, gamma_a, gamma_b, L=None):
+    """Route 1 with two spin densities: the spin blocks of the normal-ordered L."""
+    if L is None:
+        L = L_ldecomp(problem)
+    Lso, gso = spin_orbital(L, np.asarray(gamma_a, dtype=np.float64), gamma_b)
+    return spin_blocks(normal_order(Lso, gso), problem.n_orb)
 
 
 def build(problem, gamma=None, L=None):

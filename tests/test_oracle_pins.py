@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import bruteforce, direct, jastrow
+from oracle import bruteforce, direct, jastrow, spin
 
 
 def _jas(p):
@@ -221,3 +221,101 @@ def test_pins_catch_planted_mistakes(monkeypatch):
         assert np.abs(got - want).max() > 1e-6 * np.abs(want).max(), bad.__name__
     monkeypatch.setattr(direct, "intermediates", orig)
     assert np.abs(direct.build(p, g)["dU"] - want).max() < 1e-12 * np.abs(want).max()
+
+
+# ------------------------------------------------------------------ two spin densities (Appendix A)
+
+def _open_shell_densities(kind, n):
+    if kind == "rohf":                       # 2 alpha, 1 beta occupied orbitals of one orbital set
+        return np.diag([1.0, 1.0] + [0.0] * (n - 2)), np.diag([1.0] + [0.0] * (n - 1))
+    return synth.random_density(n, 31), synth.random_density(n, 32, rank=2)
+
+
+@pytest.mark.parametrize("kind", ["rohf", "random"])
+def test_open_shell_route2_matches_explicit_normal_ordering(kind):
+    """Appendix A against the spin-orbital definition (eq. dU, the general Delta h with the
+    two-body density, the zero-body term with the three-body density) for unequal spin densities."""
+    p = synth.make_small(n_orb=4, n_rad=4, n_theta=3, n_phi=3, n_atoms=3, seed=21)
+    ga, gb = _open_shell_densities(kind, 4)
+    r1 = bruteforce.build_spin(p, ga, gb)
+    r2 = spin.build(p, ga, gb)
+    scale = np.abs(r2["dU_aa"]).max()
+    assert scale > 1e-6
+    for k in ("dU_aa", "dU_ab", "dU_bb", "dh_a", "dh_b"):
+        assert np.abs(r1[k] - r2[k]).max() < 1e-12 * scale, k
+    assert abs(r1["e0"] - r2["e0"]) < 1e-12 * scale
+    # the spin-summed one-body form equals the general one, and the constant its three-body form
+    assert np.abs(r1["dh_general_a"] - r1["dh_a"]).max() < 1e-12 * scale
+    assert np.abs(r1["dh_general_b"] - r1["dh_b"]).max() < 1e-12 * scale
+    assert abs(r1["e0_rdm"] - r1["e0"]) < 1e-12 * scale
+    assert np.abs(r1["dh_ab"]).max() == 0.0                                  # no spin-flip block
+    assert np.abs(r1["dU_ba"] - r1["dU_ab"].transpose(2, 3, 0, 1)).max() < 1e-14 * scale
+    # unequal densities give unequal blocks (the test would not see a spin mix-up otherwise)
+    assert np.abs(r2["dU_aa"] - r2["dU_bb"]).max() > 1e-3 * scale
+    assert np.abs(r2["dU_ab"] - r2["dU_aa"]).max() > 1e-3 * scale
+
+
+def test_open_shell_equal_densities_reduce_to_closed_shell():
+    """gamma^a = gamma^b: every block is the closed-shell Delta U of Appendix B."""
+    p = synth.make_small(n_orb=4, n_rad=4, n_theta=3, n_phi=3, n_atoms=3, seed=21)
+    g = synth.random_density(4, 9)
+    c = direct.build(p, g)
+    s2 = spin.build(p, g, g)
+    scale = np.abs(c["dU"]).max()
+    for k in ("dU_aa", "dU_ab", "dU_bb"):
+        assert np.abs(s2[k] - c["dU"]).max() < 1e-13 * scale
+    assert np.abs(s2["dh_a"] - c["dh"]).max() < 1e-13 * scale
+    assert np.abs(s2["dh_b"] - c["dh"]).max() < 1e-13 * scale
+    assert abs(s2["e0"] - c["e0"]) < 1e-13 * scale
+
+
+def test_open_shell_spin_flip(small):
+    """Exchanging the two densities exchanges the spin labels of every output."""
+    p, _, _ = small
+    ga, gb = synth.random_density(p.n_orb, 41), synth.random_density(p.n_orb, 42, rank=1)
+    r = spin.build(p, ga, gb)
+    f = spin.build(p, gb, ga)
+    scale = np.abs(r["dU_aa"]).max()
+    assert np.abs(f["dU_aa"] - r["dU_bb"]).max() < 1e-13 * scale
+    assert np.abs(f["dU_bb"] - r["dU_aa"]).max() < 1e-13 * scale
+    assert np.abs(f["dU_ab"] - r["dU_ab"].transpose(2, 3, 0, 1)).max() < 1e-13 * scale
+    assert np.abs(f["dh_a"] - r["dh_b"]).max() < 1e-13 * scale
+    assert abs(f["e0"] - r["e0"]) < 1e-13 * scale
+
+
+def test_open_shell_pins_catch_planted_mistakes(monkeypatch):
+    """A direct term from one spin's density, the two spins' exchange terms interchanged, or a
+    dropped half in B must break agreement with the spin-orbital definition."""
+    p = synth.make_small(n_orb=3, n_rad=3, n_theta=2, n_phi=3, n_atoms=2, seed=3)
+    ga, gb = synth.random_density(3, 6), synth.random_density(3, 7, rank=1)
+    want = bruteforce.build_spin(p, ga, gb)
+    orig = spin.intermediates
+
+    def direct_from_alpha_only(V, w, phi, a, b):
+        # exchange parts right, direct parts (W, Wt) from 2 gamma^a instead of gamma^a + gamma^b
+        rho, good = orig(V, w, phi, a, b)
+        Wd = np.einsum("ixtu,tu->ix", V, a - b)
+        Wtd = np.einsum("itu,tu->i", rho, a - b)
+        out = {}
+        for s in ("a", "b"):
+            A, B = good[s]
+            out[s] = (A + np.einsum("ix,ixrs->irs", Wd, V), B + 0.5 * Wtd[:, None, None, None] * V)
+        return rho, out
+
+    def spins_interchanged(V, w, phi, a, b):
+        rho, out = orig(V, w, phi, a, b)
+        return rho, {"a": out["b"], "b": out["a"]}
+
+    def dropped_half(V, w, phi, a, b):
+        rho, out = orig(V, w, phi, a, b)
+        Wt = np.einsum("itu,tu->i", rho, a + b)
+        return rho, {s: (A, B + 0.5 * Wt[:, None, None, None] * V) for s, (A, B) in out.items()}
+
+    for bad in (direct_from_alpha_only, spins_interchanged, dropped_half):
+        monkeypatch.setattr(spin, "intermediates", bad)
+        got = spin.build(p, ga, gb)
+        worst = max(np.abs(got[k] - want[k]).max() / np.abs(want[k]).max() for k in ("dU_aa", "dU_ab", "dU_bb"))
+        assert worst > 1e-6, bad.__name__
+    monkeypatch.setattr(spin, "intermediates", orig)
+    got = spin.build(p, ga, gb)
+    assert max(np.abs(got[k] - want[k]).max() for k in ("dU_aa", "dU_ab", "dU_bb")) < 1e-12 * np.abs(want["dU_aa"]).max()
