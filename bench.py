@@ -98,9 +98,9 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one vfield_tc_kernel<2> launch on the first 1184
+# dram__bytes_read.sum + dram__bytes_write.sum of one vfield_tc_kernel<2,0> launch on the first 1184
 # outer points of the workload (profiles/vfield_tc_n2.md); valid for that kernel version only
-VFIELD_DRAM_BYTES_CAPTURED = None  # re-captured after the FP64-flush change
+VFIELD_DRAM_BYTES_CAPTURED = 19_595_734_016 + 2_730_386_688
 VFIELD_CAPTURE_OUTER = 1184
 
 
