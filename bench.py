@@ -196,6 +196,44 @@ def batched_measure(args, torch, dev, local):
             "note": "wall time of one call (host + device), inputs on the device, dU not unpacked"}
 
 
+def rohf_measure(args, torch, dev, local, p, s_closed):
+    """The spin-resolved build (Appendix A) on the same workload with 8 alpha and 7 beta occupied
+    orbitals: inputs and outputs on the device, Delta U formed but not unpacked, one warm-up and
+    two timed builds (CUDA events).  Algorithmic work: step (b) once, steps (c) and (d) once per
+    spin of electron 2."""
+    from paper_2304_07006_gb300 import Context
+    from paper_2304_07006_gb300.xtc import KERNEL_NAMES
+
+    N, NG = p.n_orb, p.n_grid
+    F = flops(N, NG)
+    total = F["b"] + 2 * F["c"] + 2 * F["d"]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    ga = t(np.diag([1.0] * 8 + [0.0] * (N - 8)))
+    gb = t(np.diag([1.0] * 7 + [0.0] * (N - 7)))
+    grid, w, phi = t(p.grid), t(p.weights), t(p.phi)
+    outs = {k: torch.empty((N, N), dtype=torch.float64, device=dev) for k in ("dh_a", "dh_b")}
+    outs["e0"] = torch.empty(1, dtype=torch.float64, device=dev)
+    steps = 2
+    with Context(args.precision, device=local, timing=True) as c:
+        c.set_jastrow(p.nuc_xyz, p.nuc_set, p.terms, p.coef)
+        c.build_rohf(grid, w, phi, ga, gb, want_dU=False, **outs)
+        stream = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        per = {k: 0.0 for k in KERNEL_NAMES}
+        for _ in range(steps):
+            c.build_rohf(grid, w, phi, ga, gb, want_dU=False, **outs)
+            for k, (ms, _) in c.timings().items():
+                per[k] += ms / steps
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sec = e0.elapsed_time(e1) / 1e3 / steps
+    return {"densities": "8 alpha, 7 beta occupied orbitals (diagonal)", "seconds_per_build": sec,
+            "algorithmic_flops": total, "tflops": total / sec / 1e12, "time_vs_closed_shell_build": sec / s_closed,
+            "per_kernel_ms": per, "note": "inputs and outputs on the device; Delta U not unpacked"}
+
+
 def run_ncu_case(args):
     """A small, quick build (same workload, outer sum restricted to P points) for kernel captures."""
     import synth
@@ -222,6 +260,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--batched", type=int, default=32, metavar="N",
                     help="also time the batched workload of N uneven instances (0: skip)")
+    ap.add_argument("--rohf", type=int, default=1, help="also time the spin-resolved build (0: skip)")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="P",
                     help="profiling aid: run one warm-up and one build of the workload restricted to the first P "
                          "outer points, print a one-line summary and exit (no benchmark line)")
@@ -381,6 +420,8 @@ def main():
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         if args.batched:
             line["batched"] = batched_measure(args, torch, dev, local)
+        if args.rohf:
+            line["rohf"] = rohf_measure(args, torch, dev, local, p, ms_step / 1e3)
         line["cpu_baseline"] = oracle_sample(p, args.cpu_sample)
         line["cpu_baseline"].pop("seconds", None)
         print(json.dumps(line), flush=True)

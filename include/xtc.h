@@ -142,6 +142,25 @@ XTC_API int xtc_set_outer_range(xtc_ctx* ctx, int64_t begin, int64_t end);
 XTC_API int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
                    const double* phi, const double* gamma, double* dU, float* dU_f32, double* dh, double* e0);
 
+/* The xTC build for two spin densities (Appendix A, "Restricted open-shell working equations"):
+ * both spins share the real orbitals phi and the Jastrow factor, so steps (a) and (b) are
+ * spin-free; steps (c) and (d) run once per spin of electron 2, with the direct terms (W, Wt)
+ * from gamma_a + gamma_b and the exchange terms from that spin's density.
+ *   n_grid, n_orb, grid_xyz, weights, phi           -- as in xtc_build_1b2b
+ *   gamma_a, gamma_b [n_orb][n_orb] symmetric alpha and beta densities (occupied = 1), FP64
+ *   dU_aa, dU_ab, dU_bb [n_orb]^4 FP64, each may be NULL -- dU_st[p][q][r][s] = [Delta U_pr^qs]^{st},
+ *                        electron 1 (p, q) of spin s, electron 2 (r, s) of spin t; the beta-alpha
+ *                        block is dU_ba[p][q][r][s] = dU_ab[r][s][p][q]
+ *   dh_a, dh_b [n_orb][n_orb] FP64 (required): [Delta h_p^q]^a and ^b
+ *   e0 [1] FP64 (required): <Psi0|L|Psi0> = -1/3 sum_s dh_s . gamma_s
+ * With gamma_a = gamma_b = gamma every block equals xtc_build_1b2b's Delta U, dh_a = dh_b its
+ * Delta h and e0 its constant (to rounding).  Pointers may be host or device memory; the call
+ * returns when the outputs are complete.  Workspace: two more N_pair^2 FP64 accumulators than
+ * xtc_build_1b2b.  Errors: as xtc_build_1b2b. */
+XTC_API int xtc_build_1b2b_rohf(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz,
+                        const double* weights, const double* phi, const double* gamma_a, const double* gamma_b,
+                        double* dU_aa, double* dU_ab, double* dU_bb, double* dh_a, double* dh_b, double* e0);
+
 /* Step (a) alone: out[k][0..2] = nabla_1 u(r1[k], r2[k]) in FP64 arithmetic on the device.
  * r1, r2 [n][3], out [n][3]. */
 XTC_API int xtc_jastrow_grad(xtc_ctx* ctx, int64_t n, const double* r1, const double* r2, double* out);

@@ -417,6 +417,70 @@ __global__ void onebody_kernel(const double* __restrict__ U, const double* __res
   if (threadIdx.x == 0) dh[p * N + q] = -0.5 * red[0];
 }
 
+// Spin builds (Appendix A): U[pq][rs] = -(Fb[pq][rs] + Fa[rs][pq]) = Delta U^{ab}(pq|rs), where
+// Ft[pq][rs] = sum_i rho_pq A^t_rs + V_pq.B^t_rs; one CTA per 32 x 32 tile of U.
+__global__ void spin_cross_kernel(const double* __restrict__ Fb, const double* __restrict__ Fa, int n_pair, int ldm,
+                                  double* __restrict__ U) {
+  __shared__ double T[32][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int ra = j0 + r, ca = i0 + threadIdx.x;  // T[r][x] = Fa[j0 + r][i0 + x]
+    T[r][threadIdx.x] = (ra < n_pair && ca < n_pair) ? Fa[static_cast<int64_t>(ra) * ldm + ca] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int row = i0 + r, col = j0 + threadIdx.x;
+    if (row < n_pair && col < n_pair)
+      U[static_cast<int64_t>(row) * ldm + col] = -(Fb[static_cast<int64_t>(row) * ldm + col] + T[threadIdx.x][r]);
+  }
+}
+
+// Delta h^s_pq = -1/2 (sum_rs U^{ss}(pq|rs) g^s_rs + sum_rs U^{st}(pq|rs) g^t_rs - sum_rs U^{ss}(ps|rq) g^s_rs),
+// t the other spin, U^{ba}(pq|rs) = U^{ab}(rs|pq) (Appendix A); one CTA per (p, q, s).
+__global__ void onebody_spin_kernel(const double* __restrict__ Uaa, const double* __restrict__ Uab,
+                                    const double* __restrict__ Ubb, const double* __restrict__ ga,
+                                    const double* __restrict__ gb, int N, int ldm, double* __restrict__ dh_a,
+                                    double* __restrict__ dh_b) {
+  const int p = blockIdx.y, q = blockIdx.x, sp = blockIdx.z;
+  const double* Us = sp ? Ubb : Uaa;
+  const double* gs = sp ? gb : ga;
+  const double* go = sp ? ga : gb;
+  const int pq = pair_of(p, q, N);
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < N * N; k += blockDim.x) {
+    const int r = k / N, s = k % N;
+    const int rs = pair_of(r, s, N);
+    const double cross = sp ? Uab[static_cast<int64_t>(rs) * ldm + pq] : Uab[static_cast<int64_t>(pq) * ldm + rs];
+    acc += gs[k] * (Us[static_cast<int64_t>(pq) * ldm + rs] -
+                    Us[static_cast<int64_t>(pair_of(p, s, N)) * ldm + pair_of(r, q, N)]) +
+           go[k] * cross;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) (sp ? dh_b : dh_a)[p * N + q] = -0.5 * red[0];
+}
+
+// e0 = -1/3 sum_pq (Delta h^a_pq gamma^a_pq + Delta h^b_pq gamma^b_pq)  (Appendix A)
+__global__ void constant_spin_kernel(const double* __restrict__ dh_a, const double* __restrict__ ga,
+                                     const double* __restrict__ dh_b, const double* __restrict__ gb, int n2,
+                                     double* __restrict__ e0) {
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n2; k += blockDim.x) acc += dh_a[k] * ga[k] + dh_b[k] * gb[k];
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *e0 = -1.0 / 3.0 * red[0];
+}
+
 // e0 = -2/3 sum_pq Delta h_pq gamma_pq
 __global__ void constant_kernel(const double* __restrict__ dh, const double* __restrict__ gamma, int n2,
                                 double* __restrict__ e0) {
@@ -542,6 +606,19 @@ void launch_onebody(const double* M, const double* gamma, int n_orb, int n_pair,
   const int ldm = static_cast<int>(m_stride(n_pair));
   onebody_kernel<<<dim3(n_orb, n_orb), 256, 0, st>>>(M, gamma, n_orb, ldm, dh);
   constant_kernel<<<1, 256, 0, st>>>(dh, gamma, n_orb * n_orb, e0);
+}
+
+void launch_spin_cross(const double* Fb, const double* Fa, int n_pair, double* U, cudaStream_t st) {
+  const int ldm = static_cast<int>(m_stride(n_pair));
+  dim3 g(blocks_for(n_pair, 32), blocks_for(n_pair, 32));
+  spin_cross_kernel<<<g, dim3(32, 8), 0, st>>>(Fb, Fa, n_pair, ldm, U);
+}
+
+void launch_onebody_spin(const double* Uaa, const double* Uab, const double* Ubb, const double* ga, const double* gb,
+                         int n_orb, int n_pair, double* dh_a, double* dh_b, double* e0, cudaStream_t st) {
+  const int ldm = static_cast<int>(m_stride(n_pair));
+  onebody_spin_kernel<<<dim3(n_orb, n_orb, 2), 256, 0, st>>>(Uaa, Uab, Ubb, ga, gb, n_orb, ldm, dh_a, dh_b);
+  constant_spin_kernel<<<1, 256, 0, st>>>(dh_a, ga, dh_b, gb, n_orb * n_orb, e0);
 }
 
 void launch_vfield_export(const void* V, bool f64, int splits, int n_pair, int64_t n_i, int64_t gcp, double* out,

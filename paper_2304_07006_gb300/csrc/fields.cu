@@ -5,10 +5,13 @@
 //     X_x    = gamma V_x                Zt  = V_x . X_x  (= sum_x V_x gamma V_x)
 //     Y_x    = V_x gamma                Z_x = rho X_x + Y_x rho
 //     A      = Vt - Zt                  B_x = 1/2 Wt V_x - Z_x
-// With gamma = sum_k lam_k c_k c_k^T (the library factorises it on the host) the N^3 products
-// become rank-r updates: H_xk = V_x c_k, Zt = sum_xk lam_k H_xk H_xk^T, W_x = 2 sum_k lam_k c_k.H_xk,
-// h_x = V_x gamma phi = sum_k lam_k (c_k.phi) H_xk, Z_x = w (phi h_x^T + h_x phi^T),
-// Wt = 2 w sum_k lam_k (c_k.phi)^2.  (Exact reformulation; no approximation.)
+// and of Appendix A (restricted open shell) for electron-2 spin t: the same with the direct
+// density 2 gamma replaced by gamma^a + gamma^b (in W, Wt) and the exchange density gamma by
+// gamma^t (in X, Y, Zt, Z).  The library factorises both on the host over one set of vectors c_k:
+// g_d = sum_k lamd_k c_k c_k^T (direct), gamma_x = sum_k lam_k c_k c_k^T (exchange), so that the N^3
+// products become rank-r updates: H_xk = V_x c_k, Zt = sum_xk lam_k H_xk H_xk^T,
+// W_x = sum_k lamd_k c_k.H_xk, h_x = V_x gamma_x phi = sum_k lam_k (c_k.phi) H_xk,
+// Z_x = w (phi h_x^T + h_x phi^T), Wt = w sum_k lamd_k (c_k.phi)^2.  (Exact reformulation.)
 //
 // A CTA owns `pts` consecutive outer points (lane-contiguous, so every global read of V is a
 // contiguous run of the outer index) and all orbital pairs; H for its points lives in shared
@@ -31,6 +34,7 @@ struct FieldsSmem {
   TC* ws;    // [P]
   TC* cs;    // [R][N]
   TC* lam;   // [R]
+  TC* lamd;  // [R]
   TC* cph;   // [R][P]
   TC* Hs;    // [3][R][N][P]
   TC* hs;    // [3][N][P]
@@ -42,10 +46,11 @@ struct FieldsSmem {
 template <typename TC>
 __host__ __device__ inline size_t carve(FieldsSmem<TC>* s, uint8_t* base, int N, int R, int P) {
   size_t off = 0;
-  TC* p[10];
-  const size_t n[10] = {static_cast<size_t>(N) * P,
+  TC* p[11];
+  const size_t n[11] = {static_cast<size_t>(N) * P,
                         static_cast<size_t>(P),
                         static_cast<size_t>(R) * N,
+                        static_cast<size_t>(R),
                         static_cast<size_t>(R),
                         static_cast<size_t>(R) * P,
                         static_cast<size_t>(3) * R * N * P,
@@ -53,11 +58,11 @@ __host__ __device__ inline size_t carve(FieldsSmem<TC>* s, uint8_t* base, int N,
                         static_cast<size_t>(3) * P,
                         static_cast<size_t>(P),
                         static_cast<size_t>(3) * R * P};
-  for (int k = 0; k < 10; ++k) {
+  for (int k = 0; k < 11; ++k) {
     p[k] = reinterpret_cast<TC*>(base + off);
     off += ((n[k] * sizeof(TC) + 15) / 16) * 16;
   }
-  if (s) *s = FieldsSmem<TC>{p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8], p[9]};
+  if (s) *s = FieldsSmem<TC>{p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8], p[9], p[10]};
   return off;
 }
 
@@ -131,7 +136,10 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
     sm.ws[k] = i < a.n_i ? static_cast<TC>(a.w[a.i0 + i]) : TC(0);
   }
   for (int k = t; k < R * N; k += THREADS) sm.cs[k] = static_cast<TC>(a.evec[k]);
-  for (int k = t; k < R; k += THREADS) sm.lam[k] = static_cast<TC>(a.lam[k]);
+  for (int k = t; k < R; k += THREADS) {
+    sm.lam[k] = static_cast<TC>(a.lam[k]);
+    sm.lamd[k] = static_cast<TC>(a.lamd[k]);
+  }
   __syncthreads();
   for (int k = t; k < R * P; k += THREADS) {
     const int kk = k / P, q = k % P;
@@ -142,8 +150,8 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
   __syncthreads();
   for (int q = t; q < P; q += THREADS) {
     TC acc = 0;
-    for (int kk = 0; kk < R; ++kk) acc += sm.lam[kk] * sm.cph[kk * P + q] * sm.cph[kk * P + q];
-    sm.Wt[q] = TC(2) * sm.ws[q] * acc;
+    for (int kk = 0; kk < R; ++kk) acc += sm.lamd[kk] * sm.cph[kk * P + q] * sm.cph[kk * P + q];
+    sm.Wt[q] = sm.ws[q] * acc;
   }
 
   // ---------------------------------------------------------------- phase 1: H_xk = V_x c_k, h_x
@@ -182,19 +190,19 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
     sm.hs[(x * N + p) * P + pt] = h;
   }
   __syncthreads();
-  // W_x = 2 sum_k lam_k sum_p c_k[p] H_xk[p]  (deterministic two-level sum)
+  // W_x = sum_k lamd_k sum_p c_k[p] H_xk[p]  (deterministic two-level sum)
   for (int k = t; k < 3 * R * P; k += THREADS) {
     const int q = k % P, xk = k / P, kk = xk % R;
     TC acc = 0;
     for (int p = 0; p < N; ++p) acc += sm.cs[kk * N + p] * sm.Hs[(xk * N + p) * P + q];
-    sm.part[k] = sm.lam[kk] * acc;
+    sm.part[k] = sm.lamd[kk] * acc;
   }
   __syncthreads();
   for (int k = t; k < 3 * P; k += THREADS) {
     const int x = k / P, q = k % P;
     TC acc = 0;
     for (int kk = 0; kk < R; ++kk) acc += sm.part[(x * R + kk) * P + q];
-    sm.Wv[k] = TC(2) * acc;
+    sm.Wv[k] = acc;
   }
   __syncthreads();
 

@@ -63,6 +63,7 @@ struct xtc_ctx {
   DBuf grid, w, phi, gamma, phiT, pair_p, pair_q;
   DBuf jtab, jtab64, rho, colmax, colexp, G;
   DBuf V, Vacc, L, R, L32, R32, eL, eR, M, evec, lam, dU_tmp, dh_tmp, e0_tmp, vout, r1, r2;
+  DBuf lamd, gamma_b, M2, M3;  // direct weights; spin builds: beta density, f^b, Delta U^{ab}
   // prepared state key (pair tables)
   int pair_n = -1;
   // timers
@@ -327,7 +328,8 @@ int xtc_destroy(xtc_ctx* ctx) {
                   &ctx->phiT, &ctx->pair_p, &ctx->pair_q, &ctx->jtab, &ctx->jtab64, &ctx->rho, &ctx->colmax,
                   &ctx->colexp, &ctx->G, &ctx->V, &ctx->Vacc, &ctx->L, &ctx->R, &ctx->L32, &ctx->R32,
                   &ctx->eL, &ctx->eR, &ctx->M, &ctx->evec, &ctx->lam, &ctx->dU_tmp,
-                  &ctx->dh_tmp, &ctx->e0_tmp, &ctx->vout, &ctx->r1, &ctx->r2};
+                  &ctx->dh_tmp, &ctx->e0_tmp, &ctx->vout, &ctx->r1, &ctx->r2,
+                  &ctx->lamd, &ctx->gamma_b, &ctx->M2, &ctx->M3};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (xtc_ctx* lane : ctx->lanes) xtc_destroy(lane);
@@ -593,63 +595,128 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
 
 }  // namespace
 
-extern "C" int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
-                              const double* phi, const double* gamma, double* dU, float* dU_f32, double* dh,
-                              double* e0) {
-  if (!ctx) return XTC_ERR_ARG;
-  if (!gamma || !dh || !e0) return fail(ctx, XTC_ERR_ARG, "gamma, dh and e0 are required");
-  CUDA_OK(cudaSetDevice(ctx->prm.device));
-  reset_timers(ctx);
-  cudaStream_t st = ctx->st;
+namespace {
 
-  // ---- gamma: symmetry, finiteness, factorisation gamma = sum_k lam_k c_k c_k^T
-  if (n_orb < 1 || n_orb > MAX_ORB) return fail(ctx, XTC_ERR_ARG, "n_orb=%d out of range", n_orb);
-  const int N = n_orb;
-  std::vector<double> g(static_cast<size_t>(N) * N);
+// One density matrix, read, checked and factorised on the host: gamma = sum_k lam_k c_k c_k^T
+// (cyclic Jacobi, exact to rounding), eigenvalues below 1e-13 of the largest dropped.
+struct Density {
+  std::vector<double> g, lam, ev;  // ev[k][p]
+  int rank = 0;
+};
+
+int read_density(xtc_ctx* ctx, const double* gamma, int N, const char* name, Density& d) {
+  cudaStream_t st = ctx->st;
+  d.g.assign(static_cast<size_t>(N) * N, 0.0);
   if (is_device_ptr(gamma)) {
-    CUDA_OK(cudaMemcpyAsync(g.data(), gamma, g.size() * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaMemcpyAsync(d.g.data(), gamma, d.g.size() * 8, cudaMemcpyDeviceToHost, st));
     CUDA_OK(cudaStreamSynchronize(st));
+  } else {
+    std::memcpy(d.g.data(), gamma, d.g.size() * 8);
   }
-  else std::memcpy(g.data(), gamma, g.size() * 8);
   double gmax = 0.0, asym = 0.0;
   for (int p = 0; p < N; ++p)
     for (int q = 0; q < N; ++q) {
-      const double v = g[static_cast<size_t>(p) * N + q];
-      if (!std::isfinite(v)) return fail(ctx, XTC_ERR_NONFINITE, "gamma has NaN/Inf");
+      const double v = d.g[static_cast<size_t>(p) * N + q];
+      if (!std::isfinite(v)) return fail(ctx, XTC_ERR_NONFINITE, "%s has NaN/Inf", name);
       gmax = std::max(gmax, std::fabs(v));
-      asym = std::max(asym, std::fabs(v - g[static_cast<size_t>(q) * N + p]));
+      asym = std::max(asym, std::fabs(v - d.g[static_cast<size_t>(q) * N + p]));
     }
-  if (asym > 1e-12 * gmax) return fail(ctx, XTC_ERR_NOT_SYMMETRIC, "max |gamma - gamma^T| = %g", asym);
-  std::vector<double> a = g, vecs;
+  if (asym > 1e-12 * gmax) return fail(ctx, XTC_ERR_NOT_SYMMETRIC, "max |%s - %s^T| = %g", name, name, asym);
+  std::vector<double> a = d.g, vecs;
   jacobi_eigen(a, vecs, N);
   double lmax = 0.0;
   for (int k = 0; k < N; ++k) lmax = std::max(lmax, std::fabs(a[static_cast<size_t>(k) * N + k]));
-  std::vector<double> lam, ev;  // ev[k][p]
+  d.lam.clear();
+  d.ev.clear();
   for (int k = 0; k < N; ++k) {
     const double l = a[static_cast<size_t>(k) * N + k];
     if (std::fabs(l) <= 1e-13 * lmax || l == 0.0) continue;
-    lam.push_back(l);
-    for (int p = 0; p < N; ++p) ev.push_back(vecs[static_cast<size_t>(p) * N + k]);
+    d.lam.push_back(l);
+    for (int p = 0; p < N; ++p) d.ev.push_back(vecs[static_cast<size_t>(p) * N + k]);
   }
-  const int rank = static_cast<int>(lam.size());
+  d.rank = static_cast<int>(d.lam.size());
+  return XTC_OK;
+}
+
+// What a build writes: the closed-shell Delta U (dU[0] / dU32), Delta h (dh[0]) and e0, or the
+// spin blocks aa, ab, bb (dU[0..2]), Delta h^a, Delta h^b (dh[0..1]) and e0.
+struct BuildOut {
+  int n_spin = 1;
+  double* dU[3] = {nullptr, nullptr, nullptr};
+  float* dU32 = nullptr;
+  double* dh[2] = {nullptr, nullptr};
+  double* e0 = nullptr;
+};
+
+// One step (c)+(d) pass over the factor list [k0, k0 + rank) into the accumulator M.
+struct Pass {
+  int k0, rank;
+  DBuf* M;
+};
+
+int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
+               const double* phi, const double* const* gammas, const BuildOut& out) {
+  CUDA_OK(cudaSetDevice(ctx->prm.device));
+  reset_timers(ctx);
+  cudaStream_t st = ctx->st;
+  const bool spin = out.n_spin == 2;
+
+  // ---- densities: symmetry, finiteness, factorisation
+  if (n_orb < 1 || n_orb > MAX_ORB) return fail(ctx, XTC_ERR_ARG, "n_orb=%d out of range", n_orb);
+  const int N = n_orb;
+  Density dens[2];
+  int rc;
+  for (int sp = 0; sp < out.n_spin; ++sp)
+    if ((rc = read_density(ctx, gammas[sp], N, spin ? (sp ? "gamma_b" : "gamma_a") : "gamma", dens[sp]))) return rc;
+
+  // Factor lists of the passes.  Closed shell: exchange weights lam_k, direct weights 2 lam_k
+  // (W = 2 V.gamma, Wt = 2 rho.gamma).  Spin t (electron 2 of spin t): the factors of gamma^t with
+  // both weights, then those of the other spin with direct weights only, so that the direct
+  // density is gamma^a + gamma^b and the exchange density gamma^t (Appendix A).
+  std::vector<double> ev, lamx, lamd;
+  std::vector<Pass> passes;
+  if (!spin) {
+    ev = dens[0].ev;
+    lamx = dens[0].lam;
+    for (double l : dens[0].lam) lamd.push_back(2.0 * l);
+    passes.push_back({0, dens[0].rank, &ctx->M});
+  } else {
+    for (int t = 0; t < 2; ++t) {
+      const Density &own = dens[t], &other = dens[1 - t];
+      const int k0 = static_cast<int>(lamx.size());
+      ev.insert(ev.end(), own.ev.begin(), own.ev.end());
+      ev.insert(ev.end(), other.ev.begin(), other.ev.end());
+      lamx.insert(lamx.end(), own.lam.begin(), own.lam.end());
+      lamx.insert(lamx.end(), other.lam.size(), 0.0);
+      lamd.insert(lamd.end(), own.lam.begin(), own.lam.end());
+      lamd.insert(lamd.end(), other.lam.begin(), other.lam.end());
+      passes.push_back({k0, own.rank + other.rank, t ? &ctx->M2 : &ctx->M});
+    }
+  }
 
   Plan pl{};
   const double *d_grid = nullptr, *d_w = nullptr, *d_phi = nullptr;
-  int rc = prepare(ctx, pl, n_grid, n_orb, grid_xyz, weights, phi, &d_grid, &d_w, &d_phi);
+  rc = prepare(ctx, pl, n_grid, n_orb, grid_xyz, weights, phi, &d_grid, &d_w, &d_phi);
   if (rc) return rc;
   const int NP = pl.NP;
   const int ldm = static_cast<int>(m_stride(NP));
+  const size_t mbytes = 8ull * NP * ldm;
 
-  // ---- device copies of gamma and its factors
-  if (!ensure(ctx->gamma, g.size() * 8) || !ensure(ctx->evec, std::max<size_t>(ev.size(), 1) * 8) ||
-      !ensure(ctx->lam, std::max<size_t>(lam.size(), 1) * 8) || !ensure(ctx->M, 8ull * NP * ldm))
-    return fail(ctx, XTC_ERR_OOM, "gamma / accumulator (%.2f GB)", 8.0 * NP * ldm / 1e9);
-  CUDA_OK(cudaMemcpyAsync(ctx->gamma.p, g.data(), g.size() * 8, cudaMemcpyHostToDevice, st));
-  if (rank > 0) {
+  // ---- device copies of the densities, their factors and the accumulators
+  const size_t gbytes = static_cast<size_t>(N) * N * 8;
+  if (!ensure(ctx->gamma, gbytes) || (spin && !ensure(ctx->gamma_b, gbytes)) ||
+      !ensure(ctx->evec, std::max<size_t>(ev.size(), 1) * 8) || !ensure(ctx->lam, std::max<size_t>(lamx.size(), 1) * 8) ||
+      !ensure(ctx->lamd, std::max<size_t>(lamd.size(), 1) * 8) || !ensure(ctx->M, mbytes) ||
+      (spin && (!ensure(ctx->M2, mbytes) || !ensure(ctx->M3, mbytes))))
+    return fail(ctx, XTC_ERR_OOM, "densities / accumulators (%.2f GB)", (spin ? 3.0 : 1.0) * mbytes / 1e9);
+  CUDA_OK(cudaMemcpyAsync(ctx->gamma.p, dens[0].g.data(), gbytes, cudaMemcpyHostToDevice, st));
+  if (spin) CUDA_OK(cudaMemcpyAsync(ctx->gamma_b.p, dens[1].g.data(), gbytes, cudaMemcpyHostToDevice, st));
+  if (!lamx.empty()) {
     CUDA_OK(cudaMemcpyAsync(ctx->evec.p, ev.data(), ev.size() * 8, cudaMemcpyHostToDevice, st));
-    CUDA_OK(cudaMemcpyAsync(ctx->lam.p, lam.data(), lam.size() * 8, cudaMemcpyHostToDevice, st));
+    CUDA_OK(cudaMemcpyAsync(ctx->lam.p, lamx.data(), lamx.size() * 8, cudaMemcpyHostToDevice, st));
+    CUDA_OK(cudaMemcpyAsync(ctx->lamd.p, lamd.data(), lamd.size() * 8, cudaMemcpyHostToDevice, st));
   }
-  CUDA_OK(cudaMemsetAsync(ctx->M.p, 0, 8ull * NP * ldm, st));
+  for (const Pass& ps : passes) CUDA_OK(cudaMemsetAsync(ps.M->p, 0, mbytes, st));
 
   // ---- step (d) operands
   // fp16 x2: step (c) writes FP32 rows L32 / R32, split per row into fp16 hi + lo (L, R, 128-byte
@@ -680,108 +747,176 @@ extern "C" int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const dou
     if ((rc = make_tmap_3d(ctx, &tm_L, ctx->L.p, true, kdim, NP, 3, AS_BK, AS_BM))) return rc;
     if ((rc = make_tmap_3d(ctx, &tm_R, ctx->R.p, true, kdim, NP, 3, AS_BK, AS_BN))) return rc;
   }
-  const int groups = std::max(1, (rank + RANK_GROUP - 1) / RANK_GROUP);
   int pts = 0;
-  for (int gi = 0; gi < groups; ++gi) {
-    const int rg = std::min(RANK_GROUP, rank - gi * RANK_GROUP);
-    const int p = choose_pts(N, std::max(rg, 0), pl.f64);
-    if (!p) return fail(ctx, XTC_ERR_UNSUPPORTED, "step (c) shared memory exceeded (n_orb=%d)", N);
-    pts = pts ? std::min(pts, p) : p;
+  for (const Pass& ps : passes) {
+    const int groups = std::max(1, (ps.rank + RANK_GROUP - 1) / RANK_GROUP);
+    for (int gi = 0; gi < groups; ++gi) {
+      const int rg = std::min(RANK_GROUP, ps.rank - gi * RANK_GROUP);
+      const int p = choose_pts(N, std::max(rg, 0), pl.f64);
+      if (!p) return fail(ctx, XTC_ERR_UNSUPPORTED, "step (c) shared memory exceeded (n_orb=%d)", N);
+      pts = pts ? std::min(pts, p) : p;
+    }
   }
 
   // ---- chunk loop
   for (int64_t c0 = pl.ob; c0 < pl.oe; c0 += pl.gc) {
     const int64_t n_i = std::min<int64_t>(pl.gc, pl.oe - c0);
     if ((rc = run_vfield(ctx, pl, d_grid, c0, n_i, maps))) return rc;
-    for (int gi = 0; gi < groups; ++gi) {
-      const int k0 = gi * RANK_GROUP;
-      const int rg = std::max(0, std::min(RANK_GROUP, rank - k0));
-      FieldsArgs fa{};
-      fa.V = ctx->V.p;
-      fa.splits = pl.f64 ? 1 : pl.splits;
-      fa.phiT = ctx->phiT.as<double>();
-      fa.ldphi = pl.NGp;
-      fa.w = d_w;
-      fa.evec = ctx->evec.as<double>() + static_cast<size_t>(k0) * N;
-      fa.lam = ctx->lam.as<double>() + k0;
-      fa.rank = rg;
-      fa.i0 = c0;
-      fa.n_i = n_i;
-      fa.gcp = pl.gc;
-      fa.n_orb = N;
-      fa.n_pair = NP;
-      fa.pts = pts;
-      fa.pair_p = ctx->pair_p.as<int>();
-      fa.pair_q = ctx->pair_q.as<int>();
-      fa.L = d16 ? ctx->L32.p : ctx->L.p;
-      fa.R = d16 ? ctx->R32.p : ctx->R.p;
-      fa.out_parts = pl.f64 ? 0 : (d16 ? 1 : 3);
-      timed(ctx, XTC_K_FIELDS, 1, [&] { launch_fields(fa, pl.f64, st); });
-      if (d16) {
-        VfieldArgs da{};
-        da.mode = 1;
-        da.rows_a = NP;
-        da.n_pair = NP;
-        da.n_tiles = (NP + vf_bn(2) - 1) / vf_bn(2);
-        da.n_kb = static_cast<int>(kdim / VF_BK);
-        da.kb_per_split = da.n_kb;
-        da.kd = std::min(ctx->vf_kd, 4);
-        da.flush = ctx->vf_flush > 0 ? ctx->vf_flush : 128;
-        da.Vacc = ctx->Vacc.as<double>();
-        da.M = ctx->M.as<double>();
-        da.ldm = m_stride(NP);
-        da.exp_a = ctx->eL.as<int>();
-        da.exp_b = ctx->eR.as<int>();
-        da.err = ctx->err_dev.as<int>();
-        timed(ctx, XTC_K_ASSEMBLE, 4, [&] {
-          launch_lr_split(ctx->L32.as<float>(), NP, kdim, ctx->L.as<uint16_t>(), ctx->eL.as<int>(), st);
-          launch_lr_split(ctx->R32.as<float>(), NP, kdim, ctx->R.as<uint16_t>(), ctx->eR.as<int>(), st);
-          launch_vfield_tc(&tm_L, &tm_R, da, 2, 1, st);
+    for (const Pass& ps : passes) {
+      const int groups = std::max(1, (ps.rank + RANK_GROUP - 1) / RANK_GROUP);
+      double* M = ps.M->as<double>();
+      for (int gi = 0; gi < groups; ++gi) {
+        const int k0 = ps.k0 + gi * RANK_GROUP;
+        const int rg = std::max(0, std::min(RANK_GROUP, ps.rank - gi * RANK_GROUP));
+        FieldsArgs fa{};
+        fa.V = ctx->V.p;
+        fa.splits = pl.f64 ? 1 : pl.splits;
+        fa.phiT = ctx->phiT.as<double>();
+        fa.ldphi = pl.NGp;
+        fa.w = d_w;
+        fa.evec = ctx->evec.as<double>() + static_cast<size_t>(k0) * N;
+        fa.lam = ctx->lam.as<double>() + k0;
+        fa.lamd = ctx->lamd.as<double>() + k0;
+        fa.rank = rg;
+        fa.i0 = c0;
+        fa.n_i = n_i;
+        fa.gcp = pl.gc;
+        fa.n_orb = N;
+        fa.n_pair = NP;
+        fa.pts = pts;
+        fa.pair_p = ctx->pair_p.as<int>();
+        fa.pair_q = ctx->pair_q.as<int>();
+        fa.L = d16 ? ctx->L32.p : ctx->L.p;
+        fa.R = d16 ? ctx->R32.p : ctx->R.p;
+        fa.out_parts = pl.f64 ? 0 : (d16 ? 1 : 3);
+        timed(ctx, XTC_K_FIELDS, 1, [&] { launch_fields(fa, pl.f64, st); });
+        if (d16) {
+          VfieldArgs da{};
+          da.mode = 1;
+          da.rows_a = NP;
+          da.n_pair = NP;
+          da.n_tiles = (NP + vf_bn(2) - 1) / vf_bn(2);
+          da.n_kb = static_cast<int>(kdim / VF_BK);
+          da.kb_per_split = da.n_kb;
+          da.kd = std::min(ctx->vf_kd, 4);
+          da.flush = ctx->vf_flush > 0 ? ctx->vf_flush : 128;
+          da.Vacc = ctx->Vacc.as<double>();
+          da.M = M;
+          da.ldm = m_stride(NP);
+          da.exp_a = ctx->eL.as<int>();
+          da.exp_b = ctx->eR.as<int>();
+          da.err = ctx->err_dev.as<int>();
+          timed(ctx, XTC_K_ASSEMBLE, 4, [&] {
+            launch_lr_split(ctx->L32.as<float>(), NP, kdim, ctx->L.as<uint16_t>(), ctx->eL.as<int>(), st);
+            launch_lr_split(ctx->R32.as<float>(), NP, kdim, ctx->R.as<uint16_t>(), ctx->eR.as<int>(), st);
+            launch_vfield_tc(&tm_L, &tm_R, da, 2, 1, st);
+          });
+          continue;
+        }
+        timed(ctx, XTC_K_ASSEMBLE, 1, [&] {
+          if (pl.f64)
+            launch_assemble_f64(ctx->L.as<double>(), ctx->R.as<double>(), NP, static_cast<int>(kdim), M, st);
+          else
+            launch_assemble_tc(&tm_L, &tm_R, NP, static_cast<int>(kdim), std::min(ctx->as_kd, 3), M,
+                               ctx->err_dev.as<int>(), st);
         });
-        continue;
       }
-      timed(ctx, XTC_K_ASSEMBLE, 1, [&] {
-        if (pl.f64)
-          launch_assemble_f64(ctx->L.as<double>(), ctx->R.as<double>(), NP, static_cast<int>(kdim),
-                              ctx->M.as<double>(), st);
-        else
-          launch_assemble_tc(&tm_L, &tm_R, NP, static_cast<int>(kdim), std::min(ctx->as_kd, 3), ctx->M.as<double>(),
-                             ctx->err_dev.as<int>(), st);
-      });
     }
   }
 
   // ---- final: Delta U, Delta h, e0
-  const bool dU_dev = dU && is_device_ptr(dU), dU32_dev = dU_f32 && is_device_ptr(dU_f32);
-  const bool dh_dev = is_device_ptr(dh), e0_dev = is_device_ptr(e0);
   const size_t n4 = static_cast<size_t>(N) * N * N * N;
-  double* udst = dU ? (dU_dev ? dU : nullptr) : nullptr;
-  float* u32dst = dU_f32 ? (dU32_dev ? dU_f32 : nullptr) : nullptr;
-  if (dU && !dU_dev) {
-    if (!ensure(ctx->dU_tmp, n4 * 8)) return fail(ctx, XTC_ERR_OOM, "dU staging");
-    udst = ctx->dU_tmp.as<double>();
+  const size_t n2b = static_cast<size_t>(N) * N * 8;
+  if (!ensure(ctx->dh_tmp, 2 * n2b) || !ensure(ctx->e0_tmp, 8)) return fail(ctx, XTC_ERR_OOM, "dh staging");
+  double* dh_d[2] = {nullptr, nullptr};
+  for (int sp = 0; sp < out.n_spin; ++sp)
+    dh_d[sp] = is_device_ptr(out.dh[sp]) ? out.dh[sp] : ctx->dh_tmp.as<double>() + static_cast<size_t>(sp) * N * N;
+  double* e0_d = is_device_ptr(out.e0) ? out.e0 : ctx->e0_tmp.as<double>();
+  // device destinations of the Delta U blocks; host ones are staged one at a time in dU_tmp
+  const int n_blocks = spin ? 3 : 1;
+  bool u_dev[3] = {false, false, false};
+  bool need_stage = false;
+  for (int b = 0; b < n_blocks; ++b) {
+    u_dev[b] = out.dU[b] && is_device_ptr(out.dU[b]);
+    need_stage |= out.dU[b] && !u_dev[b];
   }
-  if (dU_f32 && !dU32_dev) {
-    if (!ensure(ctx->vout, n4 * 4)) return fail(ctx, XTC_ERR_OOM, "dU_f32 staging");
-    u32dst = ctx->vout.as<float>();
+  const bool u32_dev = out.dU32 && is_device_ptr(out.dU32);
+  if (need_stage && !ensure(ctx->dU_tmp, n4 * 8)) return fail(ctx, XTC_ERR_OOM, "dU staging");
+  if (out.dU32 && !u32_dev && !ensure(ctx->vout, n4 * 4)) return fail(ctx, XTC_ERR_OOM, "dU_f32 staging");
+  float* u32dst = out.dU32 ? (u32_dev ? out.dU32 : ctx->vout.as<float>()) : nullptr;
+  if (!spin) {
+    double* udst = out.dU[0] ? (u_dev[0] ? out.dU[0] : ctx->dU_tmp.as<double>()) : nullptr;
+    timed(ctx, XTC_K_FINAL, (udst || u32dst) ? 4 : 3, [&] {
+      launch_symmetrize(ctx->M.as<double>(), NP, st);
+      launch_unpack(ctx->M.as<double>(), N, NP, udst, u32dst, st);
+      launch_onebody(ctx->M.as<double>(), ctx->gamma.as<double>(), N, NP, dh_d[0], e0_d, st);
+    });
+    CUDA_OK(cudaGetLastError());
+    if (out.dU[0] && !u_dev[0]) CUDA_OK(cudaMemcpyAsync(out.dU[0], udst, n4 * 8, cudaMemcpyDeviceToHost, st));
+    if (out.dU32 && !u32_dev) CUDA_OK(cudaMemcpyAsync(out.dU32, u32dst, n4 * 4, cudaMemcpyDeviceToHost, st));
+  } else {
+    // M = f^a, M2 = f^b (f^t[pq][rs] = sum_i rho_pq A^t_rs + V_pq.B^t_rs):
+    // Delta U^{ab} = -(f^b + f^a^T) into M3, then Delta U^{aa} and Delta U^{bb} in place.
+    timed(ctx, XTC_K_FINAL, 6, [&] {
+      launch_spin_cross(ctx->M2.as<double>(), ctx->M.as<double>(), NP, ctx->M3.as<double>(), st);
+      launch_symmetrize(ctx->M.as<double>(), NP, st);
+      launch_symmetrize(ctx->M2.as<double>(), NP, st);
+      launch_onebody_spin(ctx->M.as<double>(), ctx->M3.as<double>(), ctx->M2.as<double>(), ctx->gamma.as<double>(),
+                          ctx->gamma_b.as<double>(), N, NP, dh_d[0], dh_d[1], e0_d, st);
+    });
+    DBuf* src[3] = {&ctx->M, &ctx->M3, &ctx->M2};
+    for (int b = 0; b < 3; ++b) {
+      if (!out.dU[b]) continue;
+      double* udst = u_dev[b] ? out.dU[b] : ctx->dU_tmp.as<double>();
+      timed(ctx, XTC_K_FINAL, 1, [&] { launch_unpack(src[b]->as<double>(), N, NP, udst, nullptr, st); });
+      CUDA_OK(cudaGetLastError());
+      // the staging buffer is reused by the next block: this copy completes before the next unpack
+      if (!u_dev[b]) CUDA_OK(cudaMemcpyAsync(out.dU[b], udst, n4 * 8, cudaMemcpyDeviceToHost, st));
+    }
   }
-  if (!ensure(ctx->dh_tmp, static_cast<size_t>(N) * N * 8) || !ensure(ctx->e0_tmp, 8))
-    return fail(ctx, XTC_ERR_OOM, "dh staging");
-  double* dh_d = dh_dev ? dh : ctx->dh_tmp.as<double>();
-  double* e0_d = e0_dev ? e0 : ctx->e0_tmp.as<double>();
-  timed(ctx, XTC_K_FINAL, (udst || u32dst) ? 4 : 3, [&] {
-    launch_symmetrize(ctx->M.as<double>(), NP, st);
-    launch_unpack(ctx->M.as<double>(), N, NP, udst, u32dst, st);
-    launch_onebody(ctx->M.as<double>(), ctx->gamma.as<double>(), N, NP, dh_d, e0_d, st);
-  });
   CUDA_OK(cudaGetLastError());
-  if (dU && !dU_dev) CUDA_OK(cudaMemcpyAsync(dU, udst, n4 * 8, cudaMemcpyDeviceToHost, st));
-  if (dU_f32 && !dU32_dev) CUDA_OK(cudaMemcpyAsync(dU_f32, u32dst, n4 * 4, cudaMemcpyDeviceToHost, st));
-  if (!dh_dev) CUDA_OK(cudaMemcpyAsync(dh, dh_d, static_cast<size_t>(N) * N * 8, cudaMemcpyDeviceToHost, st));
-  if (!e0_dev) CUDA_OK(cudaMemcpyAsync(e0, e0_d, 8, cudaMemcpyDeviceToHost, st));
+  for (int sp = 0; sp < out.n_spin; ++sp)
+    if (dh_d[sp] != out.dh[sp]) CUDA_OK(cudaMemcpyAsync(out.dh[sp], dh_d[sp], n2b, cudaMemcpyDeviceToHost, st));
+  if (e0_d != out.e0) CUDA_OK(cudaMemcpyAsync(out.e0, e0_d, 8, cudaMemcpyDeviceToHost, st));
   if ((rc = check_device_error(ctx))) return rc;
   finish_timers(ctx);
   return XTC_OK;
+}
+
+}  // namespace
+
+extern "C" int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
+                              const double* phi, const double* gamma, double* dU, float* dU_f32, double* dh,
+                              double* e0) {
+  if (!ctx) return XTC_ERR_ARG;
+  if (!gamma || !dh || !e0) return fail(ctx, XTC_ERR_ARG, "gamma, dh and e0 are required");
+  BuildOut out;
+  out.n_spin = 1;
+  out.dU[0] = dU;
+  out.dU32 = dU_f32;
+  out.dh[0] = dh;
+  out.e0 = e0;
+  const double* g[1] = {gamma};
+  return build_impl(ctx, n_grid, n_orb, grid_xyz, weights, phi, g, out);
+}
+
+extern "C" int xtc_build_1b2b_rohf(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz,
+                                   const double* weights, const double* phi, const double* gamma_a,
+                                   const double* gamma_b, double* dU_aa, double* dU_ab, double* dU_bb, double* dh_a,
+                                   double* dh_b, double* e0) {
+  if (!ctx) return XTC_ERR_ARG;
+  if (!gamma_a || !gamma_b || !dh_a || !dh_b || !e0)
+    return fail(ctx, XTC_ERR_ARG, "gamma_a, gamma_b, dh_a, dh_b and e0 are required");
+  BuildOut out;
+  out.n_spin = 2;
+  out.dU[0] = dU_aa;
+  out.dU[1] = dU_ab;
+  out.dU[2] = dU_bb;
+  out.dh[0] = dh_a;
+  out.dh[1] = dh_b;
+  out.e0 = e0;
+  const double* g[2] = {gamma_a, gamma_b};
+  return build_impl(ctx, n_grid, n_orb, grid_xyz, weights, phi, g, out);
 }
 
 extern "C" int xtc_jastrow_grad(xtc_ctx* ctx, int64_t n, const double* r1, const double* r2, double* out) {

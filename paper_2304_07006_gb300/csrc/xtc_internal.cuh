@@ -142,8 +142,10 @@ struct FieldsArgs {
   const double* phiT;          // [n_orb][ldphi], global grid index
   int64_t ldphi;
   const double* w;
-  const double* evec;          // [rank][n_orb]  (gamma = sum_k lam_k c_k c_k^T)
-  const double* lam;           // [rank]
+  const double* evec;          // [rank][n_orb]: factors c_k of the densities
+  const double* lam;           // [rank]: exchange weights, gamma_x = sum_k lam_k c_k c_k^T (X, Y, Zt, Z)
+  const double* lamd;          // [rank]: direct weights, g_d = sum_k lamd_k c_k c_k^T (W = V.g_d, Wt = rho.g_d);
+                               // closed shell: lamd = 2 lam; spin t: g_d = gamma^a + gamma^b, gamma_x = gamma^t
   int rank;
   int64_t i0, n_i, gcp;
   int n_orb, n_pair;
@@ -172,6 +174,11 @@ void launch_assemble_f64(const double* L, const double* R, int n_pair, int kdim,
 // Final: M <- Delta U = -(M + M^T) in place; unpacking; Delta h; e0.  M row stride round_up(n_pair, AS_BN).
 void launch_symmetrize(double* M, int n_pair, cudaStream_t st);
 void launch_unpack(const double* M, int n_orb, int n_pair, double* dU, float* dU32, cudaStream_t st);
+// Spin builds: U = Delta U^{ab} = -(Fb + Fa^T) (packed pairs, row stride m_stride(n_pair)).
+void launch_spin_cross(const double* Fb, const double* Fa, int n_pair, double* U, cudaStream_t st);
+// Spin builds: Delta h^a, Delta h^b and e0 from Delta U^{aa}, ^{ab}, ^{bb} and the two densities.
+void launch_onebody_spin(const double* Uaa, const double* Uab, const double* Ubb, const double* ga, const double* gb,
+                         int n_orb, int n_pair, double* dh_a, double* dh_b, double* e0, cudaStream_t st);
 void launch_onebody(const double* M, const double* gamma, int n_orb, int n_pair, double* dh, double* e0,
                     cudaStream_t st);
 

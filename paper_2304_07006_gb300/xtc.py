@@ -20,7 +20,7 @@ KERNEL_NAMES = ("prep", "vfield", "fields", "assemble", "final", "grad")
 
 EXPORTED = ("xtc_default_params", "xtc_create", "xtc_destroy", "xtc_strerror", "xtc_last_error_detail",
             "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b", "xtc_jastrow_grad", "xtc_vfield",
-            "xtc_get_timings", "xtc_vfield_noalloc", "xtc_build_1b2b_batched")
+            "xtc_get_timings", "xtc_vfield_noalloc", "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf")
 
 
 class XtcParams(ctypes.Structure):
@@ -72,9 +72,10 @@ def load(path: str = LIB_PATH):
     lib.xtc_vfield_noalloc.argtypes = [P, I64, I, D, D, D, I64, I64, D]
     lib.xtc_get_timings.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), I]
     lib.xtc_build_1b2b_batched.argtypes = [P, I, ctypes.POINTER(XtcInstance), I]
+    lib.xtc_build_1b2b_rohf.argtypes = [P, I64, I, D, D, D, D, D, D, D, D, D, D, D]
     for name in ("xtc_create", "xtc_destroy", "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b",
                  "xtc_jastrow_grad", "xtc_vfield", "xtc_get_timings", "xtc_vfield_noalloc",
-                 "xtc_build_1b2b_batched"):
+                 "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -172,6 +173,28 @@ class Context:
         self._check(self._lib.xtc_build_1b2b(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
                                              _ptr(gamma), _ptr(dU), _ptr(dU_f32), _ptr(dh), _ptr(e0)))
         return {"dU": dU if dU is not None else dU_f32, "dh": dh, "e0": e0}
+
+    def build_rohf(self, grid, weights, phi, gamma_a, gamma_b, want_dU=True, **out):
+        """The build for separate alpha and beta densities (xtc_build_1b2b_rohf).  Outputs may be
+        given as keyword arguments dU_aa, dU_ab, dU_bb, dh_a, dh_b, e0 (numpy arrays or float64
+        tensors); missing ones are allocated as numpy arrays (the Delta U blocks only with
+        want_dU).  Returns them in a dict."""
+        grid, weights, phi = _f64(grid), _f64(weights), _f64(phi)
+        gamma_a, gamma_b = _f64(gamma_a), _f64(gamma_b)
+        n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+        res = {}
+        for k in ("dU_aa", "dU_ab", "dU_bb"):
+            res[k] = out.get(k)
+            if res[k] is None and want_dU:
+                res[k] = np.empty((n_orb,) * 4)
+        for k in ("dh_a", "dh_b"):
+            res[k] = out.get(k) if out.get(k) is not None else np.empty((n_orb, n_orb))
+        res["e0"] = out.get("e0") if out.get("e0") is not None else np.empty(1)
+        self._check(self._lib.xtc_build_1b2b_rohf(
+            self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi), _ptr(gamma_a), _ptr(gamma_b),
+            _ptr(res["dU_aa"]), _ptr(res["dU_ab"]), _ptr(res["dU_bb"]), _ptr(res["dh_a"]), _ptr(res["dh_b"]),
+            _ptr(res["e0"])))
+        return res
 
     def jastrow_grad(self, r1, r2, out=None):
         r1, r2 = _f64(r1), _f64(r2)

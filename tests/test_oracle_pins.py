@@ -269,6 +269,19 @@ def test_open_shell_equal_densities_reduce_to_closed_shell():
     assert abs(s2["e0"] - c["e0"]) < 1e-13 * scale
 
 
+def test_open_shell_blocks_average_to_closed_shell_of_mean_density():
+    """Delta U is linear in the densities: (aa + bb) / 2 and the pair-symmetrised ab block both
+    equal the closed-shell Delta U of the spin-averaged density (Appendix B as the spin average)."""
+    p = synth.make_small(n_orb=4, n_rad=4, n_theta=3, n_phi=3, n_atoms=3, seed=21)
+    ga, gb = synth.random_density(4, 9), synth.random_density(4, 10, rank=2)
+    r = spin.build(p, ga, gb)
+    c = direct.build(p, 0.5 * (ga + gb))
+    scale = np.abs(c["dU"]).max()
+    assert np.abs(0.5 * (r["dU_aa"] + r["dU_bb"]) - c["dU"]).max() < 1e-13 * scale
+    assert np.abs(0.5 * (r["dU_ab"] + r["dU_ab"].transpose(2, 3, 0, 1)) - c["dU"]).max() < 1e-13 * scale
+    assert np.abs(r["dU_ab"] - c["dU"]).max() > 1e-3 * scale       # the ab block alone is not
+
+
 def test_open_shell_spin_flip(small):
     """Exchanging the two densities exchanges the spin labels of every output."""
     p, _, _ = small
