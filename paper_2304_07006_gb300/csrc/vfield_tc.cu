@@ -17,7 +17,7 @@
 //
 // Warp roles:
 //   * warp 0 (one lane): TMA loads of the A and B tiles;
-//   * warp 1 (one lane): MMA issuer;
+//   * warps 1 and 10 (one lane each): MMA issuers of the even and the odd ranges;
 //   * warps 2..9: every `kd` stages they load the finished accumulator (tcgen05.ld) and add it into
 //     an FP32 running sum held in their registers (two warps per TMEM lane quarter, BN/2 columns
 //     each) while the MMA fills the other accumulator; at the end they store the sum, unscaled, as
@@ -43,7 +43,8 @@ namespace xtc {
 namespace {
 
 constexpr int DRAIN_WARPS = 8;       // two per TMEM lane quarter, BN/2 columns each
-constexpr int THREADS = (2 + DRAIN_WARPS) * 32;
+constexpr int MMA_WARPS = 2;         // issuers of the even / odd ranges (warps 1 and 2 + DRAIN_WARPS)
+constexpr int THREADS = (1 + MMA_WARPS + DRAIN_WARPS) * 32;
 constexpr int A_TILE = VF_BM * 64;   // bytes per part of an A tile (128 rows of 64 B)
 constexpr int GM = 8;                // row tiles per group (L2 reuse)
 
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int s = 0; s < STAGES; ++s) mbar_init(&tma_full[s], 1);
     for (int r = 0; r < NRB; ++r) mbar_init(&rdone[r], 1);
     for (int b = 0; b < 2; ++b) mbar_init(&d_free[b], DRAIN_WARPS);
-    mbar_init(fin_bar, 1);
+    mbar_init(fin_bar, MMA_WARPS);
     *abort_flag = 0;
     fence_mbar_init();
     tma_prefetch_desc(&tm_g);
@@ -202,15 +203,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                   DEV_ERR_TIMEOUT_VF);
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == 1 || warp == 2 + DRAIN_WARPS) {
     if (lane == 0) {
-      // ---------------------------------------------------------------- MMA issuer
+      // ---------------------------------------------------------------- MMA issuers
       // A range of kd stages goes into one TMEM accumulator: first the cross products of each
       // stage as it lands (the accumulator is still small), then the hi x hi product of every
-      // stage; one commit per range.
+      // stage; one commit per range.  Warp 1 issues the even ranges (accumulator 0), the last warp
+      // the odd ones (accumulator 1): a commit tracks only its own thread's MMAs, so while one
+      // issuer's commit completes the other keeps the tensor pipe fed.
       constexpr uint32_t idesc = idesc_f16(VF_BM, BN, BF16);
       bool alive = true;
-      for (int r = 0; r < n_ranges && alive; ++r) {
+      for (int r = warp == 1 ? 0 : 1; r < n_ranges && alive; r += MMA_WARPS) {
         const int it0 = r * kd, it1 = min(n_it, it0 + kd);
         const int b = r & 1, u = r >> 1;
         const uint32_t d_tmem = tmem + b * BN;
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         tc_commit(&rdone[r % NRB]);
       }
-      // every MMA issued by this thread has completed once fin_bar fires
+      // every MMA issued by both issuers has completed once fin_bar fires
       tc_commit(fin_bar);
       int zero = 0;
       mbar_wait(fin_bar, 0, reinterpret_cast<volatile int*>(&zero), args.err, DEV_ERR_TIMEOUT_VF);

@@ -75,7 +75,7 @@ struct xtc_ctx {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   int vf_kd = 2;  // K-blocks per tensor-core accumulation range in step (b)
   int vf_flush = 128;  // step (b) ranges between FP64 flushes of the running sums (0: FP32 only)
-  int as_kd = 2;  // the same for step (d)
+  int as_kd = 2;  // the same for step (d) (both engines)
   // batched builds: lane contexts, each with its own stream (created on first use)
   std::vector<xtc_ctx*> lanes;
   std::vector<cudaStream_t> lane_streams;
@@ -798,7 +798,7 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
           da.n_tiles = (NP + vf_bn(2) - 1) / vf_bn(2);
           da.n_kb = static_cast<int>(kdim / VF_BK);
           da.kb_per_split = da.n_kb;
-          da.kd = std::min(ctx->vf_kd, 4);
+          da.kd = std::min(ctx->as_kd, 4);
           da.flush = ctx->vf_flush > 0 ? ctx->vf_flush : 128;
           da.Vacc = ctx->Vacc.as<double>();
           da.M = M;
