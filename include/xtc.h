@@ -93,8 +93,9 @@ typedef struct {
   int range_stages;    /* tensor-core precisions: inner-sum stages of 32 points accumulated in the
                           tensor cores before an exactly rounded FP32 add (1..4; bf16x3 uses at
                           most 2 in step b and 3 in step d).  The tensor-core FP32 accumulator
-                          truncates, so 1 is the most accurate (Delta h error about half of the
-                          default's at N=120) and about 25% slower; 0 = default (2) */
+                          truncates toward zero, so the error grows with the range: at N=120,
+                          2 stages double the Delta h and constant errors of 1 stage for about 5%
+                          less time; 0 = default (1) */
 } xtc_params;
 
 /* Fills *p with defaults: device 0, default stream, XTC_PREC_FP16X2, automatic chunking. */

@@ -23,7 +23,7 @@
 //     each) while the MMA fills the other accumulator; at the end they store the sum, unscaled, as
 //     V[pq][x][i].
 // The tensor-core accumulator truncates toward zero at each MMA, which biases a long inner sum.
-// Each range is short (default two stages), its MMAs issue the small cross products of all its
+// Each range is short (default one stage), its MMAs issue the small cross products of all its
 // stages first so that only the hi x hi products meet a large accumulator, and the ranges are
 // summed with round-to-nearest FP32 adds.  Rounding of that FP32 sum grows with the number of
 // ranges, so every `flush` ranges the drains add their FP32 partial sums into an FP64 accumulator

@@ -73,9 +73,9 @@ struct xtc_ctx {
   double ms[XTC_N_KERNELS] = {0};
   int64_t launches[XTC_N_KERNELS] = {0};
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  int vf_kd = 2;  // K-blocks per tensor-core accumulation range in step (b)
+  int vf_kd = 1;  // K-blocks per tensor-core accumulation range in step (b)
   int vf_flush = 128;  // step (b) ranges between FP64 flushes of the running sums (0: FP32 only)
-  int as_kd = 2;  // the same for step (d) (both engines)
+  int as_kd = 1;  // the same for step (d) (both engines)
   // batched builds: lane contexts, each with its own stream (created on first use)
   std::vector<xtc_ctx*> lanes;
   std::vector<cudaStream_t> lane_streams;
