@@ -74,7 +74,7 @@ struct xtc_ctx {
   int64_t launches[XTC_N_KERNELS] = {0};
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   int vf_kd = 1;  // K-blocks per tensor-core accumulation range in step (b)
-  int vf_flush = 128;  // step (b) ranges between FP64 flushes of the running sums (0: FP32 only)
+  int vf_flush = 8192;  // inner points (K values) between FP64 flushes of the running sums (0: FP32 only)
   int as_kd = 1;  // the same for step (d) (both engines)
   // batched builds: lane contexts, each with its own stream (created on first use)
   std::vector<xtc_ctx*> lanes;
@@ -242,6 +242,10 @@ int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t NGp, int parts, int64_t n_o
   }
   return best;
 }
+
+// Ranges of kd stages (32 K values each) between FP64 flushes for a flush interval of `points` K
+// values (0: no flushes).
+int flush_ranges(int points, int kd) { return points > 0 ? std::max(1, points / (32 * kd)) : 0; }
 
 int choose_pts(int N, int R, bool f64) {
   for (int p : {8, 4, 2, 1})
@@ -575,7 +579,6 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   a.colexp = ctx->colexp.as<int>();
   a.V = ctx->V.as<float>();
   a.Vacc = ctx->Vacc.as<double>();
-  a.flush = ctx->vf_flush;
   a.n_i = n_i;
   a.gcp = pl.gc;
   a.mt_per_x = mt_per_x;
@@ -584,6 +587,7 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   a.n_kb = n_kb;
   a.kb_per_split = (a.n_kb + pl.splits - 1) / pl.splits;
   a.kd = std::min(ctx->vf_kd, pl.parts_b == 2 ? 4 : 2);
+  a.flush = flush_ranges(ctx->vf_flush, a.kd);
   a.unscale_g = std::ldexp(1.0f, -sg);
   a.err = ctx->err_dev.as<int>();
   const int splits = (a.n_kb + a.kb_per_split - 1) / a.kb_per_split;  // every slice non-empty
@@ -799,7 +803,7 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
           da.n_kb = static_cast<int>(kdim / VF_BK);
           da.kb_per_split = da.n_kb;
           da.kd = std::min(ctx->as_kd, 4);
-          da.flush = ctx->vf_flush > 0 ? ctx->vf_flush : 128;
+          da.flush = flush_ranges(ctx->vf_flush > 0 ? ctx->vf_flush : 8192, da.kd);
           da.Vacc = ctx->Vacc.as<double>();
           da.M = M;
           da.ldm = m_stride(NP);
