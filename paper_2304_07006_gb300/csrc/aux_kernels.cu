@@ -576,7 +576,7 @@ void launch_vfield_f64_impl(const double* grid, const JastrowParams* jp, int n_n
                             const double* rho, int64_t n_pad, int n_pair, int64_t i0, int64_t n_i, int64_t gcp,
                             double* V, cudaStream_t st) {
   const size_t smem = sizeof(double) * (F64_TI * (PT_COEF + NUC_COEF * n_nuc) + F64_KJ * 3 * F64_TI + F64_KJ * F64_TP);
-  cudaFuncSetAttribute(vfield_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  cudaFuncSetAttribute(vfield_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem());
   dim3 g(blocks_for(n_i, F64_TI), blocks_for(n_pair, F64_TP));
   vfield_f64_kernel<<<g, 256, smem, st>>>(grid, jp, jtab64, rho, n_pad, n_pair, i0, n_i, gcp, V);
 }

@@ -247,7 +247,7 @@ template <typename TV, typename TC, int OUT>
 void launch_t(const FieldsArgs& a, cudaStream_t st) {
   const size_t smem = fields_smem_bytes(a.n_orb, a.rank, a.pts, sizeof(TC) == 8);
   auto kern = fields_kernel<TV, TC, OUT>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem());
   const int blocks = static_cast<int>(a.gcp / a.pts);
   kern<<<blocks, THREADS, smem, st>>>(a);
 }

@@ -45,6 +45,18 @@ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // (fp16 step d) tiles fit in a row.
 inline int64_t m_stride(int64_t n_pair) { return round_up(n_pair, 384); }
 
+// The current device's opt-in maximum of dynamic shared memory per CTA.  Kernels whose dynamic
+// shared memory varies from call to call set their limit to this one value (not to the call's
+// size): the limit is per function and process-wide, and batch lanes launch from several host
+// threads, so a per-call value set by one thread could undercut another thread's launch.
+inline int max_dyn_smem() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 48 * 1024;
+  return v;
+}
+
 // Floats per inner point in the gradient producer's table: 12 for up to 4 nuclei, 16 for 5..8.
 inline int jtab_stride(int n_nuc) { return n_nuc <= 4 ? 12 : 16; }
 
