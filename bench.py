@@ -100,7 +100,7 @@ class Clocks:
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one vfield_tc_kernel<2,0> launch on the first 1184
 # outer points of the workload (profiles/vfield_tc_n2.md); valid for that kernel version only
-VFIELD_DRAM_BYTES_CAPTURED = 19_595_734_016 + 2_730_386_688
+VFIELD_DRAM_BYTES_CAPTURED = 17_627_806_208 + 2_669_686_528
 VFIELD_CAPTURE_OUTER = 1184
 
 
