@@ -234,6 +234,39 @@ def rohf_measure(args, torch, dev, local, p, s_closed):
             "per_kernel_ms": per, "note": "inputs and outputs on the device; Delta U not unpacked"}
 
 
+def large_measure(args, torch, dev, local):
+    """The large workload (4 heavy atoms + 4 H, N=200, 200,000 grid points, 8 Jastrow centres in
+    2 sets, 14 doubly occupied orbitals): one warm-up and one timed build (CUDA events), inputs and
+    outputs on the device, Delta U formed but not unpacked."""
+    from paper_2304_07006_gb300 import Context
+
+    p = synth_config("large")
+    F = flops(p.n_orb, p.n_grid)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    grid, w, phi, gam = t(p.grid), t(p.weights), t(p.phi), t(p.gamma)
+    dh = torch.empty((p.n_orb, p.n_orb), dtype=torch.float64, device=dev)
+    e0 = torch.empty(1, dtype=torch.float64, device=dev)
+    with Context(args.precision, device=local) as c:
+        c.set_jastrow(p.nuc_xyz, p.nuc_set, p.terms, p.coef)
+        c.build(grid, w, phi, gam, dh=dh, e0=e0, want_dU=False)
+        stream = torch.cuda.current_stream(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        c.build(grid, w, phi, gam, dh=dh, e0=e0, want_dU=False)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        sec = a.elapsed_time(b) / 1e3
+    return {"workload": f"large: N={p.n_orb}, {p.n_grid} grid points, {len(p.nuc_xyz)} Jastrow centres",
+            "seconds_per_build": sec, "algorithmic_flops": F["total"], "tflops": F["total"] / sec / 1e12,
+            "note": "inputs and outputs on the device; Delta U not unpacked"}
+
+
+def synth_config(name):
+    import synth
+    return synth.make_config(name)
+
+
 def run_ncu_case(args):
     """A small, quick build (same workload, outer sum restricted to P points) for kernel captures."""
     import synth
@@ -261,6 +294,7 @@ def main():
     ap.add_argument("--batched", type=int, default=32, metavar="N",
                     help="also time the batched workload of N uneven instances (0: skip)")
     ap.add_argument("--rohf", type=int, default=1, help="also time the spin-resolved build (0: skip)")
+    ap.add_argument("--large", type=int, default=1, help="also time one build of the N=200 workload (0: skip)")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="P",
                     help="profiling aid: run one warm-up and one build of the workload restricted to the first P "
                          "outer points, print a one-line summary and exit (no benchmark line)")
@@ -422,6 +456,10 @@ def main():
             line["batched"] = batched_measure(args, torch, dev, local)
         if args.rohf:
             line["rohf"] = rohf_measure(args, torch, dev, local, p, ms_step / 1e3)
+        if args.large:
+            free, _ = torch.cuda.mem_get_info(dev)
+            line["large"] = (large_measure(args, torch, dev, local) if free > 100e9
+                             else {"skipped": f"{free / 1e9:.0f} GB free on the device, 100 GB wanted"})
         line["cpu_baseline"] = oracle_sample(p, args.cpu_sample)
         line["cpu_baseline"].pop("seconds", None)
         print(json.dumps(line), flush=True)
