@@ -39,6 +39,20 @@ WORKLOAD = "n2"
 METRIC = "xTC 2-body build TFLOP/s & seconds at N=120 (mixed vs FP64, same GB300) at stated Eh error"
 
 
+def job_throughput(ms_local: float, steps: int, world: int, flops_per_step: float, dist=None, device=None):
+    """Milliseconds per step of the slowest rank and the whole-job TFLOP/s.  Every rank runs the
+    same build on its own GPU (replicas), so the job does world x the per-step work in the slowest
+    rank's time.  dist: torch.distributed (initialised) or None for one process."""
+    ms = float(ms_local)
+    if dist is not None:
+        import torch
+        tt = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_step = ms / steps
+    return ms_step, world * flops_per_step / (ms_step * 1e-3) / 1e12
+
+
 def flops(n_orb: int, n_grid: int, n_outer: int | None = None) -> dict:
     n_outer = n_grid if n_outer is None else n_outer
     npair = n_orb * (n_orb + 1) // 2
@@ -357,13 +371,7 @@ def main():
     clk = clocks.stop()
     if dist:
         dist.barrier()
-    ms_total = ev0.elapsed_time(ev1)
-    if dist:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
-    ms_step = ms_total / args.steps
-    value = world * F["total"] / (ms_step * 1e-3) / 1e12
+    ms_step, value = job_throughput(ev0.elapsed_time(ev1), args.steps, world, F["total"], dist, dev)
 
     # roofline of the dominant kernel: step (b), per-launch algorithmic flops / mean launch time
     per_kernel = {name: {"ms_per_step": kern_ms[k] / args.steps, "launches_per_step": int(kern_n[k] // args.steps)}
