@@ -209,12 +209,14 @@ XTC_API int xtc_build_1b2b_batched(xtc_ctx* ctx, int n_inst, xtc_instance* inst,
 /* Kernel timers of the last build (requires params.timing != 0).  Kernel ids: */
 enum {
   XTC_K_PREP = 0,     /* per-grid-point tables, orbital transposition, pair products rho (split) */
-  XTC_K_VFIELD = 1,   /* step (b) GEMM (tensor-core precisions); steps (a)+(b) (XTC_PREC_FP64) */
+  XTC_K_VFIELD = 1,   /* step (b) GEMM alone (tensor-core precisions); steps (a)+(b) (XTC_PREC_FP64) */
   XTC_K_FIELDS = 2,   /* step (c) */
-  XTC_K_ASSEMBLE = 3, /* step (d): Delta U accumulation */
+  XTC_K_ASSEMBLE = 3, /* step (d): Delta U accumulation (the GEMM alone) */
   XTC_K_FINAL = 4,    /* Delta U unpacking, Delta h, e0 */
   XTC_K_GRAD = 5,     /* step (a) gradient table of the tensor-core precisions */
-  XTC_N_KERNELS = 6
+  XTC_K_AUX = 6,      /* around the tensor-core GEMMs: the kernels that write V or add into M from
+                         the FP64 tile sums, and the fp16 row splits of step (d) */
+  XTC_N_KERNELS = 7
 };
 /* ms[k] = summed device milliseconds of kernel class k over the last build, launches[k] = launch
  * count; either pointer may be NULL.  n = array length (>= XTC_N_KERNELS). */

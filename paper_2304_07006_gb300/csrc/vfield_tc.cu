@@ -390,6 +390,12 @@ void launch_t(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldAr
   const int m_tiles = MODE == 0 ? 3 * a.mt_per_x : (a.rows_a + VF_BM - 1) / VF_BM;
   dim3 grid(static_cast<unsigned>(m_tiles * a.n_tiles), static_cast<unsigned>(splits));
   kern<<<grid, THREADS, smem, st>>>(*tm_g, *tm_rho, a);
+}
+
+template <int PARTS, int MODE>
+void finalize_t(const VfieldArgs& a, int splits, cudaStream_t st) {
+  const int m_tiles = MODE == 0 ? 3 * a.mt_per_x : (a.rows_a + VF_BM - 1) / VF_BM;
+  dim3 grid(static_cast<unsigned>(m_tiles * a.n_tiles), static_cast<unsigned>(splits));
   if (MODE == 0 && a.flush > 0) vfield_finalize_kernel<VfCfg<PARTS>::BN><<<grid, VF_BM, 0, st>>>(a);
   if (MODE == 1) assemble_finalize_kernel<VfCfg<PARTS>::BN><<<grid, VF_BM, 0, st>>>(a);
 }
@@ -410,6 +416,19 @@ void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const 
     launch_t<2, 0>(tm_g, tm_rho, a, splits, st);
   else
     launch_t<3, 0>(tm_g, tm_rho, a, splits, st);
+}
+
+void launch_vfield_tc_finalize(const VfieldArgs& a, int parts, int splits, cudaStream_t st) {
+  if (a.n_tiles <= 0 || splits <= 0) return;
+  if (a.mode == 1) {
+    if (a.rows_a > 0) finalize_t<2, 1>(a, splits, st);
+    return;
+  }
+  if (a.mt_per_x <= 0 || a.flush <= 0) return;
+  if (parts == 2)
+    finalize_t<2, 0>(a, splits, st);
+  else
+    finalize_t<3, 0>(a, splits, st);
 }
 
 }  // namespace xtc

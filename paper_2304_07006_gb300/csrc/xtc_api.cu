@@ -592,8 +592,8 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   a.err = ctx->err_dev.as<int>();
   const int splits = (a.n_kb + a.kb_per_split - 1) / a.kb_per_split;  // every slice non-empty
   // the GEMM, then (FP64 flushes) the kernel that writes V from the FP64 sums
-  timed(ctx, XTC_K_VFIELD, a.flush > 0 ? 2 : 1,
-        [&] { launch_vfield_tc(&maps.g_load, &maps.rho, a, pl.parts_b, splits, st); });
+  timed(ctx, XTC_K_VFIELD, 1, [&] { launch_vfield_tc(&maps.g_load, &maps.rho, a, pl.parts_b, splits, st); });
+  if (a.flush > 0) timed(ctx, XTC_K_AUX, 1, [&] { launch_vfield_tc_finalize(a, pl.parts_b, splits, st); });
   return XTC_OK;
 }
 
@@ -810,11 +810,12 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
           da.exp_a = ctx->eL.as<int>();
           da.exp_b = ctx->eR.as<int>();
           da.err = ctx->err_dev.as<int>();
-          timed(ctx, XTC_K_ASSEMBLE, 4, [&] {
+          timed(ctx, XTC_K_AUX, 2, [&] {
             launch_lr_split(ctx->L32.as<float>(), NP, kdim, ctx->L.as<uint16_t>(), ctx->eL.as<int>(), st);
             launch_lr_split(ctx->R32.as<float>(), NP, kdim, ctx->R.as<uint16_t>(), ctx->eR.as<int>(), st);
-            launch_vfield_tc(&tm_L, &tm_R, da, 2, 1, st);
           });
+          timed(ctx, XTC_K_ASSEMBLE, 1, [&] { launch_vfield_tc(&tm_L, &tm_R, da, 2, 1, st); });
+          timed(ctx, XTC_K_AUX, 1, [&] { launch_vfield_tc_finalize(da, 2, 1, st); });
           continue;
         }
         timed(ctx, XTC_K_ASSEMBLE, 1, [&] {

@@ -130,9 +130,11 @@ struct VfieldArgs {
   const int* exp_b;
 };
 bool vfield_tc_supported(int n_nuc);
-// Launches the GEMM and, when a.flush > 0, the kernel that writes V from the FP64 sums.
+// Launches the GEMM.
 void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int parts,
                       int splits, cudaStream_t st);
+// Then, with FP64 sums (a.flush > 0): mode 0 writes V from them, mode 1 adds the tiles into M.
+void launch_vfield_tc_finalize(const VfieldArgs& a, int parts, int splits, cudaStream_t st);
 
 // Steps (a)+(b), FP64 SIMT twin.  V[pq][x][il] (FP64).  jtab64[n_grid_pad][3 + n_nuc].
 void launch_jtab64(const double* grid, int64_t n_grid, int64_t n_pad, const JastrowParams* jp, int n_nuc,

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libxtc.so")
 
 PREC_FP64, PREC_FP16X2, PREC_BF16X3 = 0, 1, 2
 PRECISIONS = {"fp64": PREC_FP64, "fp16x2": PREC_FP16X2, "bf16x3": PREC_BF16X3}
-KERNEL_NAMES = ("prep", "vfield", "fields", "assemble", "final", "grad")
+KERNEL_NAMES = ("prep", "vfield", "fields", "assemble", "final", "grad", "aux")
 
 EXPORTED = ("xtc_default_params", "xtc_create", "xtc_destroy", "xtc_strerror", "xtc_last_error_detail",
             "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b", "xtc_jastrow_grad", "xtc_vfield",
