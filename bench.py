@@ -276,6 +276,31 @@ def large_measure(args, torch, dev, local):
             "note": "inputs and outputs on the device; Delta U not unpacked"}
 
 
+def three_body_measure(args, torch, dev, local):
+    """The explicit three-body tensor of eq. Ldecomp on the H2-like workload (N=10, 2,000 grid
+    points, FP64 path): one warm-up and three timed calls, output on the device."""
+    from paper_2304_07006_gb300 import Context
+
+    p = synth_config("h2")
+    N, NP = p.n_orb, p.n_orb * (p.n_orb + 1) // 2
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    grid, w, phi = t(p.grid), t(p.weights), t(p.phi)
+    L = torch.empty((N,) * 6, dtype=torch.float64, device=dev)
+    with Context("fp64", device=local) as c:
+        c.set_jastrow(p.nuc_xyz, p.nuc_set, p.terms, p.coef)
+        c.three_body_L(grid, w, phi, out=L)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            c.three_body_L(grid, w, phi, out=L)
+        torch.cuda.synchronize(dev)
+        sec = (time.perf_counter() - t0) / 3
+    flops_t = 2.0 * NP ** 3 * p.n_grid + 6.0 * NP ** 2 * p.n_grid
+    return {"workload": f"h2: N={N}, {p.n_grid} grid points, FP64", "seconds_per_call": sec,
+            "elements": N ** 6, "t_flops": flops_t,
+            "note": "wall time per call with steps (a)+(b) in FP64; L is written densely on the device"}
+
+
 def synth_config(name):
     import synth
     return synth.make_config(name)
@@ -467,6 +492,7 @@ def main():
             line["batched"] = batched_measure(args, torch, dev, local)
         if args.rohf:
             line["rohf"] = rohf_measure(args, torch, dev, local, p, ms_step / 1e3)
+        line["three_body_L"] = three_body_measure(args, torch, dev, local)
         if args.large:
             free, _ = torch.cuda.mem_get_info(dev)
             line["large"] = (large_measure(args, torch, dev, local) if free > 100e9

@@ -172,6 +172,20 @@ XTC_API int xtc_jastrow_grad(xtc_ctx* ctx, int64_t n, const double* r1, const do
 XTC_API int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
                const double* phi, int64_t outer_begin, int64_t outer_end, double* V);
 
+/* The explicit three-body tensor of eq. Ldecomp ("Decomposition of two-body correction"), for
+ * validating full transcorrelated codes on small orbital sets:
+ *   L[p][r][t][q][s][u] = L_prt^qsu = sum_i [ rho_pq V_rs.V_tu + rho_rs V_pq.V_tu + rho_tu V_pq.V_rs ](i),
+ *   rho_pq(i) = w_i phi_p(i) phi_q(i), V_rs(i) the vector pair field of step (b) (xtc_vfield),
+ * summed over the context's outer range (xtc_set_outer_range; the whole grid by default).
+ *   n_grid >= 1, 1 <= n_orb <= XTC_THREE_BODY_MAX_ORB; grid_xyz, weights, phi as in xtc_build_1b2b
+ *   L [n_orb]^6 FP64, host or device memory (n_orb = 24: 1.5 GB)
+ * V is formed in the context's precision (steps a and b); the products and sums over i are FP64.
+ * Requires xtc_set_jastrow.  Errors: XTC_ERR_ARG, XTC_ERR_STATE, XTC_ERR_OOM, XTC_ERR_CUDA and
+ * those of xtc_vfield. */
+#define XTC_THREE_BODY_MAX_ORB 24
+XTC_API int xtc_three_body_L(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
+                     const double* phi, double* L);
+
 /* One instance of a batched build: the arguments of xtc_set_jastrow and xtc_build_1b2b, with the
  * same meanings, layouts and ownership; status receives the instance's own status. */
 typedef struct xtc_instance {

@@ -64,6 +64,7 @@ struct xtc_ctx {
   DBuf jtab, jtab64, rho, colmax, colexp, G;
   DBuf V, Vacc, L, R, L32, R32, eL, eR, M, evec, lam, dU_tmp, dh_tmp, e0_tmp, vout, r1, r2;
   DBuf lamd, gamma_b, M2, M3;  // direct weights; spin builds: beta density, f^b, Delta U^{ab}
+  DBuf Lv, T3;                 // explicit three-body L: V of the outer points, the packed T
   // prepared state key (pair tables)
   int pair_n = -1;
   // timers
@@ -333,7 +334,7 @@ int xtc_destroy(xtc_ctx* ctx) {
                   &ctx->colexp, &ctx->G, &ctx->V, &ctx->Vacc, &ctx->L, &ctx->R, &ctx->L32, &ctx->R32,
                   &ctx->eL, &ctx->eR, &ctx->M, &ctx->evec, &ctx->lam, &ctx->dU_tmp,
                   &ctx->dh_tmp, &ctx->e0_tmp, &ctx->vout, &ctx->r1, &ctx->r2,
-                  &ctx->lamd, &ctx->gamma_b, &ctx->M2, &ctx->M3};
+                  &ctx->lamd, &ctx->gamma_b, &ctx->M2, &ctx->M3, &ctx->Lv, &ctx->T3};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (xtc_ctx* lane : ctx->lanes) xtc_destroy(lane);
@@ -987,6 +988,49 @@ extern "C" int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double*
   (void)n_out;
   if ((rc = check_device_error(ctx))) return rc;
   finish_timers(ctx);
+  return XTC_OK;
+}
+
+// ====================================================================== explicit three-body L
+// eq. Ldecomp for small N: V of the outer points from steps (a)+(b) in the context's precision,
+// then T[a][b][c] = sum_i rho_a V_b.V_c and L[p][r][t][q][s][u] = T[pq][rs][tu] + T[rs][pq][tu] +
+// T[tu][pq][rs] in FP64.
+extern "C" int xtc_three_body_L(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz,
+                                const double* weights, const double* phi, double* L) {
+  if (!ctx) return XTC_ERR_ARG;
+  if (!L || n_orb < 1 || n_orb > XTC_THREE_BODY_MAX_ORB || n_grid < 1 || !grid_xyz || !weights || !phi)
+    return fail(ctx, XTC_ERR_ARG, "three_body_L: null pointer, n_grid < 1 or n_orb outside 1..%d",
+                XTC_THREE_BODY_MAX_ORB);
+  if (!ctx->jastrow_set) return fail(ctx, XTC_ERR_STATE, "xtc_set_jastrow has not been called");
+  CUDA_OK(cudaSetDevice(ctx->prm.device));
+  cudaStream_t st = ctx->st;
+  const int N = n_orb, NP = N * (N + 1) / 2;
+  const int64_t ob = std::min<int64_t>(ctx->outer_begin, n_grid);
+  const int64_t oe = std::max<int64_t>(ob, ctx->outer_end < 0 ? n_grid : std::min<int64_t>(ctx->outer_end, n_grid));
+  const int64_t n_i = oe - ob;
+  const size_t n6 = static_cast<size_t>(N) * N * N * N * N * N;
+  const bool out_dev = is_device_ptr(L);
+  if (!out_dev && !ensure(ctx->dU_tmp, n6 * 8)) return fail(ctx, XTC_ERR_OOM, "L staging (%.2f GB)", n6 * 8e-9);
+  double* Ld = out_dev ? L : ctx->dU_tmp.as<double>();
+  int rc;
+  if (n_i == 0) {
+    CUDA_OK(cudaMemsetAsync(Ld, 0, n6 * 8, st));
+  } else {
+    const size_t tbytes = static_cast<size_t>(NP) * NP * NP * 8;
+    if (!ensure(ctx->Lv, static_cast<size_t>(n_i) * 3 * NP * 8) || !ensure(ctx->T3, tbytes))
+      return fail(ctx, XTC_ERR_OOM, "three_body_L workspace (%.2f GB)", tbytes * 1e-9);
+    // steps (a)+(b) for the outer points; this also builds the pair tables for n_orb
+    if ((rc = xtc_vfield(ctx, n_grid, n_orb, grid_xyz, weights, phi, ob, oe, ctx->Lv.as<double>()))) return rc;
+    const double *d_w = nullptr, *d_phi = nullptr;
+    if ((rc = stage_input(ctx, ctx->w, weights, static_cast<size_t>(n_grid), &d_w))) return rc;
+    if ((rc = stage_input(ctx, ctx->phi, phi, static_cast<size_t>(n_grid) * n_orb, &d_phi))) return rc;
+    launch_three_body_t(d_phi, d_w, ob, n_i, N, ctx->pair_p.as<int>(), ctx->pair_q.as<int>(), ctx->Lv.as<double>(),
+                        ctx->T3.as<double>(), st);
+    launch_three_body_unpack(ctx->T3.as<double>(), N, Ld, st);
+    CUDA_OK(cudaGetLastError());
+  }
+  if (!out_dev) CUDA_OK(cudaMemcpyAsync(L, Ld, n6 * 8, cudaMemcpyDeviceToHost, st));
+  if ((rc = check_device_error(ctx))) return rc;
   return XTC_OK;
 }
 

@@ -188,6 +188,11 @@ void launch_assemble_f64(const double* L, const double* R, int n_pair, int kdim,
 // Final: M <- Delta U = -(M + M^T) in place; unpacking; Delta h; e0.  M row stride round_up(n_pair, AS_BN).
 void launch_symmetrize(double* M, int n_pair, cudaStream_t st);
 void launch_unpack(const double* M, int n_orb, int n_pair, double* dU, float* dU32, cudaStream_t st);
+// Explicit three-body L (eq. Ldecomp), FP64: T[a][b][c] = sum_k rho_a(i0 + k) V[k].b . V[k].c over
+// k < n_i with V[k][x][pair] (the layout of xtc_vfield), then L[p][r][t][q][s][u] from T.
+void launch_three_body_t(const double* phi, const double* w, int64_t i0, int64_t n_i, int n_orb, const int* pair_p,
+                         const int* pair_q, const double* V, double* T, cudaStream_t st);
+void launch_three_body_unpack(const double* T, int n_orb, double* L, cudaStream_t st);
 // Spin builds: U = Delta U^{ab} = -(Fb + Fa^T) (packed pairs, row stride m_stride(n_pair)).
 void launch_spin_cross(const double* Fb, const double* Fa, int n_pair, double* U, cudaStream_t st);
 // Spin builds: Delta h^a, Delta h^b and e0 from Delta U^{aa}, ^{ab}, ^{bb} and the two densities.

@@ -20,7 +20,8 @@ KERNEL_NAMES = ("prep", "vfield", "fields", "assemble", "final", "grad", "aux")
 
 EXPORTED = ("xtc_default_params", "xtc_create", "xtc_destroy", "xtc_strerror", "xtc_last_error_detail",
             "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b", "xtc_jastrow_grad", "xtc_vfield",
-            "xtc_get_timings", "xtc_vfield_noalloc", "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf")
+            "xtc_get_timings", "xtc_vfield_noalloc", "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf",
+            "xtc_three_body_L")
 
 
 class XtcParams(ctypes.Structure):
@@ -73,9 +74,10 @@ def load(path: str = LIB_PATH):
     lib.xtc_get_timings.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), I]
     lib.xtc_build_1b2b_batched.argtypes = [P, I, ctypes.POINTER(XtcInstance), I]
     lib.xtc_build_1b2b_rohf.argtypes = [P, I64, I, D, D, D, D, D, D, D, D, D, D, D]
+    lib.xtc_three_body_L.argtypes = [P, I64, I, D, D, D, D]
     for name in ("xtc_create", "xtc_destroy", "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b",
                  "xtc_jastrow_grad", "xtc_vfield", "xtc_get_timings", "xtc_vfield_noalloc",
-                 "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf"):
+                 "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf", "xtc_three_body_L"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -195,6 +197,17 @@ class Context:
             _ptr(res["dU_aa"]), _ptr(res["dU_ab"]), _ptr(res["dU_bb"]), _ptr(res["dh_a"]), _ptr(res["dh_b"]),
             _ptr(res["e0"])))
         return res
+
+    def three_body_L(self, grid, weights, phi, out=None):
+        """The explicit three-body tensor of eq. Ldecomp (xtc_three_body_L): out[p, r, t, q, s, u] =
+        L_prt^qsu over the context's outer range; a numpy array unless out is given."""
+        grid, weights, phi = _f64(grid), _f64(weights), _f64(phi)
+        n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+        if out is None:
+            out = np.empty((n_orb,) * 6)
+        self._check(self._lib.xtc_three_body_L(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
+                                               _ptr(out)))
+        return out
 
     def jastrow_grad(self, r1, r2, out=None):
         r1, r2 = _f64(r1), _f64(r2)
