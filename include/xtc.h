@@ -172,6 +172,16 @@ XTC_API int xtc_jastrow_grad(xtc_ctx* ctx, int64_t n, const double* r1, const do
 XTC_API int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
                const double* phi, int64_t outer_begin, int64_t outer_end, double* V);
 
+/* Chunk autotuner (no counterpart in the paper; the chunk is this library's streaming unit):
+ * times xtc_build_1b2b on this problem's first outer points, min(n_grid, 2 x the rule's chunk) of
+ * them, with up to three chunk lengths (the rule's choice, and the rule under 3/4 and 1/2 of its
+ * memory budgets, each fitted to whole waves of the step (b) GEMM), after one warm-up, and keeps
+ * the fastest as the context's grid_chunk for later builds; *chunk receives it.  The outer range
+ * set by xtc_set_outer_range is restored.  Inputs as in xtc_build_1b2b (Delta U is not formed).
+ * XTC_PREC_FP64 contexts take the rule's choice without timing.  Errors: as xtc_build_1b2b. */
+XTC_API int xtc_autotune_chunk(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz,
+                       const double* weights, const double* phi, const double* gamma, int64_t* chunk);
+
 /* The explicit three-body tensor of eq. Ldecomp ("Decomposition of two-body correction"), for
  * validating full transcorrelated codes on small orbital sets:
  *   L[p][r][t][q][s][u] = L_prt^qsu = sum_i [ rho_pq V_rs.V_tu + rho_rs V_pq.V_tu + rho_tu V_pq.V_rs ](i),

@@ -3,6 +3,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -218,16 +219,18 @@ struct Plan {
   bool f64;
 };
 
-int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t NGp, int parts, int64_t n_outer, bool f64) {
+// budget_scale < 1 shrinks the memory budgets (the autotuner's smaller candidates).
+int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t NGp, int parts, int64_t n_outer, bool f64,
+                   double budget_scale = 1.0) {
   // memory budgets: 10 GB for V and the step (d) operands, 16 GB for the step (a) gradient table;
   // then the chunk that fills whole waves of the step (b) GEMM best
   const double vbytes = f64 ? 3.0 * 8 : 3.0 * 4;
   // step (d) operands per pair and outer point: FP64 L, R; bf16 x3 L, R; or FP32 L, R + fp16 x2 split
   const double lrbytes = f64 ? 2 * 4 * 8.0 : (parts == 2 ? 2 * 4 * (4.0 + 4.0) : 2 * 3 * 4 * 2.0);
   const double per_point = NP * (vbytes + lrbytes);
-  int64_t cap = static_cast<int64_t>(10.0e9 / per_point);
-  if (!f64) cap = std::min<int64_t>(cap, static_cast<int64_t>(16.0e9 / (3.0 * parts * 2.0 * NGp)));
-  cap = std::max<int64_t>(128, std::min<int64_t>(cap, 32768) / 128 * 128);
+  int64_t cap = static_cast<int64_t>(budget_scale * 10.0e9 / per_point);
+  if (!f64) cap = std::min<int64_t>(cap, static_cast<int64_t>(budget_scale * 16.0e9 / (3.0 * parts * 2.0 * NGp)));
+  cap = std::max<int64_t>(128, std::min<int64_t>(cap, static_cast<int64_t>(budget_scale * 32768)) / 128 * 128);
   const int64_t need = round_up(n_outer, 128);
   if (need <= cap) return need;
   const int nt = f64 ? 1 : (NP + vf_bn(parts) - 1) / vf_bn(parts);
@@ -988,6 +991,59 @@ extern "C" int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double*
   (void)n_out;
   if ((rc = check_device_error(ctx))) return rc;
   finish_timers(ctx);
+  return XTC_OK;
+}
+
+// ====================================================================== chunk autotuner
+// Times the build on the first outer points of this problem with up to three chunk lengths (the
+// rule's choice and the rule under 3/4 and 1/2 of its memory budgets) and keeps the fastest in
+// the context's parameters.  Every candidate covers the same outer points, so the fixed costs of
+// a build (preparation, final kernels) are the same for all and the comparison is direct.
+extern "C" int xtc_autotune_chunk(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz,
+                                  const double* weights, const double* phi, const double* gamma, int64_t* chunk) {
+  if (!ctx) return XTC_ERR_ARG;
+  if (!chunk || !gamma || n_grid < 1 || n_orb < 1 || n_orb > MAX_ORB)
+    return fail(ctx, XTC_ERR_ARG, "autotune: null pointer or bad size");
+  CUDA_OK(cudaSetDevice(ctx->prm.device));
+  const bool f64 = ctx->prm.precision == XTC_PREC_FP64;
+  const int parts = f64 ? 0 : (ctx->prm.precision == XTC_PREC_FP16X2 ? 2 : 3);
+  const int NP = n_orb * (n_orb + 1) / 2;
+  const int64_t NGp = round_up(n_grid, 128);
+  if (f64) {  // the FP64 path is too slow to time; its chunk only bounds memory
+    *chunk = ctx->prm.grid_chunk = auto_chunk(ctx, NP, NGp, parts, n_grid, true);
+    return XTC_OK;
+  }
+  std::vector<int64_t> cand;
+  for (double scale : {1.0, 0.75, 0.5}) {
+    const int64_t c = auto_chunk(ctx, NP, NGp, parts, n_grid, f64, scale);
+    if (std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+  }
+  const int64_t span = std::min<int64_t>(n_grid, 2 * cand[0]);
+  const int64_t saved_b = ctx->outer_begin, saved_e = ctx->outer_end, saved_c = ctx->prm.grid_chunk;
+  std::vector<double> dh(static_cast<size_t>(n_orb) * n_orb);
+  double e0 = 0.0;
+  ctx->outer_begin = 0;
+  ctx->outer_end = span;
+  int rc = XTC_OK;
+  int64_t best = cand[0];
+  double best_s = 0.0;
+  for (size_t k = 0; k < cand.size() && rc == XTC_OK; ++k) {
+    ctx->prm.grid_chunk = cand[k];
+    if (k == 0) rc = xtc_build_1b2b(ctx, n_grid, n_orb, grid_xyz, weights, phi, gamma, nullptr, nullptr, dh.data(), &e0);
+    if (rc != XTC_OK) break;
+    const auto t0 = std::chrono::steady_clock::now();
+    rc = xtc_build_1b2b(ctx, n_grid, n_orb, grid_xyz, weights, phi, gamma, nullptr, nullptr, dh.data(), &e0);
+    const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rc == XTC_OK && (k == 0 || sec < best_s)) {
+      best_s = sec;
+      best = cand[k];
+    }
+  }
+  ctx->outer_begin = saved_b;
+  ctx->outer_end = saved_e;
+  ctx->prm.grid_chunk = rc == XTC_OK ? best : saved_c;
+  if (rc != XTC_OK) return rc;
+  *chunk = best;
   return XTC_OK;
 }
 

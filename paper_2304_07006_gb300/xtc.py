@@ -21,7 +21,7 @@ KERNEL_NAMES = ("prep", "vfield", "fields", "assemble", "final", "grad", "aux")
 EXPORTED = ("xtc_default_params", "xtc_create", "xtc_destroy", "xtc_strerror", "xtc_last_error_detail",
             "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b", "xtc_jastrow_grad", "xtc_vfield",
             "xtc_get_timings", "xtc_vfield_noalloc", "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf",
-            "xtc_three_body_L")
+            "xtc_three_body_L", "xtc_autotune_chunk")
 
 
 class XtcParams(ctypes.Structure):
@@ -75,9 +75,10 @@ def load(path: str = LIB_PATH):
     lib.xtc_build_1b2b_batched.argtypes = [P, I, ctypes.POINTER(XtcInstance), I]
     lib.xtc_build_1b2b_rohf.argtypes = [P, I64, I, D, D, D, D, D, D, D, D, D, D, D]
     lib.xtc_three_body_L.argtypes = [P, I64, I, D, D, D, D]
+    lib.xtc_autotune_chunk.argtypes = [P, I64, I, D, D, D, D, ctypes.POINTER(ctypes.c_int64)]
     for name in ("xtc_create", "xtc_destroy", "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b",
                  "xtc_jastrow_grad", "xtc_vfield", "xtc_get_timings", "xtc_vfield_noalloc",
-                 "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf", "xtc_three_body_L"):
+                 "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf", "xtc_three_body_L", "xtc_autotune_chunk"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -197,6 +198,16 @@ class Context:
             _ptr(res["dU_aa"]), _ptr(res["dU_ab"]), _ptr(res["dU_bb"]), _ptr(res["dh_a"]), _ptr(res["dh_b"]),
             _ptr(res["e0"])))
         return res
+
+    def autotune_chunk(self, grid, weights, phi, gamma):
+        """Times a few grid-chunk lengths on this problem and keeps the fastest for later builds
+        (xtc_autotune_chunk); returns it."""
+        grid, weights, phi, gamma = _f64(grid), _f64(weights), _f64(phi), _f64(gamma)
+        n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+        c = ctypes.c_int64(0)
+        self._check(self._lib.xtc_autotune_chunk(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
+                                                 _ptr(gamma), ctypes.byref(c)))
+        return int(c.value)
 
     def three_body_L(self, grid, weights, phi, out=None):
         """The explicit three-body tensor of eq. Ldecomp (xtc_three_body_L): out[p, r, t, q, s, u] =

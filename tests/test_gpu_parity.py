@@ -310,6 +310,21 @@ def test_large_workload_sampled_outer_points(large_sampled, prec):
     assert max(errs) < TOL[prec], errs
 
 
+def test_autotune_chunk_keeps_its_choice_and_restores_the_outer_range():
+    """The water workload (40,000 points, more than one chunk): the autotuner returns a chunk
+    length (a multiple of 128) and keeps it for later builds, which cover the whole grid again and
+    equal, bitwise, the build of a context given that chunk."""
+    p = synth.make_config("water")
+    with ctx_for(p, "fp16x2") as c:
+        c.set_outer_range(0, -1)
+        chunk = c.autotune_chunk(p.grid, p.weights, p.phi, p.gamma)
+        out = c.build(p.grid, p.weights, p.phi, p.gamma, want_dU=False)
+    assert chunk > 0 and chunk % 128 == 0
+    with ctx_for(p, "fp16x2", grid_chunk=chunk) as c:
+        ref = c.build(p.grid, p.weights, p.phi, p.gamma, want_dU=False)
+    assert np.array_equal(out["dh"], ref["dh"]) and np.array_equal(out["e0"], ref["e0"])
+
+
 # ------------------------------------------------------------------ batched build
 
 def _instances(probs, gammas=None):
