@@ -12,6 +12,10 @@
 // products become rank-r updates: H_xk = V_x c_k, Zt = sum_xk lam_k H_xk H_xk^T,
 // W_x = sum_k lamd_k c_k.H_xk, h_x = V_x gamma_x phi = sum_k lam_k (c_k.phi) H_xk,
 // Z_x = w (phi h_x^T + h_x phi^T), Wt = w sum_k lamd_k (c_k.phi)^2.  (Exact reformulation.)
+// A spin build runs one pass for both spins of electron 2 (SPIN): the factors of gamma^a and
+// gamma^b together carry the direct weights (gamma^a + gamma^b), a.lam the alpha exchange weights
+// and a.lam2 the beta ones (zero on the other spin's factors); L is written once, R for alpha and
+// R2 for beta.
 //
 // A CTA owns `pts` consecutive outer points (lane-contiguous, so every global read of V is a
 // contiguous run of the outer index) and all orbital pairs; H for its points lives in shared
@@ -41,13 +45,15 @@ struct FieldsSmem {
   TC* Wv;    // [3][P]
   TC* Wt;    // [P]
   TC* part;  // [3][R][P]
+  TC* lam2;  // [R]        (SPIN)
+  TC* hs2;   // [3][N][P]  (SPIN)
 };
 
 template <typename TC>
-__host__ __device__ inline size_t carve(FieldsSmem<TC>* s, uint8_t* base, int N, int R, int P) {
+__host__ __device__ inline size_t carve(FieldsSmem<TC>* s, uint8_t* base, int N, int R, int P, bool spin) {
   size_t off = 0;
-  TC* p[11];
-  const size_t n[11] = {static_cast<size_t>(N) * P,
+  TC* p[13];
+  const size_t n[13] = {static_cast<size_t>(N) * P,
                         static_cast<size_t>(P),
                         static_cast<size_t>(R) * N,
                         static_cast<size_t>(R),
@@ -57,12 +63,14 @@ __host__ __device__ inline size_t carve(FieldsSmem<TC>* s, uint8_t* base, int N,
                         static_cast<size_t>(3) * N * P,
                         static_cast<size_t>(3) * P,
                         static_cast<size_t>(P),
-                        static_cast<size_t>(3) * R * P};
-  for (int k = 0; k < 11; ++k) {
+                        static_cast<size_t>(3) * R * P,
+                        spin ? static_cast<size_t>(R) : 0,
+                        spin ? static_cast<size_t>(3) * N * P : 0};
+  for (int k = 0; k < 13; ++k) {
     p[k] = reinterpret_cast<TC*>(base + off);
     off += ((n[k] * sizeof(TC) + 15) / 16) * 16;
   }
-  if (s) *s = FieldsSmem<TC>{p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8], p[9], p[10]};
+  if (s) *s = FieldsSmem<TC>{p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8], p[9], p[10], p[11], p[12]};
   return off;
 }
 
@@ -112,12 +120,12 @@ __device__ __forceinline__ void write4(void* base, int64_t n_pair, int64_t gcp, 
   }
 }
 
-template <typename TV, typename TC, int OUT_PARTS>
+template <typename TV, typename TC, int OUT_PARTS, bool SPIN>
 __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   const int N = a.n_orb, R = a.rank, P = a.pts;
   FieldsSmem<TC> sm;
-  carve<TC>(&sm, smem_raw, N, R, P);
+  carve<TC>(&sm, smem_raw, N, R, P, SPIN);
   const int t = threadIdx.x;
   const int pt = t % P, sub = t / P, nsub = THREADS / P;
   const int64_t il = static_cast<int64_t>(blockIdx.x) * P + pt;  // chunk-local outer point
@@ -139,6 +147,7 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
   for (int k = t; k < R; k += THREADS) {
     sm.lam[k] = static_cast<TC>(a.lam[k]);
     sm.lamd[k] = static_cast<TC>(a.lamd[k]);
+    if (SPIN) sm.lam2[k] = static_cast<TC>(a.lam2[k]);
   }
   __syncthreads();
   for (int k = t; k < R * P; k += THREADS) {
@@ -180,14 +189,16 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
       for (int kk = 0; kk < RMAX; ++kk)
         if (kk < R) acc[kk] += v * sm.cs[kk * N + s];
     }
-    TC h = 0;
+    TC h = 0, h2 = 0;
 #pragma unroll
     for (int kk = 0; kk < RMAX; ++kk)
       if (kk < R) {
         sm.Hs[((x * R + kk) * N + p) * P + pt] = acc[kk];
         h += sm.lam[kk] * sm.cph[kk * P + pt] * acc[kk];
+        if (SPIN) h2 += sm.lam2[kk] * sm.cph[kk * P + pt] * acc[kk];
       }
     sm.hs[(x * N + p) * P + pt] = h;
+    if (SPIN) sm.hs2[(x * N + p) * P + pt] = h2;
   }
   __syncthreads();
   // W_x = sum_k lamd_k sum_p c_k[p] H_xk[p]  (deterministic two-level sum)
@@ -211,19 +222,27 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
   const TC wt = sm.Wt[pt];
   const TC W0 = sm.Wv[pt], W1 = sm.Wv[P + pt], W2 = sm.Wv[2 * P + pt];
   for (int q = sub; q < a.n_pair; q += nsub) {
-    TC Lv[4] = {0, 0, 0, 0}, Rv[4] = {0, 0, 0, 0};
+    TC Lv[4] = {0, 0, 0, 0}, Rv[4] = {0, 0, 0, 0}, R2v[4] = {0, 0, 0, 0};
     if (live) {
       const int p = __ldg(a.pair_p + q), s = __ldg(a.pair_q + q);
       TC v[3];
 #pragma unroll
       for (int x = 0; x < 3; ++x)
         v[x] = static_cast<TC>(vload<TV>(V, a.splits, sstride, (static_cast<int64_t>(q) * 3 + x) * a.gcp + il));
-      TC zt = 0;
+      TC zt = 0, zt2 = 0;
       for (int x = 0; x < 3; ++x) {
         const TC* Hp = sm.Hs + (x * R * N + p) * P + pt;
         const TC* Hq = sm.Hs + (x * R * N + s) * P + pt;
 #pragma unroll 4
-        for (int kk = 0; kk < R; ++kk) zt += sm.lam[kk] * Hp[kk * N * P] * Hq[kk * N * P];
+        for (int kk = 0; kk < R; ++kk) {
+          if (SPIN) {
+            const TC hh = Hp[kk * N * P] * Hq[kk * N * P];
+            zt += sm.lam[kk] * hh;
+            zt2 += sm.lam2[kk] * hh;
+          } else {
+            zt += sm.lam[kk] * Hp[kk * N * P] * Hq[kk * N * P];
+          }
+        }
       }
       const TC vt = W0 * v[0] + W1 * v[1] + W2 * v[2];
       const TC php = sm.phis[p * P + pt], phs = sm.phis[s * P + pt];
@@ -237,16 +256,25 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
         const TC zx = w * (php * sm.hs[(x * N + s) * P + pt] + sm.hs[(x * N + p) * P + pt] * phs);
         Rv[1 + x] = TC(0.5) * wt * v[x] - zx;
       }
+      if (SPIN) {
+        R2v[0] = vt - zt2;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          const TC zx = w * (php * sm.hs2[(x * N + s) * P + pt] + sm.hs2[(x * N + p) * P + pt] * phs);
+          R2v[1 + x] = TC(0.5) * wt * v[x] - zx;
+        }
+      }
     }
     write4<TC, OUT_PARTS>(a.L, a.n_pair, a.gcp, q, il, Lv);
     write4<TC, OUT_PARTS>(a.R, a.n_pair, a.gcp, q, il, Rv);
+    if (SPIN) write4<TC, OUT_PARTS>(a.R2, a.n_pair, a.gcp, q, il, R2v);
   }
 }
 
-template <typename TV, typename TC, int OUT>
+template <typename TV, typename TC, int OUT, bool SPIN>
 void launch_t(const FieldsArgs& a, cudaStream_t st) {
-  const size_t smem = fields_smem_bytes(a.n_orb, a.rank, a.pts, sizeof(TC) == 8);
-  auto kern = fields_kernel<TV, TC, OUT>;
+  const size_t smem = fields_smem_bytes(a.n_orb, a.rank, a.pts, sizeof(TC) == 8, SPIN);
+  auto kern = fields_kernel<TV, TC, OUT, SPIN>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem());
   const int blocks = static_cast<int>(a.gcp / a.pts);
   kern<<<blocks, THREADS, smem, st>>>(a);
@@ -254,17 +282,26 @@ void launch_t(const FieldsArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-size_t fields_smem_bytes(int n_orb, int rank, int pts, bool f64) {
-  return f64 ? carve<double>(nullptr, nullptr, n_orb, rank, pts) : carve<float>(nullptr, nullptr, n_orb, rank, pts);
+size_t fields_smem_bytes(int n_orb, int rank, int pts, bool f64, bool spin) {
+  return f64 ? carve<double>(nullptr, nullptr, n_orb, rank, pts, spin)
+             : carve<float>(nullptr, nullptr, n_orb, rank, pts, spin);
+}
+
+template <bool SPIN>
+void launch_spin_t(const FieldsArgs& a, bool f64, cudaStream_t st) {
+  if (f64)
+    launch_t<double, double, 0, SPIN>(a, st);
+  else if (a.out_parts == 1)
+    launch_t<float, float, 1, SPIN>(a, st);
+  else
+    launch_t<float, float, 3, SPIN>(a, st);
 }
 
 void launch_fields(const FieldsArgs& a, bool f64, cudaStream_t st) {
-  if (f64)
-    launch_t<double, double, 0>(a, st);
-  else if (a.out_parts == 1)
-    launch_t<float, float, 1>(a, st);
+  if (a.R2)
+    launch_spin_t<true>(a, f64, st);
   else
-    launch_t<float, float, 3>(a, st);
+    launch_spin_t<false>(a, f64, st);
 }
 
 }  // namespace xtc

@@ -65,6 +65,7 @@ struct xtc_ctx {
   DBuf jtab, jtab64, rho, colmax, colexp, G;
   DBuf V, Vacc, L, R, L32, R32, eL, eR, M, evec, lam, dU_tmp, dh_tmp, e0_tmp, vout, r1, r2;
   DBuf lamd, gamma_b, M2, M3;  // direct weights; spin builds: beta density, f^b, Delta U^{ab}
+  DBuf lam2, R2, R32b, eR2;    // spin builds: beta exchange weights, R for electron-2 beta
   DBuf Lv, T3;                 // explicit three-body L: V of the outer points, the packed T
   // prepared state key (pair tables)
   int pair_n = -1;
@@ -251,9 +252,9 @@ int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t NGp, int parts, int64_t n_o
 // values (0: no flushes).
 int flush_ranges(int points, int kd) { return points > 0 ? std::max(1, points / (32 * kd)) : 0; }
 
-int choose_pts(int N, int R, bool f64) {
+int choose_pts(int N, int R, bool f64, bool spin) {
   for (int p : {8, 4, 2, 1})
-    if (fields_smem_bytes(N, R, p, f64) <= 200 * 1024) return p;
+    if (fields_smem_bytes(N, R, p, f64, spin) <= 200 * 1024) return p;
   return 0;
 }
 
@@ -337,7 +338,8 @@ int xtc_destroy(xtc_ctx* ctx) {
                   &ctx->colexp, &ctx->G, &ctx->V, &ctx->Vacc, &ctx->L, &ctx->R, &ctx->L32, &ctx->R32,
                   &ctx->eL, &ctx->eR, &ctx->M, &ctx->evec, &ctx->lam, &ctx->dU_tmp,
                   &ctx->dh_tmp, &ctx->e0_tmp, &ctx->vout, &ctx->r1, &ctx->r2,
-                  &ctx->lamd, &ctx->gamma_b, &ctx->M2, &ctx->M3, &ctx->Lv, &ctx->T3};
+                  &ctx->lamd, &ctx->gamma_b, &ctx->M2, &ctx->M3, &ctx->Lv, &ctx->T3,
+                  &ctx->lam2, &ctx->R2, &ctx->R32b, &ctx->eR2};
   for (DBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (xtc_ctx* lane : ctx->lanes) xtc_destroy(lane);
@@ -656,10 +658,12 @@ struct BuildOut {
   double* e0 = nullptr;
 };
 
-// One step (c)+(d) pass over the factor list [k0, k0 + rank) into the accumulator M.
+// One step (c)+(d) pass over the factor list [k0, k0 + rank) into the accumulator M, and for a
+// spin build also (electron 2 beta) into M2.
 struct Pass {
   int k0, rank;
   DBuf* M;
+  DBuf* M2;
 };
 
 int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
@@ -677,29 +681,29 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
   for (int sp = 0; sp < out.n_spin; ++sp)
     if ((rc = read_density(ctx, gammas[sp], N, spin ? (sp ? "gamma_b" : "gamma_a") : "gamma", dens[sp]))) return rc;
 
-  // Factor lists of the passes.  Closed shell: exchange weights lam_k, direct weights 2 lam_k
-  // (W = 2 V.gamma, Wt = 2 rho.gamma).  Spin t (electron 2 of spin t): the factors of gamma^t with
-  // both weights, then those of the other spin with direct weights only, so that the direct
-  // density is gamma^a + gamma^b and the exchange density gamma^t (Appendix A).
-  std::vector<double> ev, lamx, lamd;
+  // Factor lists.  Closed shell: exchange weights lam_k, direct weights 2 lam_k (W = 2 V.gamma,
+  // Wt = 2 rho.gamma), one pass into M.  Spin build: one pass over the factors of gamma^a and then
+  // gamma^b, all with direct weights (the direct density gamma^a + gamma^b, Appendix A), with the
+  // alpha exchange weights (lamx: gamma^a's factors) for R into M and the beta ones (lam2:
+  // gamma^b's factors) for R2 into M2.
+  std::vector<double> ev, lamx, lamd, lam2;
   std::vector<Pass> passes;
   if (!spin) {
     ev = dens[0].ev;
     lamx = dens[0].lam;
     for (double l : dens[0].lam) lamd.push_back(2.0 * l);
-    passes.push_back({0, dens[0].rank, &ctx->M});
+    passes.push_back({0, dens[0].rank, &ctx->M, nullptr});
   } else {
-    for (int t = 0; t < 2; ++t) {
-      const Density &own = dens[t], &other = dens[1 - t];
-      const int k0 = static_cast<int>(lamx.size());
-      ev.insert(ev.end(), own.ev.begin(), own.ev.end());
-      ev.insert(ev.end(), other.ev.begin(), other.ev.end());
-      lamx.insert(lamx.end(), own.lam.begin(), own.lam.end());
-      lamx.insert(lamx.end(), other.lam.size(), 0.0);
-      lamd.insert(lamd.end(), own.lam.begin(), own.lam.end());
-      lamd.insert(lamd.end(), other.lam.begin(), other.lam.end());
-      passes.push_back({k0, own.rank + other.rank, t ? &ctx->M2 : &ctx->M});
-    }
+    const Density &da = dens[0], &db = dens[1];
+    ev = da.ev;
+    ev.insert(ev.end(), db.ev.begin(), db.ev.end());
+    lamd = da.lam;
+    lamd.insert(lamd.end(), db.lam.begin(), db.lam.end());
+    lamx = da.lam;
+    lamx.insert(lamx.end(), db.lam.size(), 0.0);
+    lam2.assign(da.lam.size(), 0.0);
+    lam2.insert(lam2.end(), db.lam.begin(), db.lam.end());
+    passes.push_back({0, da.rank + db.rank, &ctx->M, &ctx->M2});
   }
 
   Plan pl{};
@@ -715,6 +719,7 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
   if (!ensure(ctx->gamma, gbytes) || (spin && !ensure(ctx->gamma_b, gbytes)) ||
       !ensure(ctx->evec, std::max<size_t>(ev.size(), 1) * 8) || !ensure(ctx->lam, std::max<size_t>(lamx.size(), 1) * 8) ||
       !ensure(ctx->lamd, std::max<size_t>(lamd.size(), 1) * 8) || !ensure(ctx->M, mbytes) ||
+      (spin && !ensure(ctx->lam2, std::max<size_t>(lam2.size(), 1) * 8)) ||
       (spin && (!ensure(ctx->M2, mbytes) || !ensure(ctx->M3, mbytes))))
     return fail(ctx, XTC_ERR_OOM, "densities / accumulators (%.2f GB)", (spin ? 3.0 : 1.0) * mbytes / 1e9);
   CUDA_OK(cudaMemcpyAsync(ctx->gamma.p, dens[0].g.data(), gbytes, cudaMemcpyHostToDevice, st));
@@ -723,8 +728,12 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
     CUDA_OK(cudaMemcpyAsync(ctx->evec.p, ev.data(), ev.size() * 8, cudaMemcpyHostToDevice, st));
     CUDA_OK(cudaMemcpyAsync(ctx->lam.p, lamx.data(), lamx.size() * 8, cudaMemcpyHostToDevice, st));
     CUDA_OK(cudaMemcpyAsync(ctx->lamd.p, lamd.data(), lamd.size() * 8, cudaMemcpyHostToDevice, st));
+    if (spin) CUDA_OK(cudaMemcpyAsync(ctx->lam2.p, lam2.data(), lam2.size() * 8, cudaMemcpyHostToDevice, st));
   }
-  for (const Pass& ps : passes) CUDA_OK(cudaMemsetAsync(ps.M->p, 0, mbytes, st));
+  for (const Pass& ps : passes) {
+    CUDA_OK(cudaMemsetAsync(ps.M->p, 0, mbytes, st));
+    if (ps.M2) CUDA_OK(cudaMemsetAsync(ps.M2->p, 0, mbytes, st));
+  }
 
   // ---- step (d) operands
   // fp16 x2: step (c) writes FP32 rows L32 / R32, split per row into fp16 hi + lo (L, R, 128-byte
@@ -732,35 +741,40 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
   const int64_t kdim = 4 * pl.gc;
   const bool d16 = !pl.f64 && pl.parts_b == 2;
   const size_t lr_bytes = pl.f64 ? 8ull * kdim * NP : (d16 ? 4ull * kdim * NP : 2ull * 3 * kdim * NP);
-  if (!ensure(ctx->L, lr_bytes) || !ensure(ctx->R, lr_bytes))
-    return fail(ctx, XTC_ERR_OOM, "step (d) operands (%.2f GB)", 2.0 * lr_bytes / 1e9);
+  if (!ensure(ctx->L, lr_bytes) || !ensure(ctx->R, lr_bytes) || (spin && !ensure(ctx->R2, lr_bytes)))
+    return fail(ctx, XTC_ERR_OOM, "step (d) operands (%.2f GB)", (spin ? 3.0 : 2.0) * lr_bytes / 1e9);
   if (d16) {
     const size_t ebytes = 4ull * m_stride(NP);
     const int bn = vf_bn(2);
     const size_t tiles = static_cast<size_t>((NP + VF_BM - 1) / VF_BM) * ((NP + bn - 1) / bn);
     if (!ensure(ctx->L32, 4ull * kdim * NP) || !ensure(ctx->R32, 4ull * kdim * NP) || !ensure(ctx->eL, ebytes) ||
-        !ensure(ctx->eR, ebytes) || !ensure(ctx->Vacc, std::max<size_t>(ctx->Vacc.n, 8ull * tiles * VF_BM * bn)))
+        !ensure(ctx->eR, ebytes) || !ensure(ctx->Vacc, std::max<size_t>(ctx->Vacc.n, 8ull * tiles * VF_BM * bn)) ||
+        (spin && (!ensure(ctx->R32b, 4ull * kdim * NP) || !ensure(ctx->eR2, ebytes))))
       return fail(ctx, XTC_ERR_OOM, "step (d) FP32 operands (%.2f GB)", 8.0 * kdim * NP / 1e9);
     // exponents of the padding columns of M stay 0
     CUDA_OK(cudaMemsetAsync(ctx->eL.p, 0, ebytes, st));
     CUDA_OK(cudaMemsetAsync(ctx->eR.p, 0, ebytes, st));
+    if (spin) CUDA_OK(cudaMemsetAsync(ctx->eR2.p, 0, ebytes, st));
   }
   VfMaps maps{};
-  CUtensorMap tm_L{}, tm_R{};
+  CUtensorMap tm_L{}, tm_R{}, tm_R2{};
   if ((rc = make_vfield_maps(ctx, pl, maps))) return rc;
   if (d16) {
     if ((rc = make_tmap_3d(ctx, &tm_L, ctx->L.p, false, 2 * kdim, NP, 1, 2 * VF_BK, VF_BM, true))) return rc;
     if ((rc = make_tmap_3d(ctx, &tm_R, ctx->R.p, false, 2 * kdim, NP, 1, 2 * VF_BK, vf_bn(2), true))) return rc;
+    if (spin && (rc = make_tmap_3d(ctx, &tm_R2, ctx->R2.p, false, 2 * kdim, NP, 1, 2 * VF_BK, vf_bn(2), true)))
+      return rc;
   } else if (!pl.f64) {
     if ((rc = make_tmap_3d(ctx, &tm_L, ctx->L.p, true, kdim, NP, 3, AS_BK, AS_BM))) return rc;
     if ((rc = make_tmap_3d(ctx, &tm_R, ctx->R.p, true, kdim, NP, 3, AS_BK, AS_BN))) return rc;
+    if (spin && (rc = make_tmap_3d(ctx, &tm_R2, ctx->R2.p, true, kdim, NP, 3, AS_BK, AS_BN))) return rc;
   }
   int pts = 0;
   for (const Pass& ps : passes) {
     const int groups = std::max(1, (ps.rank + RANK_GROUP - 1) / RANK_GROUP);
     for (int gi = 0; gi < groups; ++gi) {
       const int rg = std::min(RANK_GROUP, ps.rank - gi * RANK_GROUP);
-      const int p = choose_pts(N, std::max(rg, 0), pl.f64);
+      const int p = choose_pts(N, std::max(rg, 0), pl.f64, spin);
       if (!p) return fail(ctx, XTC_ERR_UNSUPPORTED, "step (c) shared memory exceeded (n_orb=%d)", N);
       pts = pts ? std::min(pts, p) : p;
     }
@@ -773,6 +787,7 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
     for (const Pass& ps : passes) {
       const int groups = std::max(1, (ps.rank + RANK_GROUP - 1) / RANK_GROUP);
       double* M = ps.M->as<double>();
+      double* M2 = ps.M2 ? ps.M2->as<double>() : nullptr;
       for (int gi = 0; gi < groups; ++gi) {
         const int k0 = ps.k0 + gi * RANK_GROUP;
         const int rg = std::max(0, std::min(RANK_GROUP, ps.rank - gi * RANK_GROUP));
@@ -796,6 +811,8 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
         fa.pair_q = ctx->pair_q.as<int>();
         fa.L = d16 ? ctx->L32.p : ctx->L.p;
         fa.R = d16 ? ctx->R32.p : ctx->R.p;
+        fa.R2 = M2 ? (d16 ? ctx->R32b.p : ctx->R2.p) : nullptr;
+        fa.lam2 = M2 ? ctx->lam2.as<double>() + k0 : nullptr;
         fa.out_parts = pl.f64 ? 0 : (d16 ? 1 : 3);
         timed(ctx, XTC_K_FIELDS, 1, [&] { launch_fields(fa, pl.f64, st); });
         if (d16) {
@@ -814,20 +831,33 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
           da.exp_a = ctx->eL.as<int>();
           da.exp_b = ctx->eR.as<int>();
           da.err = ctx->err_dev.as<int>();
-          timed(ctx, XTC_K_AUX, 2, [&] {
+          timed(ctx, XTC_K_AUX, M2 ? 3 : 2, [&] {
             launch_lr_split(ctx->L32.as<float>(), NP, kdim, ctx->L.as<uint16_t>(), ctx->eL.as<int>(), st);
             launch_lr_split(ctx->R32.as<float>(), NP, kdim, ctx->R.as<uint16_t>(), ctx->eR.as<int>(), st);
+            if (M2) launch_lr_split(ctx->R32b.as<float>(), NP, kdim, ctx->R2.as<uint16_t>(), ctx->eR2.as<int>(), st);
           });
           timed(ctx, XTC_K_ASSEMBLE, 1, [&] { launch_vfield_tc(&tm_L, &tm_R, da, 2, 1, st); });
           timed(ctx, XTC_K_AUX, 1, [&] { launch_vfield_tc_finalize(da, 2, 1, st); });
+          if (M2) {  // the tile sums buffer is reused after the finalize above, in stream order
+            VfieldArgs db = da;
+            db.M = M2;
+            db.exp_b = ctx->eR2.as<int>();
+            timed(ctx, XTC_K_ASSEMBLE, 1, [&] { launch_vfield_tc(&tm_L, &tm_R2, db, 2, 1, st); });
+            timed(ctx, XTC_K_AUX, 1, [&] { launch_vfield_tc_finalize(db, 2, 1, st); });
+          }
           continue;
         }
-        timed(ctx, XTC_K_ASSEMBLE, 1, [&] {
-          if (pl.f64)
+        timed(ctx, XTC_K_ASSEMBLE, M2 ? 2 : 1, [&] {
+          if (pl.f64) {
             launch_assemble_f64(ctx->L.as<double>(), ctx->R.as<double>(), NP, static_cast<int>(kdim), M, st);
-          else
+            if (M2) launch_assemble_f64(ctx->L.as<double>(), ctx->R2.as<double>(), NP, static_cast<int>(kdim), M2, st);
+          } else {
             launch_assemble_tc(&tm_L, &tm_R, NP, static_cast<int>(kdim), std::min(ctx->as_kd, 3), M,
                                ctx->err_dev.as<int>(), st);
+            if (M2)
+              launch_assemble_tc(&tm_L, &tm_R2, NP, static_cast<int>(kdim), std::min(ctx->as_kd, 3), M2,
+                                 ctx->err_dev.as<int>(), st);
+          }
         });
       }
     }

@@ -168,9 +168,11 @@ struct FieldsArgs {
   const int* pair_q;
   void* L;                     // outputs
   void* R;
+  void* R2;                    // spin builds: R for electron-2 spin beta (R is alpha); nullptr otherwise
+  const double* lam2;          // spin builds: beta exchange weights (lam holds the alpha ones)
   int out_parts;               // 0 = FP64 [4*gcp][pq]; 1 = FP32 [pq][4*gcp]; 3 = bf16 x3 split [part][pq][4*gcp]
 };
-size_t fields_smem_bytes(int n_orb, int rank, int pts, bool f64);
+size_t fields_smem_bytes(int n_orb, int rank, int pts, bool f64, bool spin);
 void launch_fields(const FieldsArgs& a, bool f64, cudaStream_t st);  // f64: FP64 V, compute and output
 
 // Step (d) operands in fp16 x2: each FP32 row src[r][0..kdim) is scaled by 2^exps[r] (largest
