@@ -21,6 +21,12 @@
  *       Delta h = -1/2 (2 Delta U_pr^qs gamma_rs - Delta U_pr^sq gamma_rs) and
  *       e0 = -2/3 Delta h_pq gamma_pq.
  *
+ * Beside this closed-shell build the library offers the build for separate alpha and beta
+ * densities of Appendix A (xtc_build_1b2b_rohf), a batched build of many instances
+ * (xtc_build_1b2b_batched), the explicit L of eq. Ldecomp for small orbital sets as a validation
+ * aid (xtc_three_body_L), steps (a) and (b) alone (xtc_jastrow_grad, xtc_vfield, and
+ * xtc_vfield_noalloc, which allocates nothing) and a chunk autotuner (xtc_autotune_chunk).
+ *
  * Units are Hartree atomic units (bohr, Eh).  Conventions:
  *   - gamma is the per-spin (alpha) density matrix; the spin factor 2 is explicit
  *     in the equations (Appendix B).  It must be symmetric.
