@@ -233,7 +233,10 @@ typedef struct xtc_instance {
  * Lane contexts are kept in ctx for later batches and released by xtc_destroy.  Inputs written
  * on ctx's stream are waited for first; the call returns when every instance is done (or has
  * failed: the first failing instance's status is returned and named in xtc_last_error_detail).
- * Each lane holds the workspace of its largest instance.  The outer range of ctx does not apply. */
+ * Each lane holds the workspace of its largest instance.  The outer range of ctx does not apply.
+ * Lanes are created with ctx's parameters, so a grid_chunk set on ctx (by the caller or by
+ * xtc_autotune_chunk for another problem) applies to every instance: leave it 0 for batches of
+ * uneven sizes. */
 XTC_API int xtc_build_1b2b_batched(xtc_ctx* ctx, int n_inst, xtc_instance* inst, int n_lanes);
 
 /* Kernel timers of the last build (requires params.timing != 0).  Kernel ids: */
