@@ -102,6 +102,15 @@ typedef struct {
                           truncates toward zero, so the error grows with the range: at N=120,
                           2 stages double the Delta h and constant errors of 1 stage for about 5%
                           less time; 0 = default (1) */
+  /* Caller allocator for the device workspace (for instance a framework's caching allocator), or
+   * both NULL for cudaMalloc / cudaFree.  alloc returns `bytes` of device memory of p->device
+   * usable on p->stream, or NULL when it cannot (the call then fails with XTC_ERR_OOM); release
+   * takes back a pointer that alloc returned, after the context's stream has finished with it.
+   * Workspace is allocated on first use, grown when a call needs more (old block released
+   * first) and released by xtc_destroy.  Callbacks may run on the library's batch-lane threads. */
+  void* (*alloc)(size_t bytes, void* user);
+  void (*release)(void* ptr, void* user);
+  void* alloc_user;    /* passed to alloc and release */
 } xtc_params;
 
 /* Fills *p with defaults: device 0, default stream, XTC_PREC_FP16X2, automatic chunking. */
@@ -177,6 +186,13 @@ XTC_API int xtc_jastrow_grad(xtc_ctx* ctx, int64_t n, const double* r1, const do
  * (pq = p*n_orb - p*(p-1)/2 + (q - p)).  V has (outer_end - outer_begin) * 3 * n_orb(n_orb+1)/2 doubles. */
 XTC_API int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
                const double* phi, int64_t outer_begin, int64_t outer_end, double* V);
+
+/* Self-test of failure detection (no counterpart in the paper): every wait inside the library's
+ * tensor-core kernels is bounded; when it runs out, the kernel records an error code and returns,
+ * and the call reports XTC_ERR_TIMEOUT.  This call runs one such wait on a barrier that nothing
+ * completes, with a limit of limit_ms (1..4000), and returns what a timed-out build would:
+ * XTC_ERR_TIMEOUT.  The context stays usable.  XTC_ERR_ARG for a limit out of range. */
+XTC_API int xtc_selftest_wait_timeout(xtc_ctx* ctx, int limit_ms);
 
 /* Chunk autotuner (no counterpart in the paper; the chunk is this library's streaming unit):
  * times xtc_build_1b2b on this problem's first outer points, min(n_grid, 2 x the rule's chunk) of

@@ -68,11 +68,11 @@ __device__ __forceinline__ uint32_t mapa_shared(const void* p, uint32_t rank) {
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
   asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
-// Bounded wait.  Returns false when the CTA has aborted or this wait timed out (then it sets the
-// abort flag and the device error word).  CLUSTER: acquire at cluster scope.
+// Bounded wait.  Returns false when the CTA has aborted or this wait timed out after limit_ns
+// (then it sets the abort flag and the device error word).  CLUSTER: acquire at cluster scope.
 template <bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int code) {
+                                          int code, unsigned long long limit_ns = TIMEOUT_NS) {
   auto test = [&] { return CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity); };
   if (test()) return true;
   const unsigned long long t0 = global_timer_ns();
@@ -80,7 +80,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   while (!test()) {
     if ((++it & 63u) == 0) {
       if (*abort_flag) return false;
-      if (global_timer_ns() - t0 > TIMEOUT_NS) {
+      if (global_timer_ns() - t0 > limit_ns) {
         *abort_flag = 1;
         atomicExch(err, code);
         return false;

@@ -19,21 +19,40 @@ using namespace xtc;
 
 namespace {
 
+// A device workspace buffer of a context; owner gives the context's allocator (the caller's
+// alloc/release callbacks, or cudaMalloc/cudaFree when they are NULL) and stream.
 struct DBuf {
   void* p = nullptr;
   size_t n = 0;
+  const xtc_params* owner = nullptr;
   template <typename T>
   T* as() const { return static_cast<T*>(p); }
 };
 
+void release(DBuf& b) {
+  if (b.p) {
+    if (b.owner && b.owner->release) {
+      // a caller allocator may hand the memory out again at once: the context's work on it ends first
+      cudaStreamSynchronize(static_cast<cudaStream_t>(b.owner->stream));
+      b.owner->release(b.p, b.owner->alloc_user);
+    } else {
+      cudaFree(b.p);
+    }
+  }
+  b.p = nullptr;
+  b.n = 0;
+}
+
 bool ensure(DBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.n >= bytes) return true;
-  if (b.p) cudaFree(b.p);
-  b.p = nullptr;
-  b.n = 0;
-  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+  release(b);
+  if (b.owner && b.owner->alloc) {
+    b.p = b.owner->alloc(bytes, b.owner->alloc_user);
+    if (!b.p) return false;
+  } else if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
     cudaGetLastError();
+    b.p = nullptr;
     return false;
   }
   b.n = bytes;
@@ -82,6 +101,12 @@ struct xtc_ctx {
   // batched builds: lane contexts, each with its own stream (created on first use)
   std::vector<xtc_ctx*> lanes;
   std::vector<cudaStream_t> lane_streams;
+
+  std::vector<DBuf*> buffers() {
+    return {&jp_dev, &err_dev, &flag_dev, &grid, &w, &phi, &gamma, &phiT, &pair_p, &pair_q, &jtab, &jtab64,
+            &rho, &colmax, &colexp, &G, &V, &Vacc, &L, &R, &L32, &R32, &eL, &eR, &M, &evec, &lam, &dU_tmp,
+            &dh_tmp, &e0_tmp, &vout, &r1, &r2, &lamd, &gamma_b, &M2, &M3, &lam2, &R2, &R32b, &eR2, &Lv, &T3};
+  }
 };
 
 namespace {
@@ -297,6 +322,7 @@ int xtc_create(xtc_ctx** out, const xtc_params* p) {
   if (p->precision < XTC_PREC_FP64 || p->precision > XTC_PREC_BF16X3) return XTC_ERR_ARG;
   if (p->grid_chunk < 0 || p->grid_chunk % 128 != 0 || p->split_k < 0 || p->split_k > 16) return XTC_ERR_ARG;
   if (p->range_stages < 0 || p->range_stages > 4) return XTC_ERR_ARG;
+  if ((p->alloc == nullptr) != (p->release == nullptr)) return XTC_ERR_ARG;
   if (cudaSetDevice(p->device) != cudaSuccess) {
     cudaGetLastError();
     return XTC_ERR_CUDA;
@@ -307,6 +333,7 @@ int xtc_create(xtc_ctx** out, const xtc_params* p) {
   xtc_ctx* ctx = new xtc_ctx();
   ctx->prm = *p;
   ctx->st = static_cast<cudaStream_t>(p->stream);
+  for (DBuf* b : ctx->buffers()) b->owner = &ctx->prm;
   ctx->n_sm = prop.multiProcessorCount;
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q{};
@@ -333,15 +360,7 @@ int xtc_destroy(xtc_ctx* ctx) {
   cudaSetDevice(ctx->prm.device);
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   else cudaDeviceSynchronize();
-  DBuf* bufs[] = {&ctx->jp_dev, &ctx->err_dev, &ctx->flag_dev, &ctx->grid, &ctx->w, &ctx->phi, &ctx->gamma,
-                  &ctx->phiT, &ctx->pair_p, &ctx->pair_q, &ctx->jtab, &ctx->jtab64, &ctx->rho, &ctx->colmax,
-                  &ctx->colexp, &ctx->G, &ctx->V, &ctx->Vacc, &ctx->L, &ctx->R, &ctx->L32, &ctx->R32,
-                  &ctx->eL, &ctx->eR, &ctx->M, &ctx->evec, &ctx->lam, &ctx->dU_tmp,
-                  &ctx->dh_tmp, &ctx->e0_tmp, &ctx->vout, &ctx->r1, &ctx->r2,
-                  &ctx->lamd, &ctx->gamma_b, &ctx->M2, &ctx->M3, &ctx->Lv, &ctx->T3,
-                  &ctx->lam2, &ctx->R2, &ctx->R32b, &ctx->eR2};
-  for (DBuf* b : bufs)
-    if (b->p) cudaFree(b->p);
+  for (DBuf* b : ctx->buffers()) release(*b);
   for (xtc_ctx* lane : ctx->lanes) xtc_destroy(lane);
   for (cudaStream_t s : ctx->lane_streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
@@ -1004,7 +1023,6 @@ extern "C" int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double*
   const bool out_dev = is_device_ptr(V);
   const size_t per_point = static_cast<size_t>(3) * pl.NP;
   const int64_t n_out = pl.oe - pl.ob;
-  DBuf tmp;
   for (int64_t c0 = pl.ob; c0 < pl.oe; c0 += pl.gc) {
     const int64_t n_i = std::min<int64_t>(pl.gc, pl.oe - c0);
     if ((rc = run_vfield(ctx, pl, d_grid, c0, n_i, maps))) return rc;
@@ -1022,6 +1040,21 @@ extern "C" int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double*
   if ((rc = check_device_error(ctx))) return rc;
   finish_timers(ctx);
   return XTC_OK;
+}
+
+// ====================================================================== bounded-wait self-test
+extern "C" int xtc_selftest_wait_timeout(xtc_ctx* ctx, int limit_ms) {
+  if (!ctx) return XTC_ERR_ARG;
+  if (limit_ms < 1 || limit_ms > 4000) return fail(ctx, XTC_ERR_ARG, "selftest: limit_ms outside 1..4000");
+  CUDA_OK(cudaSetDevice(ctx->prm.device));
+  CUDA_OK(cudaMemsetAsync(ctx->err_dev.p, 0, 16, ctx->st));
+  launch_wait_timeout_selftest(ctx->err_dev.as<int>(), 1000000ull * static_cast<unsigned long long>(limit_ms),
+                               ctx->st);
+  CUDA_OK(cudaGetLastError());
+  const int rc = check_device_error(ctx);  // XTC_ERR_TIMEOUT when the wait gave up, as it must
+  CUDA_OK(cudaMemsetAsync(ctx->err_dev.p, 0, 16, ctx->st));
+  CUDA_OK(cudaStreamSynchronize(ctx->st));
+  return rc;
 }
 
 // ====================================================================== chunk autotuner

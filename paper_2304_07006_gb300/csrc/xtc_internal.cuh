@@ -39,6 +39,10 @@ constexpr int CHUNK_ALIGN = 128;
 // Error codes written by kernels into the context's device error word.
 constexpr int DEV_ERR_TIMEOUT_VF = 1;
 constexpr int DEV_ERR_TIMEOUT_AS = 2;
+constexpr int DEV_ERR_TIMEOUT_SELFTEST = 3;
+// Self-test of the bounded waits: one CTA waits on an mbarrier that nothing arrives on, with the
+// kernels' own wait routine and a limit of limit_ns, and records DEV_ERR_TIMEOUT_SELFTEST in err.
+void launch_wait_timeout_selftest(int* err, unsigned long long limit_ns, cudaStream_t st);
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // Row stride of the FP64 accumulator M[pq][rs]: whole 128-column (bf16 step d) and 192-column

@@ -21,13 +21,19 @@ KERNEL_NAMES = ("prep", "vfield", "fields", "assemble", "final", "grad", "aux")
 EXPORTED = ("xtc_default_params", "xtc_create", "xtc_destroy", "xtc_strerror", "xtc_last_error_detail",
             "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b", "xtc_jastrow_grad", "xtc_vfield",
             "xtc_get_timings", "xtc_vfield_noalloc", "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf",
-            "xtc_three_body_L", "xtc_autotune_chunk")
+            "xtc_three_body_L", "xtc_autotune_chunk", "xtc_selftest_wait_timeout")
 
 
 class XtcParams(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("grid_chunk", ctypes.c_int64), ("split_k", ctypes.c_int), ("timing", ctypes.c_int),
-                ("range_stages", ctypes.c_int)]
+                ("range_stages", ctypes.c_int), ("alloc", ctypes.c_void_p), ("release", ctypes.c_void_p),
+                ("alloc_user", ctypes.c_void_p)]
+
+
+# xtc_params.alloc / xtc_params.release
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 
 class XtcInstance(ctypes.Structure):
@@ -76,9 +82,11 @@ def load(path: str = LIB_PATH):
     lib.xtc_build_1b2b_rohf.argtypes = [P, I64, I, D, D, D, D, D, D, D, D, D, D, D]
     lib.xtc_three_body_L.argtypes = [P, I64, I, D, D, D, D]
     lib.xtc_autotune_chunk.argtypes = [P, I64, I, D, D, D, D, ctypes.POINTER(ctypes.c_int64)]
+    lib.xtc_selftest_wait_timeout.argtypes = [P, I]
     for name in ("xtc_create", "xtc_destroy", "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b",
                  "xtc_jastrow_grad", "xtc_vfield", "xtc_get_timings", "xtc_vfield_noalloc",
-                 "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf", "xtc_three_body_L", "xtc_autotune_chunk"):
+                 "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf", "xtc_three_body_L", "xtc_autotune_chunk",
+                 "xtc_selftest_wait_timeout"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -111,7 +119,10 @@ class Context:
     """One library context (one device, one stream, one precision)."""
 
     def __init__(self, precision="fp16x2", device=0, stream=None, grid_chunk=0, split_k=0, timing=False,
-                 range_stages=0):
+                 range_stages=0, allocator=None):
+        """allocator: optional pair (alloc, release) of Python callables, alloc(nbytes) -> device
+        address (int, 0 when it cannot) and release(address), that supply the device workspace
+        (for instance from torch's caching allocator); default cudaMalloc / cudaFree."""
         lib = load()
         self._lib = lib
         p = XtcParams()
@@ -123,6 +134,13 @@ class Context:
         p.split_k = split_k
         p.timing = 1 if timing else 0
         p.range_stages = range_stages
+        self._alloc_cbs = None
+        if allocator is not None:
+            alloc_py, release_py = allocator
+            self._alloc_cbs = (ALLOC_FN(lambda n, user: alloc_py(int(n)) or None),
+                               RELEASE_FN(lambda ptr, user: release_py(int(ptr))))
+            p.alloc = ctypes.cast(self._alloc_cbs[0], ctypes.c_void_p)
+            p.release = ctypes.cast(self._alloc_cbs[1], ctypes.c_void_p)
         h = ctypes.c_void_p()
         rc = lib.xtc_create(ctypes.byref(h), ctypes.byref(p))
         if rc != 0:
@@ -198,6 +216,10 @@ class Context:
             _ptr(res["dU_aa"]), _ptr(res["dU_ab"]), _ptr(res["dU_bb"]), _ptr(res["dh_a"]), _ptr(res["dh_b"]),
             _ptr(res["e0"])))
         return res
+
+    def selftest_wait_timeout(self, limit_ms=50):
+        """Runs one bounded device wait that must time out; returns the status (XTC_ERR_TIMEOUT)."""
+        return int(self._lib.xtc_selftest_wait_timeout(self._h, int(limit_ms)))
 
     def autotune_chunk(self, grid, weights, phi, gamma):
         """Times a few grid-chunk lengths on this problem and keeps the fastest for later builds

@@ -67,3 +67,23 @@ def test_missing_library_fails_loudly(tmp_path):
             xtc.load(str(tmp_path / "nope.so"))
     finally:
         xtc._lib = saved
+
+
+def test_params_struct_layout_matches_the_header(tmp_path):
+    """The binding's xtc_params has the size and field offsets that a C compiler gives the header's."""
+    import shutil
+    import subprocess
+    from paper_2304_07006_gb300 import xtc
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f[0] for f in xtc.XtcParams._fields_]
+    body = " ".join(f'printf("%zu ", offsetof(xtc_params, {f}));' for f in fields)
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "xtc.h"\n'
+                   f'int main(void) {{ printf("%zu ", sizeof(xtc_params)); {body} return 0; }}\n')
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(xtc.XtcParams)] + [getattr(xtc.XtcParams, f).offset for f in fields]
+    assert got == want
