@@ -1,6 +1,7 @@
 // Host side of the xTC library: the C ABI of include/xtc.h, input validation, the
 // factorisation of gamma, the device workspace, TMA descriptors and the chunked build loop.
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -58,6 +59,14 @@ bool ensure(DBuf& b, size_t bytes) {
   b.n = bytes;
   return true;
 }
+
+// NVTX range for profilers (a no-op unless a tool is attached): the build, each chunk, each step.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct TimedLaunch {
   int kind;
@@ -687,6 +696,7 @@ struct Pass {
 
 int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
                const double* phi, const double* const* gammas, const BuildOut& out) {
+  NvtxRange nvtx_build(out.n_spin == 2 ? "xtc build (spin)" : "xtc build");
   CUDA_OK(cudaSetDevice(ctx->prm.device));
   reset_timers(ctx);
   cudaStream_t st = ctx->st;
@@ -801,8 +811,13 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
 
   // ---- chunk loop
   for (int64_t c0 = pl.ob; c0 < pl.oe; c0 += pl.gc) {
+    NvtxRange nvtx_chunk("chunk");
     const int64_t n_i = std::min<int64_t>(pl.gc, pl.oe - c0);
-    if ((rc = run_vfield(ctx, pl, d_grid, c0, n_i, maps))) return rc;
+    {
+      NvtxRange nvtx_ab("steps a+b");
+      if ((rc = run_vfield(ctx, pl, d_grid, c0, n_i, maps))) return rc;
+    }
+    NvtxRange nvtx_cd("steps c+d");
     for (const Pass& ps : passes) {
       const int groups = std::max(1, (ps.rank + RANK_GROUP - 1) / RANK_GROUP);
       double* M = ps.M->as<double>();
@@ -883,6 +898,7 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
   }
 
   // ---- final: Delta U, Delta h, e0
+  NvtxRange nvtx_final("final");
   const size_t n4 = static_cast<size_t>(N) * N * N * N;
   const size_t n2b = static_cast<size_t>(N) * N * 8;
   if (!ensure(ctx->dh_tmp, 2 * n2b) || !ensure(ctx->e0_tmp, 8)) return fail(ctx, XTC_ERR_OOM, "dh staging");
