@@ -332,3 +332,19 @@ def test_open_shell_pins_catch_planted_mistakes(monkeypatch):
     monkeypatch.setattr(spin, "intermediates", orig)
     got = spin.build(p, ga, gb)
     assert max(np.abs(got[k] - want[k]).max() for k in ("dU_aa", "dU_ab", "dU_bb")) < 1e-12 * np.abs(want["dU_aa"]).max()
+
+
+@pytest.mark.slow
+def test_h2_config_open_shell_routes_agree_to_1e10_hartree():
+    """The H2-like workload with one alpha and no beta electron: Appendix A against the
+    spin-orbital definition (20 spin orbitals, 6.4e7 L entries)."""
+    p = synth.make_config("h2")
+    n = p.n_orb
+    ga = np.diag([1.0] + [0.0] * (n - 1))
+    gb = np.zeros((n, n))
+    r1 = bruteforce.build_spin(p, ga, gb)
+    r2 = spin.build(p, ga, gb)
+    for k in ("dU_aa", "dU_ab", "dU_bb", "dh_a", "dh_b"):
+        assert np.abs(r1[k] - r2[k]).max() < 1e-10, k
+    assert abs(r1["e0"] - r2["e0"]) < 1e-10
+    assert abs(r1["e0_rdm"] - r2["e0"]) < 1e-10
