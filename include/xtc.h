@@ -84,7 +84,7 @@ typedef enum {
   XTC_PREC_FP16X2 = 1, /* steps (b) and (d): 2-term FP16 split (3 tensor-core products) with
                           power-of-2 scaling (per pair column of rho in step b, per row of L and R
                           in step d); FP32 accumulation in TMEM over short ranges, FP32 running
-                          sums flushed to FP64 every 128 ranges; FP64 accumulation of Delta U
+                          sums flushed to FP64 every 8,192 inner points; FP64 accumulation of Delta U
                           across grid chunks, of Delta h and of e0 */
   XTC_PREC_BF16X3 = 2  /* steps (b) and (d): 3-term BF16 split (6 products), otherwise as FP16X2 */
 } xtc_precision;
