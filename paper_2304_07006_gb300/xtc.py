@@ -107,6 +107,34 @@ def _ptr(a):
     raise TypeError(f"unsupported array type {type(a)}")
 
 
+def _size(a):
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+
+
+def _need(a, n, name, dtype="float64"):
+    """Checks that a (numpy array or tensor, or None) holds at least n elements of dtype: the
+    library reads and writes exactly the sizes its arguments imply, so a short or mistyped buffer
+    would be overrun in host or device memory."""
+    if a is None:
+        return None
+    kind = str(a.dtype).replace("torch.", "")
+    if kind != dtype:
+        raise TypeError(f"{name} must be {dtype}, not {kind}")
+    if _size(a) < n:
+        raise ValueError(f"{name} holds {_size(a)} elements, {n} needed")
+    return a
+
+
+def _grid_inputs(grid, weights, phi):
+    """n_grid, n_orb from phi ([n_grid][n_orb]) and the size checks of grid and weights."""
+    if len(phi.shape) != 2:
+        raise ValueError("phi must be [n_grid][n_orb]")
+    n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+    _need(grid, 3 * n_grid, "grid_xyz")
+    _need(weights, n_grid, "weights")
+    return n_grid, n_orb
+
+
 def _f64(a):
     if isinstance(a, np.ndarray):
         return np.ascontiguousarray(a, dtype=np.float64)
@@ -175,6 +203,10 @@ class Context:
         ns = np.ascontiguousarray(nuc_set, dtype=np.int32)
         tm = np.ascontiguousarray(terms, dtype=np.int32)
         cf = np.ascontiguousarray(coef, dtype=np.float64)
+        if nuc.ndim != 2 or nuc.shape[1] != 3 or ns.shape != (nuc.shape[0],):
+            raise ValueError("nuc_xyz must be [n_nuc][3] and nuc_set [n_nuc]")
+        if tm.ndim != 2 or tm.shape[1] != 3 or cf.ndim != 2 or cf.shape[1] != tm.shape[0]:
+            raise ValueError("terms must be [n_terms][3] and coef [n_sets][n_terms]")
         self._check(self._lib.xtc_set_jastrow(self._h, nuc.shape[0], _ptr(nuc), _ptr(ns), cf.shape[0],
                                               tm.shape[0], _ptr(tm), _ptr(cf)))
 
@@ -184,13 +216,18 @@ class Context:
     def build(self, grid, weights, phi, gamma, dU=None, dU_f32=None, dh=None, e0=None, want_dU=True):
         """Runs the build.  With numpy inputs and no outputs given, returns numpy outputs."""
         grid, weights, phi, gamma = _f64(grid), _f64(weights), _f64(phi), _f64(gamma)
-        n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+        n_grid, n_orb = _grid_inputs(grid, weights, phi)
+        _need(gamma, n_orb ** 2, "gamma")
         if dU is None and dU_f32 is None and want_dU:
             dU = np.empty((n_orb,) * 4)
         if dh is None:
             dh = np.empty((n_orb, n_orb))
         if e0 is None:
             e0 = np.empty(1)
+        _need(dU, n_orb ** 4, "dU")
+        _need(dU_f32, n_orb ** 4, "dU_f32", "float32")
+        _need(dh, n_orb ** 2, "dh")
+        _need(e0, 1, "e0")
         self._check(self._lib.xtc_build_1b2b(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
                                              _ptr(gamma), _ptr(dU), _ptr(dU_f32), _ptr(dh), _ptr(e0)))
         return {"dU": dU if dU is not None else dU_f32, "dh": dh, "e0": e0}
@@ -202,7 +239,9 @@ class Context:
         want_dU).  Returns them in a dict."""
         grid, weights, phi = _f64(grid), _f64(weights), _f64(phi)
         gamma_a, gamma_b = _f64(gamma_a), _f64(gamma_b)
-        n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+        n_grid, n_orb = _grid_inputs(grid, weights, phi)
+        _need(gamma_a, n_orb ** 2, "gamma_a")
+        _need(gamma_b, n_orb ** 2, "gamma_b")
         res = {}
         for k in ("dU_aa", "dU_ab", "dU_bb"):
             res[k] = out.get(k)
@@ -211,6 +250,11 @@ class Context:
         for k in ("dh_a", "dh_b"):
             res[k] = out.get(k) if out.get(k) is not None else np.empty((n_orb, n_orb))
         res["e0"] = out.get("e0") if out.get("e0") is not None else np.empty(1)
+        for k in ("dU_aa", "dU_ab", "dU_bb"):
+            _need(res[k], n_orb ** 4, k)
+        _need(res["dh_a"], n_orb ** 2, "dh_a")
+        _need(res["dh_b"], n_orb ** 2, "dh_b")
+        _need(res["e0"], 1, "e0")
         self._check(self._lib.xtc_build_1b2b_rohf(
             self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi), _ptr(gamma_a), _ptr(gamma_b),
             _ptr(res["dU_aa"]), _ptr(res["dU_ab"]), _ptr(res["dU_bb"]), _ptr(res["dh_a"]), _ptr(res["dh_b"]),
@@ -225,7 +269,8 @@ class Context:
         """Times a few grid-chunk lengths on this problem and keeps the fastest for later builds
         (xtc_autotune_chunk); returns it."""
         grid, weights, phi, gamma = _f64(grid), _f64(weights), _f64(phi), _f64(gamma)
-        n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+        n_grid, n_orb = _grid_inputs(grid, weights, phi)
+        _need(gamma, n_orb ** 2, "gamma")
         c = ctypes.c_int64(0)
         self._check(self._lib.xtc_autotune_chunk(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
                                                  _ptr(gamma), ctypes.byref(c)))
@@ -235,9 +280,10 @@ class Context:
         """The explicit three-body tensor of eq. Ldecomp (xtc_three_body_L): out[p, r, t, q, s, u] =
         L_prt^qsu over the context's outer range; a numpy array unless out is given."""
         grid, weights, phi = _f64(grid), _f64(weights), _f64(phi)
-        n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+        n_grid, n_orb = _grid_inputs(grid, weights, phi)
         if out is None:
             out = np.empty((n_orb,) * 6)
+        _need(out, n_orb ** 6, "L")
         self._check(self._lib.xtc_three_body_L(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
                                                _ptr(out)))
         return out
@@ -245,17 +291,21 @@ class Context:
     def jastrow_grad(self, r1, r2, out=None):
         r1, r2 = _f64(r1), _f64(r2)
         n = int(r1.shape[0])
+        _need(r1, 3 * n, "r1")
+        _need(r2, 3 * n, "r2")
         if out is None:
             out = np.empty((n, 3))
+        _need(out, 3 * n, "out")
         self._check(self._lib.xtc_jastrow_grad(self._h, n, _ptr(r1), _ptr(r2), _ptr(out)))
         return out
 
     def vfield(self, grid, weights, phi, outer_begin, outer_end, out=None):
         grid, weights, phi = _f64(grid), _f64(weights), _f64(phi)
-        n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+        n_grid, n_orb = _grid_inputs(grid, weights, phi)
         n_pair = n_orb * (n_orb + 1) // 2
         if out is None:
-            out = np.empty((outer_end - outer_begin, 3, n_pair))
+            out = np.empty((max(outer_end - outer_begin, 0), 3, n_pair))
+        _need(out, max(outer_end - outer_begin, 0) * 3 * n_pair, "V")
         self._check(self._lib.xtc_vfield(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
                                          int(outer_begin), int(outer_end), _ptr(out)))
         return out
@@ -263,7 +313,8 @@ class Context:
     def vfield_noalloc(self, grid, weights, phi, outer_begin, outer_end, out):
         """xtc_vfield without device allocation: every argument must be a CUDA tensor (float64);
         workspace comes from the library's fixed scratch array (small problems only)."""
-        n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+        n_grid, n_orb = _grid_inputs(grid, _need(weights, 0, "weights"), _need(phi, 0, "phi"))
+        _need(out, max(outer_end - outer_begin, 0) * 3 * (n_orb * (n_orb + 1) // 2), "V")
         self._check(self._lib.xtc_vfield_noalloc(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
                                                  int(outer_begin), int(outer_end), _ptr(out)))
         return out
@@ -281,12 +332,20 @@ class Context:
             ns = np.ascontiguousarray(d["nuc_set"], dtype=np.int32)
             tm = np.ascontiguousarray(d["terms"], dtype=np.int32)
             cf = np.ascontiguousarray(d["coef"], dtype=np.float64)
-            n_grid, n_orb = int(phi.shape[0]), int(phi.shape[1])
+            n_grid, n_orb = _grid_inputs(grid, w, phi)
+            _need(gamma, n_orb ** 2, f"instance {k} gamma")
+            if nuc.ndim != 2 or nuc.shape[1] != 3 or ns.shape != (nuc.shape[0],) or tm.ndim != 2 \
+                    or tm.shape[1] != 3 or cf.ndim != 2 or cf.shape[1] != tm.shape[0]:
+                raise ValueError(f"instance {k}: Jastrow arrays of inconsistent shapes")
             dU, dU32 = d.get("dU"), d.get("dU_f32")
             if dU is None and dU32 is None and want_dU:
                 dU = np.empty((n_orb,) * 4)
             dh = d.get("dh") if d.get("dh") is not None else np.empty((n_orb, n_orb))
             e0 = d.get("e0") if d.get("e0") is not None else np.empty(1)
+            _need(dU, n_orb ** 4, f"instance {k} dU")
+            _need(dU32, n_orb ** 4, f"instance {k} dU_f32", "float32")
+            _need(dh, n_orb ** 2, f"instance {k} dh")
+            _need(e0, 1, f"instance {k} e0")
             keep += [grid, w, phi, gamma, nuc, ns, tm, cf, dU, dU32, dh, e0]
             it = arr[k]
             it.n_grid, it.n_orb = n_grid, n_orb

@@ -87,3 +87,42 @@ def test_params_struct_layout_matches_the_header(tmp_path):
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(xtc.XtcParams)] + [getattr(xtc.XtcParams, f).offset for f in fields]
     assert got == want
+
+
+def _shell_context():
+    """A Context without a device: the binding's argument checks run before any library call."""
+    from paper_2304_07006_gb300 import Context
+    c = Context.__new__(Context)
+    c._h, c._lib = None, None
+    return c
+
+
+def test_binding_rejects_short_or_mistyped_buffers():
+    import numpy as np
+    c = _shell_context()
+    n_grid, n = 10, 3
+    grid, w, phi, g = np.zeros((n_grid, 3)), np.ones(n_grid), np.zeros((n_grid, n)), np.eye(n)
+    with pytest.raises(ValueError, match="grid_xyz"):
+        c.build(grid[:5], w, phi, g)
+    with pytest.raises(ValueError, match="weights"):
+        c.build(grid, w[:4], phi, g)
+    with pytest.raises(ValueError, match="gamma"):
+        c.build(grid, w, phi, np.eye(2))
+    with pytest.raises(TypeError, match="dh must be float64"):
+        c.build(grid, w, phi, g, dh=np.zeros((n, n), dtype=np.float32))
+    with pytest.raises(ValueError, match="dU"):
+        c.build(grid, w, phi, g, dU=np.zeros(n ** 3))
+    with pytest.raises(TypeError, match="dU_f32 must be float32"):
+        c.build(grid, w, phi, g, dU_f32=np.zeros(n ** 4))
+    with pytest.raises(ValueError, match="dh_b"):
+        c.build_rohf(grid, w, phi, g, g, dh_b=np.zeros(2))
+    with pytest.raises(ValueError, match="L holds"):
+        c.three_body_L(grid, w, phi, out=np.zeros(n ** 5))
+    with pytest.raises(ValueError, match="V holds"):
+        c.vfield(grid, w, phi, 0, 4, out=np.zeros(5))
+    with pytest.raises(ValueError, match="r2"):
+        c.jastrow_grad(np.zeros((4, 3)), np.zeros((2, 3)))
+    with pytest.raises(ValueError, match="nuc_set"):
+        c.set_jastrow(np.zeros((2, 3)), [0], np.array([(0, 0, 1)]), np.ones((1, 1)))
+    with pytest.raises(ValueError, match="coef"):
+        c.set_jastrow(np.zeros((2, 3)), [0, 0], np.array([(0, 0, 1)]), np.ones((1, 2)))
