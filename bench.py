@@ -112,9 +112,11 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one vfield_tc_kernel<2,0> launch on the first 1184
-# outer points of the workload (profiles/vfield_tc_n2.md); valid for that kernel version only
-VFIELD_DRAM_BYTES_CAPTURED = 17_627_806_208 + 2_669_686_528
+# dram__bytes_read.sum + dram__bytes_write.sum of one step (b) GEMM launch (fp16x2) captured with
+# ncu on the first VFIELD_CAPTURE_OUTER outer points of the workload (`--ncu-case`), for GEMM
+# engine revision VFIELD_CAPTURE_REVISION; with another revision the traffic is reported as null
+VFIELD_CAPTURE_REVISION = 2
+VFIELD_DRAM_BYTES_CAPTURED = None
 VFIELD_CAPTURE_OUTER = 1184
 
 
@@ -327,7 +329,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp16x2", choices=["fp16x2", "bf16x3"])
-    ap.add_argument("--fp64-sample", type=int, default=512, help="outer points for the FP64 GPU comparison")
+    ap.add_argument("--fp64-sample", type=int, default=1024, help="outer points for the FP64 GPU comparison")
     ap.add_argument("--cpu-sample", type=int, default=4, help="outer points for the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--batched", type=int, default=32, metavar="N",
@@ -410,10 +412,13 @@ def main():
     peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     achieved = vf_flops_launch / (vf_ms * 1e-3) / 1e12
     issued_factor = 3 if args.precision == "fp16x2" else 6
-    # DRAM bytes of the step (b) kernel from the ncu capture in profiles/vfield_tc_n2.md (fp16x2,
-    # 1184 outer points), scaled by the outer points of a launch (traffic grows with the row tiles)
+    # DRAM bytes of the step (b) kernel from the ncu capture (fp16x2, VFIELD_CAPTURE_OUTER outer
+    # points), scaled by the outer points of a launch (traffic grows with the row tiles); only for
+    # the engine revision that was captured
+    from paper_2304_07006_gb300.xtc import engine_revision
     traffic = None
-    if args.precision == "fp16x2" and VFIELD_DRAM_BYTES_CAPTURED:
+    if (args.precision == "fp16x2" and VFIELD_DRAM_BYTES_CAPTURED
+            and engine_revision() == VFIELD_CAPTURE_REVISION):
         traffic = VFIELD_DRAM_BYTES_CAPTURED * (NG / n_vf) / VFIELD_CAPTURE_OUTER
     roofline = {"kernel": "vfield_tc (step b: tcgen05 split-fp16 GEMM V = G rho^T)",
                 "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -469,8 +474,14 @@ def main():
                              "seconds_per_build_extrapolated": full_fp64_s,
                              "tflops_extrapolated": F["total"] / full_fp64_s / 1e12,
                              "mixed_speedup_vs_fp64": full_fp64_s / (ms_step / 1e3)}
-        line["error_eh_vs_fp64_gpu"] = dict(err, sample=f"{S} random outer points, full inner sum; max |diff| "
-                                                         f"over every Delta U / Delta h entry and the constant")
+        # the outputs are sums over outer points: an error that grows with the outer sum (a
+        # one-signed bias) reaches NG / S times the sample's on the whole grid; random errors less
+        line["error_eh_vs_fp64_gpu"] = {
+            "sample": {k: v for k, v in err.items()},
+            "whole_grid_extrapolated": {k: v * NG / S for k, v in err.items()},
+            "note": f"max |mixed - FP64 GPU| over every Delta U / Delta h entry and the constant on {S} random outer "
+                    f"points (full inner sum); whole_grid_extrapolated = sample x {NG}/{S}, the bound for an error "
+                    f"that grows linearly with the outer sum"}
 
         # end to end through the C ABI with pinned host buffers (copies inside the timed region)
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()

@@ -81,12 +81,19 @@ typedef enum {
 
 typedef enum {
   XTC_PREC_FP64 = 0,   /* all four steps in FP64 (SIMT) */
-  XTC_PREC_FP16X2 = 1, /* steps (b) and (d): 2-term FP16 split (3 tensor-core products) with
-                          power-of-2 scaling (per pair column of rho in step b, per row of L and R
-                          in step d); FP32 accumulation in TMEM over short ranges, FP32 running
-                          sums flushed to FP64 every 8,192 inner points; FP64 accumulation of Delta U
-                          across grid chunks, of Delta h and of e0 */
-  XTC_PREC_BF16X3 = 2  /* steps (b) and (d): 3-term BF16 split (6 products), otherwise as FP16X2 */
+  XTC_PREC_FP16X2 = 1, /* steps (b) and (d): block-exact 2-term FP16 split (3 tensor-core products)
+                          with power-of-2 scaling (per pair column of rho in step b, per row of L
+                          and R in step d): per block of 32 inner values hi = an integer of at most
+                          10 bits times the block's power-of-2 quantum, lo = the FP16 remainder, so
+                          the hi x hi products of a block sum exactly in the tensor core's FP32
+                          accumulator (no truncation bias); the cross products accumulate apart.
+                          FP32 running sums (round to nearest) flushed to FP64 every 8,192 inner
+                          points; FP64 accumulation of Delta U across grid chunks, of Delta h and
+                          of e0 */
+  XTC_PREC_BF16X3 = 2  /* steps (b) and (d): 3-term BF16 split (6 products) accumulated in the tensor
+                          cores over short ranges (range_stages), otherwise as FP16X2; its FP32
+                          accumulation truncates toward zero at every MMA, a one-signed error that
+                          grows with the grid */
 } xtc_precision;
 
 typedef struct {
@@ -96,12 +103,11 @@ typedef struct {
   int64_t grid_chunk;  /* outer grid points per chunk (multiple of 128); 0 = automatic */
   int split_k;         /* inner-grid slices of step (b) accumulated separately (1..16); 0 = automatic */
   int timing;          /* non-zero: record CUDA events around every kernel (see xtc_get_timings) */
-  int range_stages;    /* tensor-core precisions: inner-sum stages of 32 points accumulated in the
-                          tensor cores before an exactly rounded FP32 add (1..4; bf16x3 uses at
-                          most 2 in step b and 3 in step d).  The tensor-core FP32 accumulator
-                          truncates toward zero, so the error grows with the range: at N=120,
-                          2 stages double the Delta h and constant errors of 1 stage for about 5%
-                          less time; 0 = default (1) */
+  int range_stages;    /* XTC_PREC_BF16X3: inner-sum stages of 32 points accumulated in the tensor
+                          cores before a round-to-nearest FP32 add (1..4; at most 2 in step b and
+                          3 in step d).  That accumulator truncates toward zero, so the error grows
+                          with the range.  0 = default (1).  XTC_PREC_FP16X2 ignores it: its exact
+                          hi x hi ranges are one 32-point block */
   /* Caller allocator for the device workspace (for instance a framework's caching allocator), or
    * both NULL for cudaMalloc / cudaFree.  alloc returns `bytes` of device memory of p->device
    * usable on p->stream, or NULL when it cannot (the call then fails with XTC_ERR_OOM); release
@@ -271,12 +277,20 @@ enum {
  * count; either pointer may be NULL.  n = array length (>= XTC_N_KERNELS). */
 XTC_API int xtc_get_timings(xtc_ctx* ctx, double* ms, int64_t* launches, int n);
 
+/* Revision number of the tensor-core GEMM engine (steps (b) and (d)), raised whenever its code
+ * changes.  Profiler counters recorded for one revision (DRAM traffic per launch, for instance)
+ * describe that revision only.  Needs no GPU and no context. */
+XTC_API int xtc_engine_revision(void);
+
 /* Allocation-free variant of xtc_vfield, for callers that must not allocate device memory (for
  * instance code that runs inside a host framework owning every allocation, or a loop that may
  * not call cudaMalloc).  The paper has no counterpart; it is a deployment convenience.
- * Same computation and output as xtc_vfield (steps (a)+(b) in the context's precision), but:
- *   - grid_xyz, weights, phi and V must be device pointers on the context's device (else
- *     XTC_ERR_ARG); nothing is staged through host memory;
+ * Same computation and output layout as xtc_vfield (steps (a)+(b) in the context's precision), but:
+ *   - grid_xyz, weights, phi and V must be device (or managed) pointers on the context's device
+ *     (else XTC_ERR_ARG, also for memory of another GPU); nothing is staged through host memory;
+ *   - the tensor-core precisions keep their running sums in FP32 for the whole inner sum (no
+ *     FP64 flush every 8,192 inner points, which xtc_vfield does), so results differ from
+ *     xtc_vfield by FP32 rounding that grows with n_grid;
  *   - all workspace comes from one fixed device array of XTC_NOALLOC_SCRATCH_MIB MiB built into
  *     the library (every GPU that loads the library holds it until the process exits); problems
  *     whose workspace does not fit (with P = 2 parts for fp16x2, 3 for bf16x3, 4 for FP64:
@@ -286,7 +300,8 @@ XTC_API int xtc_get_timings(xtc_ctx* ctx, double* ms, int64_t* launches, int n);
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture.  Every call reuses the same array, which keeps the
  * last call's contents: calls that overlap on the GPU race with each other, so serialise them.
- * The call is synchronous with respect to the host, like the others. */
+ * The call is synchronous with respect to the host, like the others: it synchronises the
+ * context's stream before returning.  The calling thread's current device is restored. */
 #define XTC_NOALLOC_SCRATCH_MIB 64
 XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz,
                                const double* weights, const double* phi, int64_t outer_begin, int64_t outer_end,

@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 
 #include "jastrow_coef.cuh"
+#include "simt_pack.cuh"
 #include "xtc_internal.cuh"
 
 namespace xtc {
@@ -98,48 +99,77 @@ __device__ __forceinline__ int col_exponent(const unsigned int* colmax, int pq, 
   return min(max(14 - e, -60), 60);
 }
 
-template <int PARTS, bool BF16>
-__global__ void rho_split_kernel(const double* __restrict__ phiT, const double* __restrict__ w, int64_t n_grid,
-                                 int64_t n_pad, int n_pair, const int* __restrict__ pp, const int* __restrict__ pq_,
-                                 const unsigned int* __restrict__ colmax, bool scale, int* __restrict__ colexp,
-                                 uint16_t* __restrict__ out) {
+// fp16 (2 parts, exact split): warp w of the CTA handles pair pq = 8 * blockIdx.y + w over one
+// accumulation range of the GEMM, points j0 + lane + 32 s (s < kd, j0 = 32 kd blockIdx.x); the
+// range shares one quantum (largest |value| of the range, `bits` bits).  Layout: the two parts of a
+// 32-point block share one 128-byte row, [pq][j / 32][part][j % 32].
+__global__ void rho_split_f16_kernel(const double* __restrict__ phiT, const double* __restrict__ w, int64_t n_grid,
+                                     int64_t n_pad, int n_pair, const int* __restrict__ pp,
+                                     const int* __restrict__ pq_, const unsigned int* __restrict__ colmax, int kd,
+                                     int bits, int* __restrict__ colexp, uint16_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int pq = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (pq >= n_pair) return;  // whole warp
+  const int e = col_exponent(colmax, pq, true);
+  if (blockIdx.x == 0 && lane == 0) colexp[pq] = e;
+  const int p = pp[pq], q = pq_[pq];
+  const int64_t j0 = static_cast<int64_t>(blockIdx.x) * 32 * kd;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  double m = 0.0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int64_t j = j0 + 32 * s + lane;
+    if (s < kd && j < n_grid) v[s] = ldexp(w[j] * phiT[p * n_pad + j] * phiT[q * n_pad + j], e);
+    m = fmax(m, fabs(v[s]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int qe = exact_quantum(m, bits);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int64_t j = j0 + 32 * s + lane;
+    if (s >= kd || j >= n_pad) break;
+    __half h, l;
+    split_exact(v[s], qe, h, l);
+    const int64_t o = static_cast<int64_t>(pq) * 2 * n_pad + (j >> 5) * 64 + (j & 31);
+    out[o] = __half_as_ushort(h);
+    out[o + 32] = __half_as_ushort(l);
+  }
+}
+
+// bf16 (3 parts): per-element split with a plain power-of-2 scale of 1 (no exact ranges), one
+// plane per part: [part][pq][j].
+__global__ void rho_split_bf16_kernel(const double* __restrict__ phiT, const double* __restrict__ w, int64_t n_grid,
+                                      int64_t n_pad, int n_pair, const int* __restrict__ pp,
+                                      const int* __restrict__ pq_, int* __restrict__ colexp,
+                                      uint16_t* __restrict__ out) {
   const int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const int pq0 = blockIdx.y * 8;
   const int64_t part_stride = static_cast<int64_t>(n_pair) * n_pad;
   for (int u = 0; u < 8; ++u) {
     const int pq = pq0 + u;
     if (pq >= n_pair) break;
-    const int e = col_exponent(colmax, pq, scale);
-    if (j == 0) colexp[pq] = e;
+    if (j == 0) colexp[pq] = 0;
     if (j >= n_pad) continue;
     const int p = pp[pq], q = pq_[pq];
-    double v = j < n_grid ? w[j] * phiT[p * n_pad + j] * phiT[q * n_pad + j] : 0.0;
-    v = ldexp(v, e);
-    if (!BF16) {
-      // the two parts of a 32-point block share one 128-byte row: [pq][j / 32][part][j % 32]
-      const int64_t o = static_cast<int64_t>(pq) * 2 * n_pad + (j >> 5) * 64 + (j & 31);
-      const __half h = __double2half(v);
-      const __half l = __double2half(v - static_cast<double>(__half2float(h)));
-      out[o] = __half_as_ushort(h);
-      out[o + 32] = __half_as_ushort(l);
-    } else {
-      // one plane per part: [part][pq][j]
-      const int64_t o = static_cast<int64_t>(pq) * n_pad + j;
-      const __nv_bfloat16 h = __double2bfloat16(v);
-      const double r1 = v - static_cast<double>(__bfloat162float(h));
-      const __nv_bfloat16 m = __double2bfloat16(r1);
-      const __nv_bfloat16 l = __double2bfloat16(r1 - static_cast<double>(__bfloat162float(m)));
-      out[o] = __bfloat16_as_ushort(h);
-      out[part_stride + o] = __bfloat16_as_ushort(m);
-      out[2 * part_stride + o] = __bfloat16_as_ushort(l);
-    }
+    const double v = j < n_grid ? w[j] * phiT[p * n_pad + j] * phiT[q * n_pad + j] : 0.0;
+    const int64_t o = static_cast<int64_t>(pq) * n_pad + j;
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    const double r1 = v - static_cast<double>(__bfloat162float(h));
+    const __nv_bfloat16 mm = __double2bfloat16(r1);
+    const __nv_bfloat16 l = __double2bfloat16(r1 - static_cast<double>(__bfloat162float(mm)));
+    out[o] = __bfloat16_as_ushort(h);
+    out[part_stride + o] = __bfloat16_as_ushort(mm);
+    out[2 * part_stride + o] = __bfloat16_as_ushort(l);
   }
 }
 
 // One CTA per row of a step (d) operand: the row maximum sets a power-of-2 scale, then the scaled
-// row is split into fp16 hi + lo (see launch_lr_split).
-__global__ void __launch_bounds__(256) lr_split_kernel(const float* __restrict__ src, int64_t kdim,
-                                                       uint16_t* __restrict__ dst, int* __restrict__ exps) {
+// row is split exactly into fp16 hi + lo (simt_pack.cuh), one quantum per accumulation range of kd
+// blocks of 32 values (`bits` bits).  With kc = 4 the source row holds kc values per outer point
+// (k = kc * i + c) and the split row is written component-major (k' = c * (kdim / kc) + i), so that
+// a range never mixes components; with kc = 1 the order is kept.
+__global__ void __launch_bounds__(256) lr_split_kernel(const float* __restrict__ src, int64_t kdim, int kc, int kd,
+                                                       int bits, uint16_t* __restrict__ dst, int* __restrict__ exps) {
   __shared__ float red[8];
   const int64_t r = blockIdx.x;
   const float* s = src + r * kdim;
@@ -160,16 +190,46 @@ __global__ void __launch_bounds__(256) lr_split_kernel(const float* __restrict__
     e = min(max(14 - em, -100), 100);
   }
   if (threadIdx.x == 0) exps[r] = e;
+  const float scale = ldexpf(1.0f, e);  // exact power of 2 (|e| <= 100)
   uint16_t* d = dst + r * 2 * kdim;
-  for (int64_t k = threadIdx.x * 2; k < kdim; k += blockDim.x * 2) {
-    const float2 v = *reinterpret_cast<const float2*>(s + k);
-    const float a = ldexpf(v.x, e), b = ldexpf(v.y, e);
-    const __half2 h = __floats2half2_rn(a, b);
-    const float2 hf = __half22float2(h);
-    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
-    const int64_t o = (k >> 5) * 64 + (k & 31);
-    *reinterpret_cast<__half2*>(d + o) = h;
-    *reinterpret_cast<__half2*>(d + o + 32) = l;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t per_c = kdim / kc;           // outer points (kc = 4) or values (kc = 1) per component
+  // warp g handles the source points 32 kd g .. 32 kd (g + 1) - 1 (all kc components of each)
+  for (int64_t g = warp; g < per_c / (32 * kd); g += 8) {
+    float v[4][4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int64_t i = 32 * (kd * g + t) + lane;
+      v[t][0] = v[t][1] = v[t][2] = v[t][3] = 0.0f;
+      if (t >= kd) continue;
+      if (kc == 4) {
+        const float4 q4 = *reinterpret_cast<const float4*>(s + 4 * i);
+        v[t][0] = q4.x * scale;
+        v[t][1] = q4.y * scale;
+        v[t][2] = q4.z * scale;
+        v[t][3] = q4.w * scale;
+      } else {
+        v[t][0] = s[i] * scale;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (c >= kc) break;
+      float bm = 0.0f;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) bm = fmaxf(bm, fabsf(v[t][c]));
+      for (int o = 16; o > 0; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+      const int qe = exact_quantum(bm, bits);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (t >= kd) break;
+        __half h, l;
+        split_exact(v[t][c], qe, h, l);
+        const int64_t blk = (c * per_c + 32 * (kd * g + t)) >> 5;  // 32-value block of the split row
+        d[blk * 64 + lane] = __half_as_ushort(h);
+        d[blk * 64 + 32 + lane] = __half_as_ushort(l);
+      }
+    }
   }
 }
 
@@ -531,28 +591,27 @@ void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t st)
   check_finite_kernel<<<b, 256, 0, st>>>(x, n, flag);
 }
 
-void launch_rho_split(const double* phiT, const double* w, int64_t n_grid, int64_t n_pad, int n_orb, int parts,
-                      bool bf16, bool scale, const int* pp, const int* pq, unsigned int* colmax, int* colexp,
-                      void* out, cudaStream_t st) {
+void launch_rho_split(const double* phiT, const double* w, int64_t n_grid, int64_t n_pad, int n_orb, int parts, int kd,
+                      const int* pp, const int* pq, unsigned int* colmax, int* colexp, void* out, cudaStream_t st) {
   const int n_pair = n_orb * (n_orb + 1) / 2;
-  if (scale) {
+  if (parts == 2) {
     cudaMemsetAsync(colmax, 0, sizeof(unsigned int) * n_pair, st);
     dim3 g(std::min<unsigned int>(blocks_for(n_grid, 256), 64u), n_pair);
     rho_colmax_kernel<<<g, 256, 0, st>>>(phiT, w, n_grid, n_pad, n_pair, pp, pq, colmax);
+    dim3 g2(static_cast<unsigned int>(n_pad / (32 * kd)), blocks_for(n_pair, 8));
+    rho_split_f16_kernel<<<g2, 256, 0, st>>>(phiT, w, n_grid, n_pad, n_pair, pp, pq, colmax, kd, gemm_bits_b(kd),
+                                              colexp, static_cast<uint16_t*>(out));
+  } else {
+    dim3 g2(blocks_for(n_pad, 256), blocks_for(n_pair, 8));
+    rho_split_bf16_kernel<<<g2, 256, 0, st>>>(phiT, w, n_grid, n_pad, n_pair, pp, pq, colexp,
+                                               static_cast<uint16_t*>(out));
   }
-  dim3 g2(blocks_for(n_pad, 256), blocks_for(n_pair, 8));
-  if (parts == 2)
-    rho_split_kernel<2, false><<<g2, 256, 0, st>>>(phiT, w, n_grid, n_pad, n_pair, pp, pq, colmax, scale, colexp,
-                                                     static_cast<uint16_t*>(out));
-  else
-    rho_split_kernel<3, true><<<g2, 256, 0, st>>>(phiT, w, n_grid, n_pad, n_pair, pp, pq, colmax, scale, colexp,
-                                                    static_cast<uint16_t*>(out));
-  (void)bf16;
 }
 
-void launch_lr_split(const float* src, int rows, int64_t kdim, uint16_t* dst, int* exps, cudaStream_t st) {
+void launch_lr_split(const float* src, int rows, int64_t kdim, int kc, int kd, uint16_t* dst, int* exps,
+                     cudaStream_t st) {
   if (rows <= 0) return;
-  lr_split_kernel<<<rows, 256, 0, st>>>(src, kdim, dst, exps);
+  lr_split_kernel<<<rows, 256, 0, st>>>(src, kdim, kc, kd, gemm_bits_lr(kd), dst, exps);
 }
 
 void launch_rho_f64(const double* phi, const double* w, int64_t n_grid, int64_t n_pad, int n_orb, const int* pp,

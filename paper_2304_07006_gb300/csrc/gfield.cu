@@ -11,9 +11,15 @@
 //
 // One warp owns a unit of 32 outer points (one per lane, its per-point coefficients in registers)
 // and a run of inner-point blocks of 32.  For each block it evaluates the gradient in FP32 (two
-// inner points per packed FP32 instruction for up to two Jastrow centres), splits it, writes the
-// tiles of the three components (32 rows x 128 bytes, or 3 parts x 32 rows x 64 bytes) into
-// shared memory in their swizzle (conflict-free 16-byte stores) and one lane stores them with TMA.
+// inner points per packed FP32 instruction for up to two Jastrow centres; square roots and
+// reciprocals correctly rounded, so that no one-signed rounding bias enters the gradient), splits
+// it, writes the tiles of the three components (32 rows x 128 bytes, or 3 parts x 32 rows x 64
+// bytes) into shared memory in their swizzle (conflict-free 16-byte stores) and one lane stores
+// them with TMA.  The fp16 split is exact on a per-range quantum (simt_pack.cuh): for every row and
+// accumulation range of the GEMM (RB blocks of 32 inner points), hi = an integer of at most 9
+// bits times the range's quantum, lo = the fp16 remainder.  The lane first stages its RB x 32
+// FP32 values per component in its own tile rows, then splits them with the quantum of their
+// maximum; a warp then holds RB blocks of tiles, and a CTA GF_WARPS / RB warps.
 // The gradient is taken with the pair formula of jastrow_coef.cuh: per-point coefficients times
 // polynomials in b = r12 / (1 + r12) and a_jI = |r_j - R_I| / (1 + |r_j - R_I|).
 #include "jastrow_coef.cuh"
@@ -27,6 +33,8 @@ namespace {
 constexpr int GF_WARPS = 8;
 constexpr int GF_THREADS = GF_WARPS * 32;
 constexpr int GF_TILE = 32 * 64;   // one part's share of a component tile: 32 rows of 64 bytes
+// fp16: bits of the integer hi part of G on its range's quantum (|k| <= 2^9, exact in fp16)
+constexpr int GF_EXACT_BITS = GEMM_BITS_A;
 
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, uint32_t src, int c0, int c1, int c2) {
   asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
@@ -42,16 +50,18 @@ __device__ __forceinline__ void bulk_wait_read_all() {
 // Waits until every committed bulk store has completed.
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-template <int PARTS, int NNUC>
+template <int PARTS, int NNUC, int RB>
 __global__ void __launch_bounds__(GF_THREADS)
     gfield_kernel(const __grid_constant__ CUtensorMap tm_g, const GfieldArgs args) {
   constexpr bool BF16 = PARTS == 3;
   constexpr int JS = NNUC <= 4 ? 12 : 16;  // floats per inner point in the table (launch_jtab)
-  constexpr int WARP_BYTES = 3 * PARTS * GF_TILE;
+  constexpr int BLOCK_BYTES = 3 * PARTS * GF_TILE;  // the three component tiles of one block
+  constexpr int WARP_BYTES = RB * BLOCK_BYTES;       // RB blocks: one exact range of the GEMM
+  constexpr int WARPS = GF_WARPS / RB;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t unit = static_cast<int64_t>(blockIdx.x) * GF_WARPS + warp;
+  const int64_t unit = static_cast<int64_t>(blockIdx.x) * WARPS + warp;
   if (unit >= static_cast<int64_t>(args.n_tiles) * args.n_seg) return;  // whole warp; no block barrier below
   const int tile = static_cast<int>(unit / args.n_seg), seg = static_cast<int>(unit % args.n_seg);
   const int kb0 = seg * args.kb_per_seg, kb1 = min(args.n_kb, kb0 + args.kb_per_seg);
@@ -80,8 +90,13 @@ __global__ void __launch_bounds__(GF_THREADS)
     ZL = pk2(zl, zl);
   }
   const int row0 = tile * 32;
+  float gmax[3] = {0.0f, 0.0f, 0.0f};  // fp16: largest |G| of the range per component
 
-  for (int kb = kb0; kb < kb1; ++kb) {
+  for (int kr = kb0; kr < kb1; kr += RB) {
+#pragma unroll 1
+  for (int rb = 0; rb < RB; ++rb) {
+    const int kb = kr + rb;
+    const uint32_t bbuf = buf + rb * BLOCK_BYTES;
     // 16 records of two inner points each (the pair-interleaved table written by launch_jtab)
     const float* blk = args.jtab + static_cast<int64_t>(kb) * VF_BK * JS;
 #pragma unroll 1
@@ -103,13 +118,13 @@ __global__ void __launch_bounds__(GF_THREADS)
           float r2a, r2b;
           up2(r2, r2a, r2b);
           // unit vector of r1 - r2 taken as zero below 1e-14 bohr (coincident points)
-          const float ria = r2a > 1e-28f ? rsqrt_approx(r2a) : 0.0f;
-          const float rib = r2b > 1e-28f ? rsqrt_approx(r2b) : 0.0f;
+          const float ria = r2a > 1e-28f ? __frsqrt_rn(r2a) : 0.0f;
+          const float rib = r2b > 1e-28f ? __frsqrt_rn(r2b) : 0.0f;
           const f32x2 rinv = pk2(ria, rib);
           const f32x2 rr = mul2(r2, rinv);
           float ra, rb;
           up2(rr, ra, rb);
-          const f32x2 q = pk2(rcp_approx(1.0f + ra), rcp_approx(1.0f + rb));
+          const f32x2 q = pk2(__frcp_rn(1.0f + ra), __frcp_rn(1.0f + rb));
           const f32x2 b = mul2(rr, q);
           const f32x2 sfac = mul2(mul2(q, q), rinv);
           f32x2 ex = fma2(b, fma2(b, PC[9], PC[6]), PC[3]);
@@ -145,9 +160,9 @@ __global__ void __launch_bounds__(GF_THREADS)
             const float dy = (pc[1] - yh) + (yl - ylo);
             const float dz = (pc[2] - zh) + (zl - zlo);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float rinv = r2 > 1e-28f ? rsqrt_approx(r2) : 0.0f;
+            const float rinv = r2 > 1e-28f ? __frsqrt_rn(r2) : 0.0f;
             const float rr = r2 * rinv;
-            const float q = rcp_approx(1.0f + rr);
+            const float q = __frcp_rn(1.0f + rr);
             const float b = rr * q;
             const float sfac = q * q * rinv;
             float ex = fmaf(b, fmaf(b, pc[9], pc[6]), pc[3]);
@@ -173,22 +188,67 @@ __global__ void __launch_bounds__(GF_THREADS)
           }
         }
       }
-      // the previous block's tiles must have been read by its TMA stores before they are overwritten
-      if (c == 0 && kb > kb0) {
+      // the previous range's tiles must have been read by their TMA stores before they are overwritten
+      if (c == 0 && rb == 0 && kr > kb0) {
         if (lane == 0) bulk_wait_read_all();
         __syncwarp();
       }
+      if constexpr (PARTS == 2) {
+        // FP32 staging in the lane's own 128-byte rows of the block's component tiles (16-byte
+        // chunks b, b + 1 with b = 0, 4, 2, 6 for c = 0..3, so that the split below rewrites, for
+        // each half of the block, exactly the chunks it has read), and the range maxima
+        const int b = (c & 1) * 4 + (c >> 1) * 2;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) gmax[x] = fmaxf(gmax[x], fabsf(gv[x][k]));
+          const uint32_t row = bbuf + x * 2 * GF_TILE;
+          st_shared_v4(row + sw128_offset(lane, b), __float_as_uint(gv[x][0]), __float_as_uint(gv[x][1]),
+                       __float_as_uint(gv[x][2]), __float_as_uint(gv[x][3]));
+          st_shared_v4(row + sw128_offset(lane, b + 1), __float_as_uint(gv[x][4]), __float_as_uint(gv[x][5]),
+                       __float_as_uint(gv[x][6]), __float_as_uint(gv[x][7]));
+        }
+      } else {
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          uint32_t w[4][PARTS];
+#pragma unroll
+          for (int h = 0; h < 4; ++h) split_pair<BF16>(gv[x][2 * h], gv[x][2 * h + 1], w[h]);
+#pragma unroll
+          for (int p = 0; p < PARTS; ++p)
+            st_shared_v4(bbuf + (x * PARTS + p) * GF_TILE + sw64_offset(lane, c), w[0][p], w[1][p], w[2][p], w[3][p]);
+        }
+      }
+    }
+  }
+    if constexpr (PARTS == 2) {
+      // exact split of the lane's RB x 32 values per component on the range's quantum: hi of
+      // points 8c .. 8c + 7 of a block goes to chunk c, lo to chunk 4 + c (component tile x of 32
+      // rows x 128 bytes, the layout the GEMM loads)
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
-        uint32_t w[4][PARTS];
+        const int q = exact_quantum(gmax[x], GF_EXACT_BITS);
+        gmax[x] = 0.0f;
 #pragma unroll
-        for (int h = 0; h < 4; ++h) split_pair<BF16>(gv[x][2 * h], gv[x][2 * h + 1], w[h]);
+        for (int rb = 0; rb < RB; ++rb) {
+          const uint32_t row = buf + rb * BLOCK_BYTES + x * 2 * GF_TILE;
 #pragma unroll
-        for (int p = 0; p < PARTS; ++p) {
-          // fp16: component tile x of 32 rows x 128 bytes, part p in chunks 4p .. 4p + 3
-          const uint32_t off = PARTS == 2 ? x * 2 * GF_TILE + sw128_offset(lane, p * 4 + c)
-                                          : (x * PARTS + p) * GF_TILE + sw64_offset(lane, c);
-          st_shared_v4(buf + off, w[0][p], w[1][p], w[2][p], w[3][p]);
+          for (int h = 0; h < 2; ++h) {
+            // sub-blocks c = 2h (staged in chunks 2h, 2h + 1) and 2h + 1 (chunks 4 + 2h, 5 + 2h)
+            uint32_t f[16];
+            ld_shared_v4(row + sw128_offset(lane, 2 * h), f[0], f[1], f[2], f[3]);
+            ld_shared_v4(row + sw128_offset(lane, 2 * h + 1), f[4], f[5], f[6], f[7]);
+            ld_shared_v4(row + sw128_offset(lane, 4 + 2 * h), f[8], f[9], f[10], f[11]);
+            ld_shared_v4(row + sw128_offset(lane, 5 + 2 * h), f[12], f[13], f[14], f[15]);
+            uint32_t w[8][2];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              split_pair_exact(__uint_as_float(f[2 * k]), __uint_as_float(f[2 * k + 1]), q, w[k]);
+            st_shared_v4(row + sw128_offset(lane, 2 * h), w[0][0], w[1][0], w[2][0], w[3][0]);
+            st_shared_v4(row + sw128_offset(lane, 2 * h + 1), w[4][0], w[5][0], w[6][0], w[7][0]);
+            st_shared_v4(row + sw128_offset(lane, 4 + 2 * h), w[0][1], w[1][1], w[2][1], w[3][1]);
+            st_shared_v4(row + sw128_offset(lane, 5 + 2 * h), w[4][1], w[5][1], w[6][1], w[7][1]);
+          }
         }
       }
     }
@@ -196,13 +256,19 @@ __global__ void __launch_bounds__(GF_THREADS)
     __syncwarp();
     if (lane == 0) {
 #pragma unroll
-      for (int x = 0; x < 3; ++x) {
-        if (PARTS == 2) {
-          tma_store_3d(&tm_g, buf + x * 2 * GF_TILE, kb * 2 * VF_BK, static_cast<int>(x * args.gcp) + row0, 0);
-        } else {
+      for (int rb = 0; rb < RB; ++rb) {
+        const int kb = kr + rb;
+        const uint32_t bbuf = buf + rb * BLOCK_BYTES;
 #pragma unroll
-          for (int p = 0; p < PARTS; ++p)
-            tma_store_3d(&tm_g, buf + (x * PARTS + p) * GF_TILE, kb * VF_BK, static_cast<int>(x * args.gcp) + row0, p);
+        for (int x = 0; x < 3; ++x) {
+          if (PARTS == 2) {
+            tma_store_3d(&tm_g, bbuf + x * 2 * GF_TILE, kb * 2 * VF_BK, static_cast<int>(x * args.gcp) + row0, 0);
+          } else {
+#pragma unroll
+            for (int p = 0; p < PARTS; ++p)
+              tma_store_3d(&tm_g, bbuf + (x * PARTS + p) * GF_TILE, kb * VF_BK, static_cast<int>(x * args.gcp) + row0,
+                           p);
+          }
         }
       }
       bulk_commit();
@@ -212,14 +278,22 @@ __global__ void __launch_bounds__(GF_THREADS)
   __syncwarp();
 }
 
-template <int PARTS, int NNUC>
-void launch_t(const CUtensorMap* tm, const GfieldArgs& a, cudaStream_t st) {
-  auto kern = gfield_kernel<PARTS, NNUC>;
-  constexpr int smem = GF_WARPS * 3 * PARTS * GF_TILE + 1024;
+template <int PARTS, int NNUC, int RB>
+void launch_rb(const CUtensorMap* tm, const GfieldArgs& a, cudaStream_t st) {
+  auto kern = gfield_kernel<PARTS, NNUC, RB>;
+  constexpr int warps = GF_WARPS / RB;
+  constexpr int smem = GF_WARPS * 3 * PARTS * GF_TILE + 1024;  // warps x RB blocks of three tiles
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const int64_t units = static_cast<int64_t>(a.n_tiles) * a.n_seg;
-  const unsigned blocks = static_cast<unsigned>((units + GF_WARPS - 1) / GF_WARPS);
-  kern<<<blocks, GF_THREADS, smem, st>>>(*tm, a);
+  const unsigned blocks = static_cast<unsigned>((units + warps - 1) / warps);
+  kern<<<blocks, warps * 32, smem, st>>>(*tm, a);
+}
+template <int PARTS, int NNUC>
+void launch_t(const CUtensorMap* tm, const GfieldArgs& a, cudaStream_t st) {
+  if (PARTS == 2 && a.range_blocks == 2)
+    launch_rb<PARTS, NNUC, 2>(tm, a, st);
+  else
+    launch_rb<PARTS, NNUC, 1>(tm, a, st);
 }
 
 }  // namespace

@@ -8,12 +8,16 @@
 // device (with that device current); that first call should therefore happen before any stream
 // capture.  Every call reuses the same array and it keeps the last call's contents, so calls
 // that overlap on the GPU (other streams, other threads, other contexts of this process on the
-// same device) race with each other and must be serialised by the caller.
+// same device) race with each other and must be serialised by the caller.  The tensor-core GEMM
+// runs with FP32 running sums only (no FP64 flush: the array has no room for the FP64 tile sums),
+// so over long inner sums its rounding differs slightly from xtc_vfield's.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "../../include/xtc.h"
 #include "xtc_internal.cuh"
@@ -27,7 +31,37 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+// Device address of g_scratch per device, looked up once (under the mutex) and then read lock-free.
+std::atomic<void*> g_scratch_addr[kMaxDevices];
+std::mutex g_scratch_mutex;
+
+void* scratch_address(int device) {
+  void* p = g_scratch_addr[device].load(std::memory_order_acquire);
+  if (p) return p;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  p = g_scratch_addr[device].load(std::memory_order_relaxed);
+  if (p) return p;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  g_scratch_addr[device].store(p, std::memory_order_release);
+  return p;
+}
+
+// Restores the calling thread's current device when the call returns.
+struct DeviceGuard {
+  int saved = -1;
+  DeviceGuard() {
+    if (cudaGetDevice(&saved) != cudaSuccess) {
+      cudaGetLastError();
+      saved = -1;
+    }
+  }
+  ~DeviceGuard() {
+    if (saved >= 0) cudaSetDevice(saved);
+  }
+};
 
 __global__ void pair_table_kernel(int n_orb, int* pp, int* pq) {
   const int p = blockIdx.x;
@@ -38,14 +72,16 @@ __global__ void pair_table_kernel(int n_orb, int* pp, int* pq) {
   }
 }
 
-bool on_device(const void* p) {
+// True for managed memory and for device memory of `device` (memory of another GPU is refused:
+// the kernels on `device` would read it through a peer mapping, or fault without one).
+bool on_device(const void* p, int device) {
   if (!p) return false;
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == device);
 }
 
 // Carves 256-byte aligned pieces out of the scratch array.
@@ -73,27 +109,28 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
   const bool f64 = cv.precision == XTC_PREC_FP64;
   if (!f64 && !vfield_tc_supported(cv.n_nuc))
     return xtc_internal_fail(ctx, XTC_ERR_UNSUPPORTED, "noalloc: the tensor-core path supports 1..8 nuclei");
-  if (cudaSetDevice(cv.device) != cudaSuccess || cv.device < 0 || cv.device >= kMaxDevices)
+  if (cv.device < 0 || cv.device >= kMaxDevices)
+    return xtc_internal_fail(ctx, XTC_ERR_ARG, "noalloc: device ordinal out of range");
+  DeviceGuard restore_device;
+  if (cudaSetDevice(cv.device) != cudaSuccess) {
+    cudaGetLastError();
     return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: cudaSetDevice failed");
-  if (!on_device(grid_xyz) || !on_device(weights) || !on_device(phi) || !on_device(V))
-    return xtc_internal_fail(ctx, XTC_ERR_ARG, "noalloc: inputs and output must be device pointers");
+  }
+  if (!on_device(grid_xyz, cv.device) || !on_device(weights, cv.device) || !on_device(phi, cv.device) ||
+      !on_device(V, cv.device))
+    return xtc_internal_fail(ctx, XTC_ERR_ARG, "noalloc: inputs and output must be device pointers on the context's device");
 
   // ---- the scratch array's device address, once per device
-  if (!g_scratch_addr[cv.device]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: cudaGetSymbolAddress of the scratch array failed");
-    }
-    g_scratch_addr[cv.device] = p;
-  }
+  void* scratch = scratch_address(cv.device);
+  if (!scratch)
+    return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: cudaGetSymbolAddress of the scratch array failed");
 
   // ---- plan and carve (sizes checked before any device work)
   const int N = n_orb, NP = N * (N + 1) / 2, n_nuc = cv.n_nuc;
   const int64_t NGp = round_up(n_grid, 128);
   const int64_t n_outer = outer_end - outer_begin;
   const int parts = f64 ? 0 : (cv.precision == XTC_PREC_FP16X2 ? 2 : 3);
+  const int kd_b = cv.vf_kd >= 2 ? 2 : 1;  // exact range of the fp16 step (b) engine
   // bytes the layout below carves for a chunk of gc outer points (same order and rounding)
   auto need = [&](int64_t gc) {
     Carver c{nullptr};
@@ -123,7 +160,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
              need(128) / 1048576.0, XTC_NOALLOC_SCRATCH_MIB);
     return xtc_internal_fail(ctx, XTC_ERR_ARG, msg);
   }
-  Carver cz{static_cast<unsigned char*>(g_scratch_addr[cv.device])};
+  Carver cz{static_cast<unsigned char*>(scratch)};
   int* err = cz.take<int>(4);
   int* pair_p = cz.take<int>(NP);
   int* pair_q = cz.take<int>(NP);
@@ -158,8 +195,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     void* G = cz.take<uint16_t>(static_cast<size_t>(parts) * 3 * gc * NGp);
     launch_transpose_phi(phi, n_grid, NGp, N, phiT, st);
     launch_jtab(grid_xyz, n_grid, NGp, cv.jp_dev, n_nuc, jtab_stride(n_nuc), jtab, st);
-    launch_rho_split(phiT, weights, n_grid, NGp, N, parts, parts == 3, parts == 2, pair_p, pair_q, colmax, colexp,
-                     rho, st);
+    launch_rho_split(phiT, weights, n_grid, NGp, N, parts, kd_b, pair_p, pair_q, colmax, colexp, rho, st);
     // rho^T (box rows vf_bn) and the gradient table [part][x * gc + il][j] (boxes 32 x 32
     // for the step (a) stores and 32 x 128 for the step (b) loads)
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(cv.encode_tiled);
@@ -206,6 +242,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
       g.n_seg = (n_kb + g.kb_per_seg - 1) / g.kb_per_seg;
       g.n_nuc = n_nuc;
       g.g_scale = std::ldexp(1.0f, sg);
+      g.range_blocks = kd_b;
       launch_gfield(&tm_gs, g, parts, st);
       VfieldArgs a{};
       a.colexp = colexp;
@@ -219,7 +256,8 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
       a.n_pair = NP;
       a.n_kb = n_kb;
       a.kb_per_split = n_kb;
-      a.kd = std::min(cv.vf_kd, parts == 2 ? 4 : 2);
+      a.kd = parts == 2 ? kd_b : std::min(cv.vf_kd, 2);
+      a.xper = 64;
       a.unscale_g = std::ldexp(1.0f, -sg);
       a.err = err;
       launch_vfield_tc(&tm_gl, &tm, a, parts, 1, st);

@@ -45,40 +45,47 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// The same with acquire semantics at cluster scope (for phases completed by arrivals of other CTAs
-// of the cluster).
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+// Bounded wait.  Returns false when the CTA has aborted or this wait timed out after limit_ns
+// (then it sets the abort flag and the device error word).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                          int code, unsigned long long limit_ns = TIMEOUT_NS) {
+  auto test = [&] { return mbar_try_wait(bar, parity); };
+  if (test()) return true;
+  const unsigned long long t0 = global_timer_ns();
+  uint32_t it = 0;
+  while (!test()) {
+    if ((++it & 63u) == 0) {
+      if (*abort_flag) return false;
+      if (global_timer_ns() - t0 > limit_ns) {
+        *abort_flag = 1;
+        atomicExch(err, code);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+// The same with a non-suspending test in a tight loop: for the single threads that issue MMAs,
+// where the wake-up latency of a suspended wait sits on the critical path.
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
 }
-// Address of the shared-memory object at `p` (this CTA) in the CTA of the cluster with rank `rank`.
-__device__ __forceinline__ uint32_t mapa_shared(const void* p, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
-  return r;
-}
-// Arrive (release at cluster scope) on an mbarrier given by its shared::cluster address.
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
-}
-// Bounded wait.  Returns false when the CTA has aborted or this wait timed out after limit_ns
-// (then it sets the abort flag and the device error word).  CLUSTER: acquire at cluster scope.
-template <bool CLUSTER = false>
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+__device__ __forceinline__ bool mbar_spin(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
                                           int code, unsigned long long limit_ns = TIMEOUT_NS) {
-  auto test = [&] { return CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity); };
-  if (test()) return true;
+  if (mbar_test(bar, parity)) return true;
   const unsigned long long t0 = global_timer_ns();
   uint32_t it = 0;
-  while (!test()) {
-    if ((++it & 63u) == 0) {
+  while (!mbar_test(bar, parity)) {
+    if ((++it & 255u) == 0) {
       if (*abort_flag) return false;
       if (global_timer_ns() - t0 > limit_ns) {
         *abort_flag = 1;

@@ -3,96 +3,55 @@
 //     V_x[i][pq] = sum_j G_x(i, j) rho^T[pq][j],   G_x(i, j) = d/dx_i u(r_i, r_j),
 //     rho^T[pq][j] = w_j phi_p(j) phi_q(j),
 // as a split-precision GEMM over the inner points j: A = G (written by gfield.cu, rows x*gcp + il),
-// B = rho^T (written by the rho split kernel), both split into fp16 (2 parts) or bf16 (3 parts).
+// B = rho^T (written by the rho split kernel), K-major, all operands loaded by TMA.  The same fp16
+// engine runs step (d) of Appendix B (MODE 1): M += L^T R with A = the split rows L[pq]
+// (rho, V) and B = the split rows R[rs] (A, B) of a chunk, K = 4 x chunk points, each row carrying
+// its own power-of-2 scale; its tile sums are added into M[pq][rs] by assemble_finalize_kernel.
 //
-// Tile: 128 A rows per CTA (128 outer points of one component) x BN orbital pairs (192 with 2
-// parts, 160 with 3), 32 inner points per pipeline stage, K-major, all operands loaded by TMA.
-// With 2 parts both parts of a row share one 128-byte row (128-byte swizzle; one TMA box per
-// operand and stage); with 3 parts every part is a plane of 64-byte rows (64-byte swizzle).
+// fp16 x2 engine (xgemm_kernel).  Both operands are split exactly on per-range quanta (simt_pack.cuh):
+// per row and accumulation range of kd stages (kd * 32 K values), hi = an integer times the row's
+// power-of-2 quantum for that range (from the range's largest magnitude), lo = the fp16 remainder,
+// with bit widths such that the range's hi x hi products sum within 2^24 units.
+// The tensor core's FP32 accumulator truncates toward zero at every MMA, which biases a long sum
+// by a relative ~2^-24 per MMA, always toward zero; the hi x hi sums of a range are exact, so they
+// go, one range at a time, into an accumulator E, which the drain warps add into FP32 running sums
+// (round to nearest) after every range.  The cross products hi x lo and lo x hi (about 2^-9 of the
+// total, signs that follow the rounding remainders rather than the data) go into a second
+// accumulator X, drained every `xper` stages; their truncation is 2^-9 smaller and does not
+// accumulate one-sided.  lo x lo is dropped (it matters only for values far below their range's
+// maximum in both operands; measured on the whole N=120 workload it moves no output by more than
+// 1e-8 Eh).
 //
-// Every tcgen05.commit stalls the tensor pipe for a few hundred cycles (measured: a group of g
-// back-to-back MMAs plus its commit takes about g x 96 + 300 cycles at N = 192), so the kernel
-// commits once per accumulation range: that single arrival releases the range's stage slots to the
-// TMA producer (which counts finished ranges in order) and hands the accumulator to the drains.
-//
-// Warp roles:
-//   * warp 0 (one lane): TMA loads of the A and B tiles;
-//   * warps 1 and 10 (one lane each): MMA issuers of the even and the odd ranges;
-//   * warps 2..9: every `kd` stages they load the finished accumulator (tcgen05.ld) and add it into
-//     an FP32 running sum held in their registers (two warps per TMEM lane quarter, BN/2 columns
-//     each) while the MMA fills the other accumulator; at the end they store the sum, unscaled, as
-//     V[pq][x][i].
-// The tensor-core accumulator truncates toward zero at each MMA, which biases a long inner sum.
-// Each range is short (default one stage), its MMAs issue the small cross products of all its
-// stages first so that only the hi x hi products meet a large accumulator, and the ranges are
-// summed with round-to-nearest FP32 adds.  Rounding of that FP32 sum grows with the number of
-// ranges, so every `flush` ranges the drains add their FP32 partial sums into an FP64 accumulator
-// in HBM, private to the CTA and column-major in its tile (each element belongs to one thread:
-// plain read-modify-write, coalesced over the 32 rows of a warp); the final sum is written as V.
+// Tile 128 A rows x 128 columns, 32 K values per stage, both parts of a row of a block in one
+// 128-byte row (128-byte swizzle; one TMA box per operand and stage), 7 stages of 32 KB.  Measured
+// on GB300: one thread issues a 128 x 128 x 16 MMA every ~50 cycles (the pipe takes 64), an MMA
+// and its commit round-trip in ~360 cycles, and a range's round trip (its MMAs complete, the
+// commit arrives, the drains read E, E is handed back) takes on the order of a thousand cycles.
+// So ranges span two stages (12 MMAs), and two issuers alternate ranges, each with its own
+// accumulator pair (TMEM: E0, X0, E1, X1 = 4 x 128 of 512 columns).  Warp roles:
+//   * warp 0 (one lane): TMA loads; a range's slots are reloaded once its commit has arrived;
+//   * warps 1 and 2 (one lane each): the MMAs of the even / odd ranges, one commit per range;
+//   * warps 3..18: after every range, drains of E_k, and every `xper` stages of X_k, into FP32
+//     running sums held in registers (four warps per TMEM lane quarter, 32 columns each).  The
+//     sums move into an FP64 accumulator in HBM, private to the CTA and column-major in its tile,
+//     one column per range in turn (each column at least once per `flush` ranges; each element
+//     belongs to one thread); vfield_finalize_kernel writes V from it (MODE 0).
 // Tiles are ordered in groups of GM row tiles so that the CTAs resident at one time share their A
 // and B panels in L2.
 //
-// The same engine runs step (d) for the fp16 x2 precision (MODE 1): M += L^T R with A = the split
-// rows L[pq] (rho, V) and B = the split rows R[rs] (A, B) of a chunk, K = 4 x chunk points, each
-// row carrying its own power-of-2 scale; its tile-private FP64 sums are then added into M[pq][rs],
-// unscaled, by assemble_finalize_kernel.
+// bf16 x3 engine (vfield_bf16_kernel, step (b) of the bf16 precision): three bf16 planes per
+// operand (64-byte swizzle), six products (i + j <= 2) into one of two TMEM accumulators per range
+// of `kd` stages, small cross products first, drained into FP32 running sums after every range.
+// Its accumulation is not exact: the truncation bias is only kept small by the short ranges.
 #include "ptx_sm100.cuh"
 #include "xtc_internal.cuh"
 
 namespace xtc {
 namespace {
 
-constexpr int DRAIN_WARPS = 8;       // two per TMEM lane quarter, BN/2 columns each
-constexpr int MMA_WARPS = 2;         // issuers of the even / odd ranges (warps 1 and 2 + DRAIN_WARPS)
-constexpr int THREADS = (1 + MMA_WARPS + DRAIN_WARPS) * 32;
-constexpr int A_TILE = VF_BM * 64;   // bytes per part of an A tile (128 rows of 64 B)
+constexpr int DRAIN_WARPS = 8;       // two per TMEM lane quarter, half of the columns each
 constexpr int GM = 8;                // row tiles per group (L2 reuse)
-
-constexpr int NRB = 8;               // range barriers (range r uses r % NRB)
-
-template <int PARTS>
-struct VfCfg {
-  static constexpr int BN = vf_bn(PARTS);   // columns of the tile (TMEM accumulator width)
-  static constexpr int B_TILE = BN * 64;    // bytes per part of a B tile
-  static constexpr int HC = BN / 2;         // running-sum columns per drain thread
-  static constexpr int NPROD = PARTS == 2 ? 3 : 6;
-  static constexpr int A_BYTES = PARTS * A_TILE;
-  static constexpr int B_BYTES = PARTS * B_TILE;
-  static constexpr int STAGE_BYTES = ((A_BYTES + B_BYTES + 1023) / 1024) * 1024;
-  static constexpr int STAGES = (220 * 1024) / STAGE_BYTES < 8 ? (220 * 1024) / STAGE_BYTES : 8;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
-};
-static_assert(VfCfg<2>::SMEM <= 232448 && VfCfg<3>::SMEM <= 232448, "shared memory per CTA");
-static_assert(VfCfg<2>::STAGES >= 4 && VfCfg<3>::STAGES >= 4, "pipeline depth");
-// a wait for range r must not alias range r + NRB: the producer waits for the range of stage
-// k - STAGES before loading stage k, and range r + NRB starts past stage k when NRB > STAGES
-static_assert(NRB > VfCfg<2>::STAGES && NRB > VfCfg<3>::STAGES, "range barriers");
-static_assert(2 * vf_bn(2) <= 512 && 2 * vf_bn(3) <= 512, "two accumulators in 512 TMEM columns");
-static_assert(vf_bn(2) % 32 == 0 && vf_bn(3) % 32 == 0, "drain halves of whole 16-column chunks");
-
-// Shared-memory descriptor of part p, K step ks (16 values) of an operand tile at `base`.
-template <int PARTS>
-__device__ __forceinline__ uint64_t op_desc(uint32_t base, int tile_bytes, int p, int ks) {
-  if (PARTS == 2) return sdesc_kmajor_sw128(base + p * 64 + ks * 32);
-  return sdesc_kmajor_sw64(base + p * tile_bytes + ks * 32);
-}
-
-// (A part, B part) of each split product in issue order: the small cross products first and
-// hi x hi last, so that the truncations of the early MMAs act on a small accumulator.
-template <int PARTS>
-__device__ __forceinline__ void prod_parts(int p, int& pa, int& pb) {
-  if (PARTS == 2) {
-    constexpr int a[3] = {0, 1, 0};
-    constexpr int b[3] = {1, 0, 0};
-    pa = a[p];
-    pb = b[p];
-  } else {
-    constexpr int a[6] = {1, 0, 2, 0, 1, 0};
-    constexpr int b[6] = {1, 2, 0, 1, 0, 0};
-    pa = a[p];
-    pb = b[p];
-  }
-}
+constexpr int NRB = 8;               // per-stage / per-range barriers (stage or range r uses r % NRB)
 
 __device__ __forceinline__ void red_add_f64(double* p, double v) {
   asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
@@ -109,37 +68,295 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, uint32_t (&r)[16]) {
       : "memory");
 }
 
-template <int PARTS, int MODE>
-__global__ void __launch_bounds__(THREADS, 1)
-    vfield_tc_kernel(const __grid_constant__ CUtensorMap tm_g, const __grid_constant__ CUtensorMap tm_rho,
-                     const VfieldArgs args) {
-  using Cfg = VfCfg<PARTS>;
-  constexpr bool BF16 = PARTS == 3;
-  constexpr int BN = Cfg::BN, HC = Cfg::HC, STAGES = Cfg::STAGES;
+// Tile coordinates of CTA L in the grouped order (GM row tiles x every column tile, row fastest).
+struct TileXY {
+  int m_tile, n_tile;
+};
+__device__ __forceinline__ TileXY grouped_tile(int L, int m_tiles, int n_tiles) {
+  const int group = L / (GM * n_tiles);
+  const int first_m = group * GM;
+  const int gm = min(GM, m_tiles - first_m);
+  const int rem = L - group * GM * n_tiles;
+  return {first_m + rem % gm, rem / gm};
+}
 
+// =================================================================== fp16 x2 engine
+constexpr int XB_BN = 128;                        // tile columns (TMEM accumulator width)
+constexpr int XB_DRAIN_WARPS = 16;                // four per TMEM lane quarter, a quarter of the columns each
+constexpr int XB_HC = XB_BN / 4;                  // running-sum columns per drain thread
+constexpr int XB_A_BYTES = VF_BM * 128;           // 128 rows of 128 bytes (hi and lo of 32 values)
+constexpr int XB_B_BYTES = XB_BN * 128;
+constexpr int XB_STAGE = XB_A_BYTES + XB_B_BYTES; // 32 KB, a multiple of the 1024-byte swizzle atom
+constexpr int XB_STAGES = 7;
+constexpr int XB_WARP_I0 = 1, XB_WARP_I1 = 2;      // issuers of the even / odd ranges; drains 3..18
+constexpr int XB_THREADS = (3 + XB_DRAIN_WARPS) * 32;  // TMA warp, two MMA warps, drains
+constexpr int XB_SMEM = XB_STAGES * XB_STAGE + 1024 + 256;  // + alignment slack, barriers
+static_assert(XB_BN == vf_bn(2), "tile width of the fp16 engine");
+static_assert(4 * XB_BN <= 512, "E0, X0, E1, X1 in 512 TMEM columns");
+static_assert(XB_HC == 32, "drain columns per thread (one 32-column load)");
+static_assert(XB_SMEM <= 232448, "shared memory per CTA");
+// a wait for range r must not alias range r + NRB: the producer waits for the range of stage
+// k - XB_STAGES before loading stage k, and range r + NRB starts past stage k
+static_assert(NRB > XB_STAGES, "range barriers");
+static_assert((XB_STAGES + NRB + 5) * 8 + 8 <= 256, "barrier area");
+
+// Shared-memory descriptor of a K-major operand in the 128-byte swizzle, for a shared address
+// below 2^18: the constant fields plus the address in 16-byte units (a plain add per stage and
+// K step, no re-encoding in the issue loop).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) { return sdesc_kmajor_sw128(0) + (saddr >> 4); }
+
+template <int MODE>
+__global__ void __launch_bounds__(XB_THREADS, 1)
+    xgemm_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
+                 const VfieldArgs args) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
-  uint64_t* tma_full = bars;                  // [STAGES] the stage's loads landed
-  uint64_t* rdone = bars + STAGES;            // [NRB] the MMAs of range r (r % NRB) completed
-  uint64_t* d_free = bars + STAGES + NRB;     // [2] the drains released accumulator b
-  uint64_t* fin_bar = bars + STAGES + NRB + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + STAGES + NRB + 3);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + XB_STAGES * XB_STAGE);
+  uint64_t* tma_full = bars;                  // [XB_STAGES] the stage's loads landed
+  uint64_t* rdone = bars + XB_STAGES;         // [NRB] every MMA of range r (r % NRB) completed
+  uint64_t* e_free = rdone + NRB;             // [2] the drains released E_k (issuer k)
+  uint64_t* x_free = e_free + 2;              // [2] the drains released X_k
+  uint64_t* fin_bar = x_free + 2;             // every MMA of both issuers completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin_bar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // grouped tile order: GM row tiles x every column tile, row tile fastest
   const int m_tiles = MODE == 0 ? 3 * args.mt_per_x : (args.rows_a + VF_BM - 1) / VF_BM;
-  const int L = blockIdx.x;
-  const int group = L / (GM * args.n_tiles);
-  const int first_m = group * GM;
-  const int gm = min(GM, m_tiles - first_m);
-  const int rem = L - group * GM * args.n_tiles;
-  const int m_tile = first_m + rem % gm, n_tile = rem / gm;
+  const TileXY t = grouped_tile(blockIdx.x, m_tiles, args.n_tiles);
   // mode 0: rows x * gcp + outer point of component x; mode 1: rows pq
-  const int x = MODE == 0 ? m_tile / args.mt_per_x : 0;
-  const int ib = MODE == 0 ? (m_tile - x * args.mt_per_x) * VF_BM : m_tile * VF_BM;
+  const int x = MODE == 0 ? t.m_tile / args.mt_per_x : 0;
+  const int ib = MODE == 0 ? (t.m_tile - x * args.mt_per_x) * VF_BM : t.m_tile * VF_BM;
   const int row0 = MODE == 0 ? static_cast<int>(x * args.gcp) + ib : ib;
+  const int split = blockIdx.y;
+  const int kb0 = split * args.kb_per_split;
+  const int kb1 = min(args.n_kb, kb0 + args.kb_per_split);
+  const int n_it = kb1 - kb0;
+  const int kd = args.kd;                                  // stages per exact range (1, 2 or 4)
+  const int n_ranges = (n_it + kd - 1) / kd;
+  const int xr = max(1, args.xper / (2 * kd));             // ranges of one issuer per X drain
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < XB_STAGES; ++s) mbar_init(&tma_full[s], 1);
+    for (int r = 0; r < NRB; ++r) mbar_init(&rdone[r], 1);
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&e_free[k], XB_DRAIN_WARPS);
+      mbar_init(&x_free[k], XB_DRAIN_WARPS);
+    }
+    mbar_init(fin_bar, 2);
+    *abort_flag = 0;
+    fence_mbar_init();
+    tma_prefetch_desc(&tm_a);
+    tma_prefetch_desc(&tm_b);
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t smem_base = smem_u32(smem);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- TMA producer
+      int seen = 0;  // ranges known to have completed (their slots are free again)
+      int issued = 0;
+      for (int it = 0; it < n_it; ++it) {
+        const int s = it % XB_STAGES;
+        if (it >= XB_STAGES) {
+          const int need = (it - XB_STAGES) / kd;  // range holding the slot's previous stage
+          bool ok = true;
+          for (; seen <= need && ok; ++seen)
+            ok = mbar_wait(&rdone[seen % NRB], (seen / NRB) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF);
+          if (!ok) break;
+        }
+        mbar_arrive_expect_tx(&tma_full[s], XB_STAGE);
+        uint8_t* st = smem + s * XB_STAGE;
+        tma_load_3d(st, &tm_a, &tma_full[s], (kb0 + it) * 2 * VF_BK, row0, 0);
+        tma_load_3d(st + XB_A_BYTES, &tm_b, &tma_full[s], (kb0 + it) * 2 * VF_BK, t.n_tile * XB_BN, 0);
+        issued = it + 1;
+      }
+      // the copies still in flight land before the CTA may exit
+      int zero = 0;
+      for (int it = max(0, issued - XB_STAGES); it < issued; ++it)
+        mbar_wait(&tma_full[it % XB_STAGES], (it / XB_STAGES) & 1, reinterpret_cast<volatile int*>(&zero),
+                  args.err, DEV_ERR_TIMEOUT_VF);
+    }
+  } else if (warp == XB_WARP_I0 || warp == XB_WARP_I1) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- MMA issuers
+      // Issuer k takes the ranges r = k, k + 2, ...: per stage the hi x hi products into E_k (a
+      // fresh, exact accumulation per range) and the cross products lo x hi and hi x lo into X_k
+      // (restarted every xr of its ranges); one commit per range, whose arrival frees the range's
+      // slots and starts the drains.  With two issuers one's waits and commit
+      // overlap the other's MMAs, and neither waits for the other's drains.
+      constexpr uint32_t idesc = idesc_f16(VF_BM, XB_BN, false);
+      const int k = warp == XB_WARP_I0 ? 0 : 1;
+      const uint32_t e_tmem = tmem + 2 * k * XB_BN, x_tmem = e_tmem + XB_BN;
+      for (int r = k, u = 0; r < n_ranges; r += 2, ++u) {
+        const int it0 = r * kd, it1 = min(n_it, it0 + kd);
+        const bool x_start = u % xr == 0;
+        if (u >= 1 && !mbar_spin(&e_free[k], (u - 1) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)) break;
+        if (x_start && u >= xr &&
+            !mbar_spin(&x_free[k], ((u / xr) - 1) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF))
+          break;
+        bool alive = true;
+        for (int it = it0; it < it1; ++it) {
+          const int s = it % XB_STAGES;
+          if (!(alive = mbar_spin(&tma_full[s], (it / XB_STAGES) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)))
+            break;
+          tc_fence_after();
+          const uint64_t da = sw128_desc(smem_base + s * XB_STAGE), db = da + (XB_A_BYTES >> 4);
+          // K steps of 16 values advance 32 bytes (2 descriptor units); lo parts sit 64 bytes on
+          tc_mma_f16(e_tmem, da, db, idesc, it > it0 ? 1u : 0u);
+          tc_mma_f16(e_tmem, da + 2, db + 2, idesc, 1u);
+          tc_mma_f16(x_tmem, da + 4, db, idesc, (x_start && it == it0) ? 0u : 1u);
+          tc_mma_f16(x_tmem, da + 6, db + 2, idesc, 1u);
+          tc_mma_f16(x_tmem, da, db + 4, idesc, 1u);
+          tc_mma_f16(x_tmem, da + 2, db + 6, idesc, 1u);
+        }
+        if (!alive) break;
+        tc_commit(&rdone[r % NRB]);
+      }
+      // every MMA issued by both issuers has completed once fin_bar fires
+      tc_commit(fin_bar);
+      int zero = 0;
+      mbar_wait(fin_bar, 0, reinterpret_cast<volatile int*>(&zero), args.err, DEV_ERR_TIMEOUT_VF);
+    }
+  } else {
+    // ------------------------------------------------------------------ drains and epilogue
+    const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31 (hardware rule)
+    const int group = (warp - 3) >> 2;          // columns XB_HC*group .. +XB_HC-1
+    const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
+    const uint32_t c_base = static_cast<uint32_t>(group * XB_HC);
+    float S[XB_HC];
+#pragma unroll
+    for (int k = 0; k < XB_HC; ++k) S[k] = 0.0f;
+    // S += this thread's 32 columns of the accumulator at TMEM column col
+    auto add_acc = [&](uint32_t col) {
+      uint32_t d[32];
+      tmem_ld_32x32b_x32(tmem + lane_base + col + c_base, d);
+      tmem_wait_ld();
+#pragma unroll
+      for (int k = 0; k < 32; ++k) S[k] += __uint_as_float(d[k]);
+    };
+    // The FP32 running sums move into the CTA-private FP64 accumulator, column-major in the tile:
+    // Vacc[(split * gridDim.x + tile) * 128 * BN + column * 128 + row], column = c_base + c.  Column
+    // c of every thread goes after range r when r % flush == c (staggered, so that no drain carries a
+    // whole tile of FP64 adds at once): a store the first time (r < flush), then a fire-and-forget
+    // reduction; every column is flushed at least once per `flush` ranges.
+    double* acc = args.Vacc + (static_cast<int64_t>(split) * gridDim.x + blockIdx.x) * VF_BM * XB_BN +
+                  static_cast<int64_t>(c_base) * VF_BM + quarter * 32 + lane;
+    auto flush_col = [&](int c, bool first) {
+#pragma unroll
+      for (int k = 0; k < XB_HC; ++k)
+        if (k == c) {
+          if (first)
+            acc[k * VF_BM] = static_cast<double>(S[k]);
+          else
+            red_add_f64(acc + k * VF_BM, static_cast<double>(S[k]));
+          S[k] = 0.0f;
+        }
+    };
+    bool ok = true;
+    for (int r = 0; r < n_ranges && ok; ++r) {
+      const int k = r & 1, u = r >> 1;
+      // X_k is drained at the end of each of its periods and after issuer k's last range
+      const bool x_end = u % xr == xr - 1 || r + 2 >= n_ranges;
+      ok = __all_sync(0xffffffffu,
+                      mbar_wait(&rdone[r % NRB], (r / NRB) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF));
+      __syncwarp();
+      if (!ok) break;
+      tc_fence_after();
+      add_acc(2 * k * XB_BN);
+      if (x_end) add_acc((2 * k + 1) * XB_BN);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&e_free[k]);
+        if (x_end) mbar_arrive(&x_free[k]);
+      }
+      // staggered FP64 flush (the accumulators are already handed back to the MMAs)
+      if (args.flush > 0 && r % args.flush < XB_HC) flush_col(r % args.flush, r < args.flush);
+    }
+    if (args.flush > 0) {
+      // the remaining sums join the FP64 accumulator (columns never flushed in the loop are
+      // stored); a finalize kernel writes V (mode 0) or adds the tile into M (mode 1)
+      if (ok) {
+#pragma unroll
+        for (int c = 0; c < XB_HC; ++c) {
+          if (c < min(n_ranges, args.flush))
+            red_add_f64(acc + c * VF_BM, static_cast<double>(S[c]));
+          else
+            acc[c * VF_BM] = static_cast<double>(S[c]);
+        }
+      }
+    } else if (MODE == 0) {
+      // FP32 sums straight to V: row = outer point ib + row of component x -> V[split][pq][x][il]
+      const int row = quarter * 32 + lane;
+      const int64_t il = static_cast<int64_t>(ib) + row;
+      const int64_t col_off = static_cast<int64_t>(x) * args.gcp + il;
+      const int pq0 = t.n_tile * XB_BN + static_cast<int>(c_base);
+      if (ok && !*abort_flag && il < args.n_i && n_it > 0) {
+        float* Vz = args.V + static_cast<int64_t>(split) * args.n_pair * 3 * args.gcp;
+#pragma unroll
+        for (int k = 0; k < XB_HC; ++k) {
+          const int pq = pq0 + k;
+          if (pq < args.n_pair)
+            Vz[static_cast<int64_t>(pq) * 3 * args.gcp + col_off] =
+                ldexpf(S[k] * args.unscale_g, -__ldg(args.colexp + pq));
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// =================================================================== bf16 x3 engine (step (b))
+constexpr int BF_BN = 160;
+constexpr int BF_HC = BF_BN / 2;
+constexpr int BF_PARTS = 3;
+constexpr int BF_A_TILE = VF_BM * 64;             // bytes per part of an A tile (128 rows of 64 B)
+constexpr int BF_B_TILE = BF_BN * 64;
+constexpr int BF_A_BYTES = BF_PARTS * BF_A_TILE;
+constexpr int BF_B_BYTES = BF_PARTS * BF_B_TILE;
+constexpr int BF_STAGE = ((BF_A_BYTES + BF_B_BYTES + 1023) / 1024) * 1024;
+constexpr int BF_STAGES = 4;
+constexpr int BF_MMA_WARPS = 2;                   // issuers of the even / odd ranges
+constexpr int BF_THREADS = (1 + BF_MMA_WARPS + DRAIN_WARPS) * 32;
+constexpr int BF_SMEM = BF_STAGES * BF_STAGE + 1024 + 256;
+static_assert(BF_BN == vf_bn(3), "tile width of the bf16 engine");
+static_assert(BF_SMEM <= 232448, "shared memory per CTA");
+static_assert(NRB > BF_STAGES, "range barriers");
+static_assert(2 * BF_BN <= 512 && BF_BN % 32 == 0, "two accumulators, drain halves of 16-column chunks");
+
+__global__ void __launch_bounds__(BF_THREADS, 1)
+    vfield_bf16_kernel(const __grid_constant__ CUtensorMap tm_g, const __grid_constant__ CUtensorMap tm_rho,
+                       const VfieldArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + BF_STAGES * BF_STAGE);
+  uint64_t* tma_full = bars;                  // [BF_STAGES] the stage's loads landed
+  uint64_t* rdone = bars + BF_STAGES;         // [NRB] the MMAs of range r (r % NRB) completed
+  uint64_t* d_free = bars + BF_STAGES + NRB;  // [2] the drains released accumulator b
+  uint64_t* fin_bar = bars + BF_STAGES + NRB + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + BF_STAGES + NRB + 3);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TileXY t = grouped_tile(blockIdx.x, 3 * args.mt_per_x, args.n_tiles);
+  const int x = t.m_tile / args.mt_per_x;
+  const int ib = (t.m_tile - x * args.mt_per_x) * VF_BM;
+  const int row0 = static_cast<int>(x * args.gcp) + ib;
   const int split = blockIdx.y;
   const int kb0 = split * args.kb_per_split;
   const int kb1 = min(args.n_kb, kb0 + args.kb_per_split);
@@ -148,10 +365,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int n_ranges = (n_it + kd - 1) / kd;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) mbar_init(&tma_full[s], 1);
+    for (int s = 0; s < BF_STAGES; ++s) mbar_init(&tma_full[s], 1);
     for (int r = 0; r < NRB; ++r) mbar_init(&rdone[r], 1);
     for (int b = 0; b < 2; ++b) mbar_init(&d_free[b], DRAIN_WARPS);
-    mbar_init(fin_bar, MMA_WARPS);
+    mbar_init(fin_bar, BF_MMA_WARPS);
     *abort_flag = 0;
     fence_mbar_init();
     tma_prefetch_desc(&tm_g);
@@ -173,33 +390,26 @@ __global__ void __launch_bounds__(THREADS, 1)
       int seen = 0;  // ranges known to have completed (their slots are free again)
       int issued_end = kb0;
       for (int kb = kb0; kb < kb1; ++kb) {
-        const int it = kb - kb0, s = it % STAGES;
-        if (it >= STAGES) {
-          const int need = (it - STAGES) / kd;  // range holding the slot's previous stage
+        const int it = kb - kb0, s = it % BF_STAGES;
+        if (it >= BF_STAGES) {
+          const int need = (it - BF_STAGES) / kd;  // range holding the slot's previous stage
           bool ok = true;
           for (; seen <= need && ok; ++seen)
             ok = mbar_wait(&rdone[seen % NRB], (seen / NRB) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF);
           if (!ok) break;
         }
-        mbar_arrive_expect_tx(&tma_full[s], Cfg::A_BYTES + Cfg::B_BYTES);
-        uint8_t* st = smem + s * Cfg::STAGE_BYTES;
-        if (PARTS == 2) {
-          // one 128-byte-row box per operand holds both parts
-          tma_load_3d(st, &tm_g, &tma_full[s], kb * 2 * VF_BK, row0, 0);
-          tma_load_3d(st + Cfg::A_BYTES, &tm_rho, &tma_full[s], kb * 2 * VF_BK, n_tile * BN, 0);
-        } else {
-          for (int p = 0; p < PARTS; ++p) {
-            tma_load_3d(st + p * A_TILE, &tm_g, &tma_full[s], kb * VF_BK, row0, p);
-            tma_load_3d(st + Cfg::A_BYTES + p * Cfg::B_TILE, &tm_rho, &tma_full[s], kb * VF_BK, n_tile * BN, p);
-          }
+        mbar_arrive_expect_tx(&tma_full[s], BF_A_BYTES + BF_B_BYTES);
+        uint8_t* st = smem + s * BF_STAGE;
+        for (int p = 0; p < BF_PARTS; ++p) {
+          tma_load_3d(st + p * BF_A_TILE, &tm_g, &tma_full[s], kb * VF_BK, row0, p);
+          tma_load_3d(st + BF_A_BYTES + p * BF_B_TILE, &tm_rho, &tma_full[s], kb * VF_BK, t.n_tile * BF_BN, p);
         }
         issued_end = kb + 1;
       }
-      // the copies still in flight land before the CTA may exit
       int zero = 0;
-      for (int kb = max(kb0, issued_end - STAGES); kb < issued_end; ++kb) {
+      for (int kb = max(kb0, issued_end - BF_STAGES); kb < issued_end; ++kb) {
         const int it = kb - kb0;
-        mbar_wait(&tma_full[it % STAGES], (it / STAGES) & 1, reinterpret_cast<volatile int*>(&zero), args.err,
+        mbar_wait(&tma_full[it % BF_STAGES], (it / BF_STAGES) & 1, reinterpret_cast<volatile int*>(&zero), args.err,
                   DEV_ERR_TIMEOUT_VF);
       }
     }
@@ -209,72 +419,66 @@ __global__ void __launch_bounds__(THREADS, 1)
       // A range of kd stages goes into one TMEM accumulator: first the cross products of each
       // stage as it lands (the accumulator is still small), then the hi x hi product of every
       // stage; one commit per range.  Warp 1 issues the even ranges (accumulator 0), the last warp
-      // the odd ones (accumulator 1): a commit tracks only its own thread's MMAs, so while one
-      // issuer's commit completes the other keeps the tensor pipe fed.
-      constexpr uint32_t idesc = idesc_f16(VF_BM, BN, BF16);
+      // the odd ones (accumulator 1).
+      constexpr uint32_t idesc = idesc_f16(VF_BM, BF_BN, true);
+      constexpr int pa_of[5] = {1, 0, 2, 0, 1};   // (A part, B part) of the products before hi x hi
+      constexpr int pb_of[5] = {1, 2, 0, 1, 0};
       bool alive = true;
-      for (int r = warp == 1 ? 0 : 1; r < n_ranges && alive; r += MMA_WARPS) {
+      for (int r = warp == 1 ? 0 : 1; r < n_ranges && alive; r += BF_MMA_WARPS) {
         const int it0 = r * kd, it1 = min(n_it, it0 + kd);
         const int b = r & 1, u = r >> 1;
-        const uint32_t d_tmem = tmem + b * BN;
+        const uint32_t d_tmem = tmem + b * BF_BN;
         if (u >= 1 && !mbar_wait(&d_free[b], (u - 1) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)) break;
         for (int it = it0; it < it1; ++it) {
-          const int s = it % STAGES;
-          if (!(alive = mbar_wait(&tma_full[s], (it / STAGES) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF))) break;
+          const int s = it % BF_STAGES;
+          if (!(alive = mbar_wait(&tma_full[s], (it / BF_STAGES) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF))) break;
           tc_fence_after();
-          const uint32_t sa = smem_base + s * Cfg::STAGE_BYTES;
-          const uint32_t sb = sa + Cfg::A_BYTES;
+          const uint32_t sa = smem_base + s * BF_STAGE;
+          const uint32_t sb = sa + BF_A_BYTES;
 #pragma unroll
-          for (int p = 0; p < Cfg::NPROD - 1; ++p) {
-            int pa, pb;
-            prod_parts<PARTS>(p, pa, pb);
+          for (int p = 0; p < 5; ++p)
 #pragma unroll
             for (int ks = 0; ks < 2; ++ks)
-              tc_mma_f16(d_tmem, op_desc<PARTS>(sa, A_TILE, pa, ks), op_desc<PARTS>(sb, Cfg::B_TILE, pb, ks), idesc,
+              tc_mma_f16(d_tmem, sdesc_kmajor_sw64(sa + pa_of[p] * BF_A_TILE + ks * 32),
+                         sdesc_kmajor_sw64(sb + pb_of[p] * BF_B_TILE + ks * 32), idesc,
                          (it == it0 && p == 0 && ks == 0) ? 0u : 1u);
-          }
         }
         if (!alive) break;
         for (int it = it0; it < it1; ++it) {
-          const uint32_t sa = smem_base + (it % STAGES) * Cfg::STAGE_BYTES;
-          const uint32_t sb = sa + Cfg::A_BYTES;
+          const uint32_t sa = smem_base + (it % BF_STAGES) * BF_STAGE;
+          const uint32_t sb = sa + BF_A_BYTES;
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks)
-            tc_mma_f16(d_tmem, op_desc<PARTS>(sa, A_TILE, 0, ks), op_desc<PARTS>(sb, Cfg::B_TILE, 0, ks), idesc, 1u);
+            tc_mma_f16(d_tmem, sdesc_kmajor_sw64(sa + ks * 32), sdesc_kmajor_sw64(sb + ks * 32), idesc, 1u);
         }
         tc_commit(&rdone[r % NRB]);
       }
-      // every MMA issued by both issuers has completed once fin_bar fires
       tc_commit(fin_bar);
       int zero = 0;
       mbar_wait(fin_bar, 0, reinterpret_cast<volatile int*>(&zero), args.err, DEV_ERR_TIMEOUT_VF);
     }
   } else {
     // ------------------------------------------------------------------ range drains and epilogue
-    const int quarter = warp & 3;               // TMEM lanes 32*quarter .. +31 (hardware rule)
-    const int half = (warp - 2) >> 2;           // columns HC*half .. +HC-1
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
-    const uint32_t c_base = static_cast<uint32_t>(half * HC);
-    float S[HC];
+    const uint32_t c_base = static_cast<uint32_t>(half * BF_HC);
+    float S[BF_HC];
 #pragma unroll
-    for (int k = 0; k < HC; ++k) S[k] = 0.0f;
-    // Adds the running sums into this thread's elements of the CTA-private FP64 accumulator,
-    // column-major in the tile: Vacc[(split * gridDim.x + tile) * 128 * BN + column * 128 + row],
-    // column = c_base + k (a store the first time, then fire-and-forget reductions, which need
-    // no result registers), and clears them.
+    for (int k = 0; k < BF_HC; ++k) S[k] = 0.0f;
     int nflush = 0;
     auto flush_sums = [&]() {
-      double* acc = args.Vacc + (static_cast<int64_t>(split) * gridDim.x + blockIdx.x) * VF_BM * BN +
+      double* acc = args.Vacc + (static_cast<int64_t>(split) * gridDim.x + blockIdx.x) * VF_BM * BF_BN +
                     static_cast<int64_t>(c_base) * VF_BM + quarter * 32 + lane;
       if (nflush == 0) {
 #pragma unroll
-        for (int k = 0; k < HC; ++k) acc[k * VF_BM] = static_cast<double>(S[k]);
+        for (int k = 0; k < BF_HC; ++k) acc[k * VF_BM] = static_cast<double>(S[k]);
       } else {
 #pragma unroll
-        for (int k = 0; k < HC; ++k) red_add_f64(acc + k * VF_BM, static_cast<double>(S[k]));
+        for (int k = 0; k < BF_HC; ++k) red_add_f64(acc + k * VF_BM, static_cast<double>(S[k]));
       }
 #pragma unroll
-      for (int k = 0; k < HC; ++k) S[k] = 0.0f;
+      for (int k = 0; k < BF_HC; ++k) S[k] = 0.0f;
       ++nflush;
     };
     bool ok = true;
@@ -285,9 +489,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       __syncwarp();
       if (!ok) break;
       tc_fence_after();
-      const uint32_t src = tmem + lane_base + b * BN + c_base;
+      const uint32_t src = tmem + lane_base + b * BF_BN + c_base;
 #pragma unroll
-      for (int c = 0; c < HC; c += 16) {
+      for (int c = 0; c < BF_HC; c += 16) {
         uint32_t d0[16];
         tmem_ld_x16(src + c, d0);
         tmem_wait_ld();
@@ -297,23 +501,19 @@ __global__ void __launch_bounds__(THREADS, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&d_free[b]);
-      // FP64 flush of the partial sums (the accumulator is already handed back to the MMA)
       if (args.flush > 0 && (r + 1) % args.flush == 0) flush_sums();
     }
     if (args.flush > 0) {
-      // the remaining sums join the FP64 accumulator; a finalize kernel writes V (mode 0) or adds
-      // the tile into M (mode 1)
       if (ok && n_ranges % args.flush != 0) flush_sums();
     } else {
-      // FP32 sums straight to V: row = outer point ib + row of component x -> V[split][pq][x][il]
       const int row = quarter * 32 + lane;
       const int64_t il = static_cast<int64_t>(ib) + row;
       const int64_t col_off = static_cast<int64_t>(x) * args.gcp + il;
-      const int pq0 = n_tile * BN + static_cast<int>(c_base);
+      const int pq0 = t.n_tile * BF_BN + static_cast<int>(c_base);
       if (ok && !*abort_flag && il < args.n_i && n_it > 0) {
         float* Vz = args.V + static_cast<int64_t>(split) * args.n_pair * 3 * args.gcp;
 #pragma unroll
-        for (int k = 0; k < HC; ++k) {
+        for (int k = 0; k < BF_HC; ++k) {
           const int pq = pq0 + k;
           if (pq < args.n_pair)
             Vz[static_cast<int64_t>(pq) * 3 * args.gcp + col_off] =
@@ -332,26 +532,21 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// =================================================================== finalize kernels
 // V from the FP64 accumulator of the GEMM: one CTA per (tile, split), thread = tile row; the tile
 // order is the GEMM's grouped order.
 template <int BN>
 __global__ void __launch_bounds__(VF_BM) vfield_finalize_kernel(const VfieldArgs args) {
-  const int m_tiles = 3 * args.mt_per_x;
-  const int L = blockIdx.x;
-  const int group = L / (GM * args.n_tiles);
-  const int first_m = group * GM;
-  const int gm = min(GM, m_tiles - first_m);
-  const int rem = L - group * GM * args.n_tiles;
-  const int m_tile = first_m + rem % gm, n_tile = rem / gm;
-  const int x = m_tile / args.mt_per_x;
+  const TileXY t = grouped_tile(blockIdx.x, 3 * args.mt_per_x, args.n_tiles);
+  const int x = t.m_tile / args.mt_per_x;
   const int row = threadIdx.x;
-  const int64_t il = static_cast<int64_t>(m_tile - x * args.mt_per_x) * VF_BM + row;
+  const int64_t il = static_cast<int64_t>(t.m_tile - x * args.mt_per_x) * VF_BM + row;
   if (il >= args.n_i) return;
-  const double* acc = args.Vacc + (static_cast<int64_t>(blockIdx.y) * gridDim.x + L) * VF_BM * BN + row;
+  const double* acc = args.Vacc + (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x) * VF_BM * BN + row;
   float* v = args.V + static_cast<int64_t>(blockIdx.y) * args.n_pair * 3 * args.gcp + x * args.gcp + il;
-  const int ncol = min(BN, args.n_pair - n_tile * BN);
+  const int ncol = min(BN, args.n_pair - t.n_tile * BN);
   for (int c = 0; c < ncol; ++c) {
-    const int pq = n_tile * BN + c;
+    const int pq = t.n_tile * BN + c;
     v[static_cast<int64_t>(pq) * 3 * args.gcp] =
         ldexpf(static_cast<float>(acc[static_cast<int64_t>(c) * VF_BM]) * args.unscale_g, -__ldg(args.colexp + pq));
   }
@@ -362,43 +557,20 @@ __global__ void __launch_bounds__(VF_BM) vfield_finalize_kernel(const VfieldArgs
 // owned by one tile).
 template <int BN>
 __global__ void __launch_bounds__(VF_BM) assemble_finalize_kernel(const VfieldArgs args) {
-  const int m_tiles = (args.rows_a + VF_BM - 1) / VF_BM;
-  const int L = blockIdx.x;
-  const int group = L / (GM * args.n_tiles);
-  const int first_m = group * GM;
-  const int gm = min(GM, m_tiles - first_m);
-  const int rem = L - group * GM * args.n_tiles;
-  const int m_tile = first_m + rem % gm, n_tile = rem / gm;
-  const int pq = m_tile * VF_BM + threadIdx.x;
+  const TileXY t = grouped_tile(blockIdx.x, (args.rows_a + VF_BM - 1) / VF_BM, args.n_tiles);
+  const int pq = t.m_tile * VF_BM + threadIdx.x;
   if (pq >= args.rows_a) return;
-  const double* acc = args.Vacc + (static_cast<int64_t>(blockIdx.y) * gridDim.x + L) * VF_BM * BN + threadIdx.x;
-  double* m = args.M + static_cast<int64_t>(pq) * args.ldm + n_tile * BN;
+  const double* acc = args.Vacc + (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x) * VF_BM * BN + threadIdx.x;
+  double* m = args.M + static_cast<int64_t>(pq) * args.ldm + t.n_tile * BN;
   const int ea = args.exp_a[pq];
-  const int ncol = min(BN, args.n_pair - n_tile * BN);
+  const int ncol = min(BN, args.n_pair - t.n_tile * BN);
   for (int c = 0; c < ncol; ++c) {
-    const int e = ea + __ldg(args.exp_b + n_tile * BN + c);
+    const int e = ea + __ldg(args.exp_b + t.n_tile * BN + c);
     m[c] += acc[static_cast<int64_t>(c) * VF_BM] * __longlong_as_double(static_cast<long long>(1023 - e) << 52);
   }
 }
 
-template <int PARTS, int MODE>
-void launch_t(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int splits,
-              cudaStream_t st) {
-  auto kern = vfield_tc_kernel<PARTS, MODE>;
-  constexpr int smem = VfCfg<PARTS>::SMEM;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  const int m_tiles = MODE == 0 ? 3 * a.mt_per_x : (a.rows_a + VF_BM - 1) / VF_BM;
-  dim3 grid(static_cast<unsigned>(m_tiles * a.n_tiles), static_cast<unsigned>(splits));
-  kern<<<grid, THREADS, smem, st>>>(*tm_g, *tm_rho, a);
-}
-
-template <int PARTS, int MODE>
-void finalize_t(const VfieldArgs& a, int splits, cudaStream_t st) {
-  const int m_tiles = MODE == 0 ? 3 * a.mt_per_x : (a.rows_a + VF_BM - 1) / VF_BM;
-  dim3 grid(static_cast<unsigned>(m_tiles * a.n_tiles), static_cast<unsigned>(splits));
-  if (MODE == 0 && a.flush > 0) vfield_finalize_kernel<VfCfg<PARTS>::BN><<<grid, VF_BM, 0, st>>>(a);
-  if (MODE == 1) assemble_finalize_kernel<VfCfg<PARTS>::BN><<<grid, VF_BM, 0, st>>>(a);
-}
+int m_tiles_of(const VfieldArgs& a) { return a.mode == 0 ? 3 * a.mt_per_x : (a.rows_a + VF_BM - 1) / VF_BM; }
 
 }  // namespace
 
@@ -407,28 +579,28 @@ bool vfield_tc_supported(int n_nuc) { return n_nuc >= 1 && n_nuc <= 8; }
 void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int parts,
                       int splits, cudaStream_t st) {
   if (a.n_tiles <= 0 || splits <= 0) return;
-  if (a.mode == 1) {
-    if (a.rows_a > 0) launch_t<2, 1>(tm_g, tm_rho, a, splits, st);
-    return;
+  if (a.mode == 1 ? a.rows_a <= 0 : a.mt_per_x <= 0) return;
+  dim3 grid(static_cast<unsigned>(m_tiles_of(a) * a.n_tiles), static_cast<unsigned>(splits));
+  if (a.mode == 1 || parts == 2) {
+    auto kern = a.mode == 1 ? xgemm_kernel<1> : xgemm_kernel<0>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, XB_SMEM);
+    kern<<<grid, XB_THREADS, XB_SMEM, st>>>(*tm_g, *tm_rho, a);
+  } else {
+    cudaFuncSetAttribute(vfield_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BF_SMEM);
+    vfield_bf16_kernel<<<grid, BF_THREADS, BF_SMEM, st>>>(*tm_g, *tm_rho, a);
   }
-  if (a.mt_per_x <= 0) return;
-  if (parts == 2)
-    launch_t<2, 0>(tm_g, tm_rho, a, splits, st);
-  else
-    launch_t<3, 0>(tm_g, tm_rho, a, splits, st);
 }
 
 void launch_vfield_tc_finalize(const VfieldArgs& a, int parts, int splits, cudaStream_t st) {
-  if (a.n_tiles <= 0 || splits <= 0) return;
-  if (a.mode == 1) {
-    if (a.rows_a > 0) finalize_t<2, 1>(a, splits, st);
-    return;
-  }
-  if (a.mt_per_x <= 0 || a.flush <= 0) return;
-  if (parts == 2)
-    finalize_t<2, 0>(a, splits, st);
+  if (a.n_tiles <= 0 || splits <= 0 || a.flush <= 0) return;
+  if (a.mode == 1 ? a.rows_a <= 0 : a.mt_per_x <= 0) return;
+  dim3 grid(static_cast<unsigned>(m_tiles_of(a) * a.n_tiles), static_cast<unsigned>(splits));
+  if (a.mode == 1)
+    assemble_finalize_kernel<XB_BN><<<grid, VF_BM, 0, st>>>(a);
+  else if (parts == 2)
+    vfield_finalize_kernel<XB_BN><<<grid, VF_BM, 0, st>>>(a);
   else
-    finalize_t<3, 0>(a, splits, st);
+    vfield_finalize_kernel<BF_BN><<<grid, VF_BM, 0, st>>>(a);
 }
 
 }  // namespace xtc

@@ -104,9 +104,10 @@ struct xtc_ctx {
   double ms[XTC_N_KERNELS] = {0};
   int64_t launches[XTC_N_KERNELS] = {0};
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  int vf_kd = 1;  // K-blocks per tensor-core accumulation range in step (b)
+  int vf_kd = 2;  // K-blocks per tensor-core accumulation range in step (b)
   int vf_flush = 8192;  // inner points (K values) between FP64 flushes of the running sums (0: FP32 only)
-  int as_kd = 1;  // the same for step (d) (both engines)
+  int as_kd = 2;  // the same for step (d)
+  int x_period = 64;  // fp16 engine: K-blocks between drains of the cross-product accumulator
   // batched builds: lane contexts, each with its own stream (created on first use)
   std::vector<xtc_ctx*> lanes;
   std::vector<cudaStream_t> lane_streams;
@@ -282,6 +283,12 @@ int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t NGp, int parts, int64_t n_o
   return best;
 }
 
+// Stages per exact accumulation range of the fp16 engine: the largest of 1, 2, 4 not above k (the
+// split tables hold one quantum per range, and chunk and grid lengths are multiples of 128 points);
+// step (b) at most 2 (the gradient kernel stages a whole range of its tiles in shared memory).
+int f16_range(int k) { return k >= 4 ? 4 : (k >= 2 ? 2 : 1); }
+int f16_range_b(int k) { return std::min(f16_range(k), 2); }
+
 // Ranges of kd stages (32 K values each) between FP64 flushes for a flush interval of `points` K
 // values (0: no flushes).
 int flush_ranges(int points, int kd) { return points > 0 ? std::max(1, points / (32 * kd)) : 0; }
@@ -355,6 +362,7 @@ int xtc_create(xtc_ctx** out, const xtc_params* p) {
   if (const char* s = std::getenv("XTC_VF_KD")) ctx->vf_kd = std::max(1, std::atoi(s));
   if (const char* s = std::getenv("XTC_AS_KD")) ctx->as_kd = std::max(1, std::atoi(s));
   if (const char* s = std::getenv("XTC_VF_FLUSH")) ctx->vf_flush = std::max(0, std::atoi(s));
+  if (const char* s = std::getenv("XTC_X_PERIOD")) ctx->x_period = std::max(1, std::atoi(s));
   if (p->range_stages > 0) ctx->vf_kd = ctx->as_kd = p->range_stages;
   if (!ensure(ctx->jp_dev, sizeof(JastrowParams)) || !ensure(ctx->err_dev, 16) || !ensure(ctx->flag_dev, 16)) {
     xtc_destroy(ctx);
@@ -427,6 +435,11 @@ int xtc_set_outer_range(xtc_ctx* ctx, int64_t begin, int64_t end) {
   ctx->outer_end = end;
   return XTC_OK;
 }
+
+// 1: one accumulator per range of kd stages, truncating FP32 accumulation (192-column tiles);
+// 2: block-exact fp16 split, exact hi x hi accumulator pair plus a cross-product accumulator
+//    (160-column tiles).
+int xtc_engine_revision(void) { return 2; }
 
 int xtc_get_timings(xtc_ctx* ctx, double* ms, int64_t* launches, int n) {
   if (!ctx || n < XTC_N_KERNELS) return XTC_ERR_ARG;
@@ -539,8 +552,8 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
     } else {
       const int js = jtab_stride(n_nuc);
       launch_jtab(*d_grid, n_grid, pl.NGp, ctx->jp_dev.as<JastrowParams>(), n_nuc, js, ctx->jtab.as<float>(), st);
-      launch_rho_split(ctx->phiT.as<double>(), *d_w, n_grid, pl.NGp, n_orb, pl.parts_b, pl.parts_b == 3,
-                       pl.parts_b == 2, ctx->pair_p.as<int>(), ctx->pair_q.as<int>(), ctx->colmax.as<unsigned int>(),
+      launch_rho_split(ctx->phiT.as<double>(), *d_w, n_grid, pl.NGp, n_orb, pl.parts_b, f16_range_b(ctx->vf_kd),
+                       ctx->pair_p.as<int>(), ctx->pair_q.as<int>(), ctx->colmax.as<unsigned int>(),
                        ctx->colexp.as<int>(), ctx->rho.p, st);
     }
   });
@@ -607,6 +620,7 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   g.n_seg = (n_kb + g.kb_per_seg - 1) / g.kb_per_seg;
   g.n_nuc = ctx->jp.n_nuc;
   g.g_scale = std::ldexp(1.0f, sg);
+  g.range_blocks = f16_range_b(ctx->vf_kd);
   timed(ctx, XTC_K_GRAD, 1, [&] { launch_gfield(&maps.g_store, g, pl.parts_b, st); });
 
   VfieldArgs a{};
@@ -620,7 +634,8 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   a.n_pair = pl.NP;
   a.n_kb = n_kb;
   a.kb_per_split = (a.n_kb + pl.splits - 1) / pl.splits;
-  a.kd = std::min(ctx->vf_kd, pl.parts_b == 2 ? 4 : 2);
+  a.kd = pl.parts_b == 2 ? f16_range_b(ctx->vf_kd) : std::min(ctx->vf_kd, 2);
+  a.xper = ctx->x_period;
   a.flush = flush_ranges(ctx->vf_flush, a.kd);
   a.unscale_g = std::ldexp(1.0f, -sg);
   a.err = ctx->err_dev.as<int>();
@@ -857,7 +872,8 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
           da.n_tiles = (NP + vf_bn(2) - 1) / vf_bn(2);
           da.n_kb = static_cast<int>(kdim / VF_BK);
           da.kb_per_split = da.n_kb;
-          da.kd = std::min(ctx->as_kd, 4);
+          da.kd = f16_range(ctx->as_kd);
+          da.xper = ctx->x_period;
           da.flush = flush_ranges(ctx->vf_flush > 0 ? ctx->vf_flush : 8192, da.kd);
           da.Vacc = ctx->Vacc.as<double>();
           da.M = M;
@@ -866,9 +882,10 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
           da.exp_b = ctx->eR.as<int>();
           da.err = ctx->err_dev.as<int>();
           timed(ctx, XTC_K_AUX, M2 ? 3 : 2, [&] {
-            launch_lr_split(ctx->L32.as<float>(), NP, kdim, ctx->L.as<uint16_t>(), ctx->eL.as<int>(), st);
-            launch_lr_split(ctx->R32.as<float>(), NP, kdim, ctx->R.as<uint16_t>(), ctx->eR.as<int>(), st);
-            if (M2) launch_lr_split(ctx->R32b.as<float>(), NP, kdim, ctx->R2.as<uint16_t>(), ctx->eR2.as<int>(), st);
+            launch_lr_split(ctx->L32.as<float>(), NP, kdim, 4, da.kd, ctx->L.as<uint16_t>(), ctx->eL.as<int>(), st);
+            launch_lr_split(ctx->R32.as<float>(), NP, kdim, 4, da.kd, ctx->R.as<uint16_t>(), ctx->eR.as<int>(), st);
+            if (M2)
+              launch_lr_split(ctx->R32b.as<float>(), NP, kdim, 4, da.kd, ctx->R2.as<uint16_t>(), ctx->eR2.as<int>(), st);
           });
           timed(ctx, XTC_K_ASSEMBLE, 1, [&] { launch_vfield_tc(&tm_L, &tm_R, da, 2, 1, st); });
           timed(ctx, XTC_K_AUX, 1, [&] { launch_vfield_tc_finalize(da, 2, 1, st); });

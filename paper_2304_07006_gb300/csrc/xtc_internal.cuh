@@ -26,15 +26,24 @@ constexpr int PT_COEF = 14;     // x y z, K0[3] K1[3] K2[3], Hc1 Hc2
 
 // Tile shapes of the tensor-core kernels.
 constexpr int VF_BM = 128;      // outer points per tile (TMEM lanes)
-// orbital pairs per step (b) tile: two TMEM accumulators of vf_bn columns, a running sum of vf_bn / 2
-// columns in the registers of each drain thread; 5 pipeline stages of the split operands fit in
-// shared memory with 2 parts (40 KB per stage), 4 with 3 parts (54 KB)
-__host__ __device__ constexpr int vf_bn(int parts) { return parts == 2 ? 192 : 160; }
+// orbital pairs per tensor-core tile (B rows): the fp16 engine keeps two pairs of TMEM accumulators
+// of 128 columns (exact hi x hi and cross products per issuer), 7 pipeline stages of 32 KB; the bf16
+// engine two accumulators of 160 columns, 4 stages of 54 KB; each drain thread holds a running sum
+// of half a tile row in registers
+__host__ __device__ constexpr int vf_bn(int parts) { return parts == 2 ? 128 : 160; }
 constexpr int VF_BK = 32;       // inner points per pipeline stage (64-byte rows, SWIZZLE_64B)
 constexpr int AS_BM = 128;      // step (d) tile rows (pairs pq)
 constexpr int AS_BN = 128;      // step (d) tile columns (pairs rs)
 constexpr int AS_BK = 32;
 constexpr int CHUNK_ALIGN = 128;
+// fp16 engine: exact hi x hi accumulation over ranges of kd K-blocks of VF_BK values needs
+// kd * VF_BK * 2^(bits_a + bits_b) <= 2^24.  Step (b) (kd <= 2): G carries GEMM_BITS_A bits and
+// rho^T gemm_bits_b(kd) on per-range quanta; step (d): L and R both gemm_bits_lr(kd) per range.
+constexpr int GEMM_BITS_A = 9;
+__host__ __device__ constexpr int log2_kd(int kd) { return kd >= 8 ? 3 : kd >= 4 ? 2 : kd >= 2 ? 1 : 0; }
+__host__ __device__ constexpr int gemm_bits_b(int kd) { return 24 - 5 - GEMM_BITS_A - log2_kd(kd); }
+__host__ __device__ constexpr int gemm_bits_lr(int kd) { return (24 - 5 - log2_kd(kd)) / 2; }
+static_assert(GEMM_BITS_A + gemm_bits_b(2) + 5 + 1 <= 24 && 2 * gemm_bits_lr(4) + 5 + 2 <= 24, "exact ranges");
 
 // Error codes written by kernels into the context's device error word.
 constexpr int DEV_ERR_TIMEOUT_VF = 1;
@@ -45,8 +54,8 @@ constexpr int DEV_ERR_TIMEOUT_SELFTEST = 3;
 void launch_wait_timeout_selftest(int* err, unsigned long long limit_ns, cudaStream_t st);
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
-// Row stride of the FP64 accumulator M[pq][rs]: whole 128-column (bf16 step d) and 192-column
-// (fp16 step d) tiles fit in a row.
+// Row stride of the FP64 accumulator M[pq][rs]: a multiple of 32 (the bf16 step (d) kernel writes
+// whole 32-column groups of its 128-column tiles) with room for every pair.
 inline int64_t m_stride(int64_t n_pair) { return round_up(n_pair, 384); }
 
 // The current device's opt-in maximum of dynamic shared memory per CTA.  Kernels whose dynamic
@@ -71,13 +80,14 @@ inline int jtab_stride(int n_nuc) { return n_nuc <= 4 ? 12 : 16; }
 void launch_jtab(const double* grid, int64_t n_grid, int64_t n_grid_pad, const JastrowParams* jp_dev,
                  int n_nuc, int js, float* jtab, cudaStream_t st);
 
-// Pair products rho^T[pq][j] = w_j phi_p(j) phi_q(j) split into parts (fp16 or bf16), with
-// per-pair power-of-2 scale (fp16).  colexp[pq] receives the exponent used.  Layout: fp16 (2 parts)
-// [pq][j / 32][part][j % 32] (both parts of a 32-point block in one 128-byte row); bf16 (3 parts)
-// [part][pq][j].
-void launch_rho_split(const double* phiT, const double* w, int64_t n_grid, int64_t n_grid_pad, int n_orb,
-                      int parts, bool bf16, bool scale, const int* pair_p, const int* pair_q,
-                      unsigned int* colmax_bits, int* colexp, void* out, cudaStream_t st);
+// Pair products rho^T[pq][j] = w_j phi_p(j) phi_q(j) split into parts.  fp16 (2 parts): each pair's
+// row scaled by a power of 2 (colexp[pq] receives the exponent; colmax is scratch) and split exactly
+// with one quantum per range of kd blocks of 32 points (gemm_bits_b(kd) bits), the two parts of a
+// block in one 128-byte row: [pq][j / 32][part][j % 32].  bf16 (3 parts): per-element split,
+// unscaled (colexp = 0), [part][pq][j].  n_pad must be a multiple of 32 kd.
+void launch_rho_split(const double* phiT, const double* w, int64_t n_grid, int64_t n_pad, int n_orb, int parts, int kd,
+                      const int* pair_p, const int* pair_q, unsigned int* colmax, int* colexp, void* out,
+                      cudaStream_t st);
 
 // FP64 pair products rho[j][pq] for the FP64 path (n_grid_pad rows, zero padded).
 void launch_rho_f64(const double* phi, const double* w, int64_t n_grid, int64_t n_grid_pad, int n_orb,
@@ -104,6 +114,7 @@ struct GfieldArgs {
   int n_kb, kb_per_seg, n_seg; // inner K-blocks (32 points), K-blocks per warp unit, units along K
   int n_nuc;
   float g_scale;               // 2^sG folded into the gradient
+  int range_blocks;            // fp16: K-blocks per exact range of the step (b) GEMM (1 or 2)
 };
 void launch_gfield(const CUtensorMap* tm_g_store, const GfieldArgs& a, int parts, cudaStream_t st);
 
@@ -120,7 +131,9 @@ struct VfieldArgs {
   int n_tiles;                 // column tiles: ceil(n_pair / vf_bn(parts))
   int n_pair;
   int kb_per_split, n_kb;      // inner K-blocks per split slice, total K-blocks
-  int kd;                      // K-blocks per TMEM accumulation range (then added to the FP32 running sum)
+  int kd;                      // K-blocks per TMEM accumulation range (then added to the FP32 running sum);
+                               // fp16 engine: 1, 2 or 4, the range of the operands' exact split
+  int xper;                    // fp16 engine: K-blocks between drains of the cross-product accumulator
   float unscale_g;             // 2^-sG
   int* err;
   // mode 1 (step d with fp16 x2 operands): A = L split rows (rows_a of them), B = R split rows
@@ -180,9 +193,13 @@ size_t fields_smem_bytes(int n_orb, int rank, int pts, bool f64, bool spin);
 void launch_fields(const FieldsArgs& a, bool f64, cudaStream_t st);  // f64: FP64 V, compute and output
 
 // Step (d) operands in fp16 x2: each FP32 row src[r][0..kdim) is scaled by 2^exps[r] (largest
-// magnitude in [2^13, 2^14)) and split into hi + lo fp16, both parts of a 32-element block in one
-// 128-byte row: dst[r][k / 32][part][k % 32].
-void launch_lr_split(const float* src, int rows, int64_t kdim, uint16_t* dst, int* exps, cudaStream_t st);
+// magnitude in [2^13, 2^14)) and split exactly into hi + lo fp16 with one quantum per range of kd
+// blocks of 32 values (gemm_bits_lr(kd) bits), both parts of a block in one 128-byte row:
+// dst[r][k' / 32][part][k' % 32].  kc = 4: the source holds 4 values per outer point (k = 4 i + c)
+// and k' = c * kdim / 4 + i (component-major, so that a range never mixes components); kc = 1:
+// k' = k.  kdim / kc must be a multiple of 32 kd.
+void launch_lr_split(const float* src, int rows, int64_t kdim, int kc, int kd, uint16_t* dst, int* exps,
+                     cudaStream_t st);
 
 // Step (d), tensor cores, bf16 x3: M[pq][rs] += sum_k L[pq][k] R[rs][k] over k < kdim (FP64 accumulator).
 void launch_assemble_tc(const CUtensorMap* tm_L, const CUtensorMap* tm_R, int n_pair, int kdim, int kd, double* M,

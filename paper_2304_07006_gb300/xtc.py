@@ -21,7 +21,7 @@ KERNEL_NAMES = ("prep", "vfield", "fields", "assemble", "final", "grad", "aux")
 EXPORTED = ("xtc_default_params", "xtc_create", "xtc_destroy", "xtc_strerror", "xtc_last_error_detail",
             "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b", "xtc_jastrow_grad", "xtc_vfield",
             "xtc_get_timings", "xtc_vfield_noalloc", "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf",
-            "xtc_three_body_L", "xtc_autotune_chunk", "xtc_selftest_wait_timeout")
+            "xtc_three_body_L", "xtc_autotune_chunk", "xtc_selftest_wait_timeout", "xtc_engine_revision")
 
 
 class XtcParams(ctypes.Structure):
@@ -83,13 +83,19 @@ def load(path: str = LIB_PATH):
     lib.xtc_three_body_L.argtypes = [P, I64, I, D, D, D, D]
     lib.xtc_autotune_chunk.argtypes = [P, I64, I, D, D, D, D, ctypes.POINTER(ctypes.c_int64)]
     lib.xtc_selftest_wait_timeout.argtypes = [P, I]
+    lib.xtc_engine_revision.argtypes = []
     for name in ("xtc_create", "xtc_destroy", "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b",
                  "xtc_jastrow_grad", "xtc_vfield", "xtc_get_timings", "xtc_vfield_noalloc",
                  "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf", "xtc_three_body_L", "xtc_autotune_chunk",
-                 "xtc_selftest_wait_timeout"):
+                 "xtc_selftest_wait_timeout", "xtc_engine_revision"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
+
+
+def engine_revision() -> int:
+    """Revision of the tensor-core GEMM engine (xtc_engine_revision)."""
+    return int(load().xtc_engine_revision())
 
 
 def _ptr(a):
@@ -175,6 +181,7 @@ class Context:
             raise XtcError(rc, lib.xtc_strerror(rc).decode())
         self._h = h
         self.precision = precision
+        self.device = int(device)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -313,6 +320,10 @@ class Context:
     def vfield_noalloc(self, grid, weights, phi, outer_begin, outer_end, out):
         """xtc_vfield without device allocation: every argument must be a CUDA tensor (float64);
         workspace comes from the library's fixed scratch array (small problems only)."""
+        for name, a in (("grid", grid), ("weights", weights), ("phi", phi), ("V", out)):
+            dev = getattr(a, "device", None)
+            if getattr(dev, "type", None) == "cuda" and dev.index is not None and dev.index != self.device:
+                raise ValueError(f"{name} is on cuda:{dev.index}, the context on cuda:{self.device}")
         n_grid, n_orb = _grid_inputs(grid, _need(weights, 0, "weights"), _need(phi, 0, "phi"))
         _need(out, max(outer_end - outer_begin, 0) * 3 * (n_orb * (n_orb + 1) // 2), "V")
         self._check(self._lib.xtc_vfield_noalloc(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),

@@ -1,12 +1,12 @@
 """GPU parity of the CUDA path against the CPU oracle, through the C ABI.
 
-Tolerances (Hartree): FP64 path 1e-8 absolute on every Delta U / Delta h entry and on the
-constant (observed ~1e-14 on small inputs).  Mixed paths (fp16x2, bf16x3): 1e-6 absolute, or
-1e-6 relative to the largest magnitude of that output when it exceeds 1 Eh (synthetic stress
-inputs with a dense random density reach |<L>| ~ 20 Eh).  Full-size workloads are compared on
-sampled outer points: the outputs are linear in the outer grid sum, so the GPU run restricted to
-an outer range equals the oracle restricted to the same points (full inner sum in both); whole
-grids are compared with the FP64 GPU path, itself pinned to the oracle above."""
+Tolerances, absolute in Hartree on every Delta U and Delta h entry and on the constant: FP64 path
+1e-8 Eh (observed ~1e-14 on small inputs), mixed paths (fp16x2, bf16x3) 1e-6 Eh.  Full-size
+workloads are compared on sampled outer points: the outputs are linear in the outer grid sum, so
+the GPU run restricted to an outer range equals the oracle restricted to the same points (full
+inner sum in both); whole grids are compared with the FP64 GPU path, itself pinned to the oracle
+above.  A sample of n of the N_g outer points is held to 1e-6 Eh x n / N_g: an error that grows
+with the outer sum (a one-signed rounding bias) must stay within 1e-6 Eh on the whole grid."""
 import numpy as np
 import pytest
 
@@ -26,14 +26,13 @@ def ctx_for(p, prec, **kw):
     return c
 
 
-def max_err(out, ref):
-    """Largest error over Delta U, Delta h and the constant, each divided by its allowance
-    max(1, |reference|max); compare with an absolute tolerance in Eh."""
+def max_err(out, ref, keys=("dU", "dh", "e0")):
+    """Largest absolute error (Eh) over Delta U, Delta h and the constant."""
     errs = []
-    for k in ("dU", "dh", "e0"):
+    for k in keys:
         a = np.asarray(out[k], dtype=np.float64).reshape(-1)
         b = np.asarray(ref[k], dtype=np.float64).reshape(-1)
-        errs.append(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+        errs.append(np.abs(a - b).max())
     return max(errs)
 
 
@@ -95,7 +94,9 @@ def test_chunks_splits_and_ragged_tail(small, prec):
     assert max_err(out, ref) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp16x2", pytest.param("bf16x3", marks=pytest.mark.xfail(
+    strict=True, reason="bf16x3 still accumulates in the tensor core's truncating FP32 (about 2e-7 of |<L>|, "
+                        "which is 23 Eh here); fp16x2 accumulates its hi x hi products exactly"))])
 def test_four_nuclei_full_rank_density_in_two_groups(prec):
     # rank 20 > 16 exercises the grouped factorisation of gamma
     p = synth.make_small(n_orb=20, n_rad=6, n_theta=4, n_phi=5, n_atoms=4, seed=9)
@@ -247,17 +248,23 @@ def test_water_workload_whole_grid_against_fp64_gpu(prec):
     assert max_err(out, ref) < 1e-6
 
 
-def test_n2_workload_bench_chunking_against_fp64_gpu():
-    """2,048 outer points of the N=120 workload in the chunk size the benchmark uses (9,472
-    outer points per launch), mixed against FP64."""
-    p = _sampled("n2", 2048, 13)
+def test_n2_headline_workload_10240_outer_points_against_fp64_gpu():
+    """The headline workload (N=120, 100,000 points, 7 doubly occupied) on 10,240 random outer
+    points, default fp16x2 path in the benchmark's automatic chunking against the FP64 GPU path on
+    the same points.  Both sides are linear in the outer sum, so an error that grows with it (a
+    one-signed rounding bias) scales to the whole grid by N_g / n: the tolerance is the target
+    1e-6 Eh x 10,240 / 100,000 on every Delta U and Delta h entry and on the constant."""
+    n = 10240
+    p = _sampled("n2", n, 13)
     outs = {}
     for prec in ("fp64", "fp16x2"):
-        with ctx_for(p, prec, grid_chunk=9472 if prec != "fp64" else 0) as c:
-            c.set_outer_range(0, 2048)
+        with ctx_for(p, prec) as c:
+            c.set_outer_range(0, n)
             outs[prec] = c.build(p.grid, p.weights, p.phi, p.gamma)
     ref = {"dU": outs["fp64"]["dU"], "dh": outs["fp64"]["dh"], "e0": float(outs["fp64"]["e0"][0])}
-    assert max_err(outs["fp16x2"], ref) < 1e-6
+    tol = 1e-6 * n / p.n_grid
+    errs = {k: max_err(outs["fp16x2"], ref, (k,)) for k in ("dU", "dh", "e0")}
+    assert max(errs.values()) < tol, (errs, tol)
 
 
 @pytest.mark.parametrize("prec", ["fp16x2", "bf16x3", "fp64"])
@@ -300,14 +307,23 @@ def large_sampled():
 
 @pytest.mark.parametrize("prec", ["fp16x2", "fp64"])
 def test_large_workload_sampled_outer_points(large_sampled, prec):
+    """Delta h, the constant and 200,000 sampled Delta U entries (the dense N^4 Delta U is built
+    on the device and sampled there) of the N=200 workload on 2 outer points."""
+    torch = pytest.importorskip("torch")
     p, ref = large_sampled
+    N = p.n_orb
+    dU = torch.empty((N,) * 4, dtype=torch.float64, device="cuda")
     with ctx_for(p, prec) as c:
         c.set_outer_range(0, 2)
-        out = c.build(p.grid, p.weights, p.phi, p.gamma, want_dU=False)
-    ref = {"dh": ref["dh"], "e0": ref["e0"]}
-    errs = [np.abs(np.asarray(out[k], dtype=np.float64).reshape(-1) - np.asarray(ref[k]).reshape(-1)).max()
-            / max(1.0, np.abs(np.asarray(ref[k])).max()) for k in ("dh", "e0")]
-    assert max(errs) < TOL[prec], errs
+        out = c.build(p.grid, p.weights, p.phi, p.gamma, dU=dU)
+    rng = np.random.default_rng(15)
+    idx = rng.integers(0, N, size=(4, 200_000))
+    got = dU[tuple(torch.from_numpy(i).cuda() for i in idx)].cpu().numpy()
+    del dU
+    errs = {"dU": np.abs(got - ref["dU"][tuple(idx)]).max()}
+    for k in ("dh", "e0"):
+        errs[k] = np.abs(np.asarray(out[k], dtype=np.float64).reshape(-1) - np.asarray(ref[k]).reshape(-1)).max()
+    assert max(errs.values()) < TOL[prec], errs
 
 
 def test_autotune_chunk_keeps_its_choice_and_restores_the_outer_range():
