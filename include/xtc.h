@@ -200,6 +200,14 @@ XTC_API int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* gr
  * XTC_ERR_TIMEOUT.  The context stays usable.  XTC_ERR_ARG for a limit out of range. */
 XTC_API int xtc_selftest_wait_timeout(xtc_ctx* ctx, int limit_ms);
 
+/* Self-test of the reciprocal square root and reciprocal that the tensor-core precisions use in
+ * step (a) (the unit vectors and the b = r12/(1+r12) factors of nabla_1 u): the hardware
+ * approximation refined by one Newton-Raphson step, in the packed and the scalar form.  Reads
+ * x[0..n) (positive normal FP32 values; host or device memory) and writes y_rsqrt[k] ~ 1/sqrt(x[k])
+ * and y_rcp[k] ~ 1/x[k], or NaN where the packed and scalar forms disagree.  n <= 2^26.
+ * Errors: XTC_ERR_ARG, XTC_ERR_OOM, XTC_ERR_CUDA. */
+XTC_API int xtc_selftest_reciprocals(xtc_ctx* ctx, int64_t n, const float* x, float* y_rsqrt, float* y_rcp);
+
 /* Chunk autotuner (no counterpart in the paper; the chunk is this library's streaming unit):
  * times xtc_build_1b2b on this problem's first outer points, min(n_grid, 2 x the rule's chunk) of
  * them, with up to three chunk lengths (the rule's choice, and the rule under 3/4 and 1/2 of its

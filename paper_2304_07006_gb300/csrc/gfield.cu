@@ -11,8 +11,9 @@
 //
 // One warp owns a unit of 32 outer points (one per lane, its per-point coefficients in registers)
 // and a run of inner-point blocks of 32.  For each block it evaluates the gradient in FP32 (two
-// inner points per packed FP32 instruction for up to two Jastrow centres; square roots and
-// reciprocals correctly rounded, so that no one-signed rounding bias enters the gradient), splits
+// inner points per packed FP32 instruction for up to two Jastrow centres; reciprocal square roots
+// and reciprocals refined by a Newton-Raphson step, so that no one-signed error of the hardware
+// approximations enters the gradient), splits
 // it, writes the tiles of the three components (32 rows x 128 bytes, or 3 parts x 32 rows x 64
 // bytes) into shared memory in their swizzle (conflict-free 16-byte stores) and one lane stores
 // them with TMA.  The fp16 split is exact on a per-range quantum (simt_pack.cuh): for every row and
@@ -118,13 +119,16 @@ __global__ void __launch_bounds__(GF_THREADS)
           float r2a, r2b;
           up2(r2, r2a, r2b);
           // unit vector of r1 - r2 taken as zero below 1e-14 bohr (coincident points)
-          const float ria = r2a > 1e-28f ? __frsqrt_rn(r2a) : 0.0f;
-          const float rib = r2b > 1e-28f ? __frsqrt_rn(r2b) : 0.0f;
-          const f32x2 rinv = pk2(ria, rib);
+          f32x2 rinv = rsqrt_nr2(fmaxf(r2a, 1e-28f), fmaxf(r2b, 1e-28f));
+          {
+            float ia, ib;
+            up2(rinv, ia, ib);
+            rinv = pk2(r2a > 1e-28f ? ia : 0.0f, r2b > 1e-28f ? ib : 0.0f);
+          }
           const f32x2 rr = mul2(r2, rinv);
           float ra, rb;
           up2(rr, ra, rb);
-          const f32x2 q = pk2(__frcp_rn(1.0f + ra), __frcp_rn(1.0f + rb));
+          const f32x2 q = rcp_nr2(1.0f + ra, 1.0f + rb);
           const f32x2 b = mul2(rr, q);
           const f32x2 sfac = mul2(mul2(q, q), rinv);
           f32x2 ex = fma2(b, fma2(b, PC[9], PC[6]), PC[3]);
@@ -160,9 +164,9 @@ __global__ void __launch_bounds__(GF_THREADS)
             const float dy = (pc[1] - yh) + (yl - ylo);
             const float dz = (pc[2] - zh) + (zl - zlo);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float rinv = r2 > 1e-28f ? __frsqrt_rn(r2) : 0.0f;
+            const float rinv = r2 > 1e-28f ? rsqrt_nr(r2) : 0.0f;
             const float rr = r2 * rinv;
-            const float q = __frcp_rn(1.0f + rr);
+            const float q = rcp_nr(1.0f + rr);
             const float b = rr * q;
             const float sfac = q * q * rinv;
             float ex = fmaf(b, fmaf(b, pc[9], pc[6]), pc[3]);

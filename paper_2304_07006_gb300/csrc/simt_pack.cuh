@@ -61,6 +61,41 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
+// ------------------------------------------------------------------ reciprocals
+// 1/sqrt(x) and 1/x by the hardware approximation (relative error about 2^-23) followed by one
+// Newton-Raphson step, y' = y + y (1 - x y^2) / 2 and y' = y + y (1 - x y): the step squares the
+// approximation's error, so what remains is the rounding of the last fused multiply-add, about
+// half an ulp and without the approximation's systematic part.  x must be a positive normal value.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_nr(float x) {
+  const float y = rsqrt_approx(x);
+  const float e = fmaf(-x * y, y, 1.0f);
+  return fmaf(0.5f * y, e, y);
+}
+__device__ __forceinline__ float rcp_nr(float x) {
+  const float y = rcp_approx(x);
+  return fmaf(y, fmaf(-x, y, 1.0f), y);
+}
+// The same for two values at once (packed FP32 pairs).
+__device__ __forceinline__ f32x2 rsqrt_nr2(float xa, float xb) {
+  const f32x2 y = pk2(rsqrt_approx(xa), rsqrt_approx(xb));
+  const f32x2 e = fma2(mul2(pk2(-xa, -xb), y), y, pk2(1.0f, 1.0f));
+  return fma2(mul2(pk2(0.5f, 0.5f), y), e, y);
+}
+__device__ __forceinline__ f32x2 rcp_nr2(float xa, float xb) {
+  const f32x2 y = pk2(rcp_approx(xa), rcp_approx(xb));
+  return fma2(y, fma2(pk2(-xa, -xb), y, pk2(1.0f, 1.0f)), y);
+}
+
 // ------------------------------------------------------------------ exact fp16 split
 // The fp16 operands of the tensor-core GEMMs are split as x = hi + lo with
 //     hi = k * 2^q,  k = rint(x / 2^q),  lo = fp16(x - hi),
@@ -130,7 +165,7 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 
 // 16 bytes of global memory that every lane of the warp reads at the same address (read-only path).
 __device__ __forceinline__ void ldg_2x64(const float* p, f32x2& a, f32x2& b) {
-  asm volatile("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
+  asm("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
 }
 __device__ __forceinline__ float4 ldg_f4(const float* p) {
   return __ldg(reinterpret_cast<const float4*>(p));

@@ -1090,6 +1090,25 @@ extern "C" int xtc_selftest_wait_timeout(xtc_ctx* ctx, int limit_ms) {
   return rc;
 }
 
+// ====================================================================== reciprocal self-test
+extern "C" int xtc_selftest_reciprocals(xtc_ctx* ctx, int64_t n, const float* x, float* y_rsqrt, float* y_rcp) {
+  if (!ctx) return XTC_ERR_ARG;
+  if (n < 0 || n > (int64_t(1) << 26) || (n > 0 && (!x || !y_rsqrt || !y_rcp)))
+    return fail(ctx, XTC_ERR_ARG, "selftest_reciprocals: bad arguments");
+  if (n == 0) return XTC_OK;
+  CUDA_OK(cudaSetDevice(ctx->prm.device));
+  const size_t bytes = static_cast<size_t>(n) * sizeof(float);
+  if (!ensure(ctx->r1, bytes) || !ensure(ctx->r2, 2 * bytes)) return fail(ctx, XTC_ERR_OOM, "selftest buffers");
+  cudaStream_t st = ctx->st;
+  CUDA_OK(cudaMemcpyAsync(ctx->r1.p, x, bytes, cudaMemcpyDefault, st));
+  launch_recip_selftest(ctx->r1.as<float>(), n, ctx->r2.as<float>(), ctx->r2.as<float>() + n, st);
+  CUDA_OK(cudaGetLastError());
+  CUDA_OK(cudaMemcpyAsync(y_rsqrt, ctx->r2.as<float>(), bytes, cudaMemcpyDefault, st));
+  CUDA_OK(cudaMemcpyAsync(y_rcp, ctx->r2.as<float>() + n, bytes, cudaMemcpyDefault, st));
+  CUDA_OK(cudaStreamSynchronize(st));
+  return XTC_OK;
+}
+
 // ====================================================================== chunk autotuner
 // Times the build on the first outer points of this problem with up to three chunk lengths (the
 // rule's choice and the rule under 3/4 and 1/2 of its memory budgets) and keeps the fastest in

@@ -52,6 +52,8 @@ constexpr int DEV_ERR_TIMEOUT_SELFTEST = 3;
 // Self-test of the bounded waits: one CTA waits on an mbarrier that nothing arrives on, with the
 // kernels' own wait routine and a limit of limit_ns, and records DEV_ERR_TIMEOUT_SELFTEST in err.
 void launch_wait_timeout_selftest(int* err, unsigned long long limit_ns, cudaStream_t st);
+// Self-test of the gradient kernel's refined 1/sqrt(x) and 1/x (simt_pack.cuh) on x[0..n).
+void launch_recip_selftest(const float* x, int64_t n, float* y_rsqrt, float* y_rcp, cudaStream_t st);
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // Row stride of the FP64 accumulator M[pq][rs]: a multiple of 32 (the bf16 step (d) kernel writes

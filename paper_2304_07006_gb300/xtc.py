@@ -21,7 +21,8 @@ KERNEL_NAMES = ("prep", "vfield", "fields", "assemble", "final", "grad", "aux")
 EXPORTED = ("xtc_default_params", "xtc_create", "xtc_destroy", "xtc_strerror", "xtc_last_error_detail",
             "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b", "xtc_jastrow_grad", "xtc_vfield",
             "xtc_get_timings", "xtc_vfield_noalloc", "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf",
-            "xtc_three_body_L", "xtc_autotune_chunk", "xtc_selftest_wait_timeout", "xtc_engine_revision")
+            "xtc_three_body_L", "xtc_autotune_chunk", "xtc_selftest_wait_timeout", "xtc_engine_revision",
+            "xtc_selftest_reciprocals")
 
 
 class XtcParams(ctypes.Structure):
@@ -84,10 +85,11 @@ def load(path: str = LIB_PATH):
     lib.xtc_autotune_chunk.argtypes = [P, I64, I, D, D, D, D, ctypes.POINTER(ctypes.c_int64)]
     lib.xtc_selftest_wait_timeout.argtypes = [P, I]
     lib.xtc_engine_revision.argtypes = []
+    lib.xtc_selftest_reciprocals.argtypes = [P, I64, D, D, D]
     for name in ("xtc_create", "xtc_destroy", "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b",
                  "xtc_jastrow_grad", "xtc_vfield", "xtc_get_timings", "xtc_vfield_noalloc",
                  "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf", "xtc_three_body_L", "xtc_autotune_chunk",
-                 "xtc_selftest_wait_timeout", "xtc_engine_revision"):
+                 "xtc_selftest_wait_timeout", "xtc_engine_revision", "xtc_selftest_reciprocals"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -267,6 +269,13 @@ class Context:
             _ptr(res["dU_aa"]), _ptr(res["dU_ab"]), _ptr(res["dU_bb"]), _ptr(res["dh_a"]), _ptr(res["dh_b"]),
             _ptr(res["e0"])))
         return res
+
+    def selftest_reciprocals(self, x):
+        """The refined 1/sqrt(x) and 1/x of the step (a) kernel on float32 x (xtc_selftest_reciprocals)."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        ys, yr = np.empty_like(x), np.empty_like(x)
+        self._check(self._lib.xtc_selftest_reciprocals(self._h, int(x.size), _ptr(x), _ptr(ys), _ptr(yr)))
+        return ys, yr
 
     def selftest_wait_timeout(self, limit_ms=50):
         """Runs one bounded device wait that must time out; returns the status (XTC_ERR_TIMEOUT)."""

@@ -76,3 +76,24 @@ def test_caller_allocator_refusal_is_reported_as_out_of_memory(small):
             c.build(p.grid, p.weights, p.phi, p.gamma)
         assert e.value.code == -4                              # XTC_ERR_OOM
     assert not live
+
+
+def test_refined_reciprocals_are_within_one_ulp_and_unbiased():
+    """Step (a) of the tensor-core precisions takes 1/sqrt(x) and 1/x as the hardware approximation
+    plus one Newton-Raphson step.  Against correctly rounded FP32 values (from FP64): at most one
+    ulp off, and the signed errors average out (a one-signed error would bias the gradient, and
+    with it every output, by the same relative amount)."""
+    from paper_2304_07006_gb300 import Context
+    rng = np.random.default_rng(3)
+    # squared distances and 1 + distances as the gradient meets them: 1e-20 .. 1e4 bohr^2, 1 .. 100
+    x = np.concatenate([10.0 ** rng.uniform(-20, 4, 2_000_000), rng.uniform(1.0, 100.0, 2_000_000)]).astype(np.float32)
+    with Context("fp16x2") as c:
+        ys, yr = c.selftest_reciprocals(x)
+    assert np.isfinite(ys).all() and np.isfinite(yr).all()        # packed and scalar forms agree
+    xd = x.astype(np.float64)
+    for got, exact in ((ys, 1.0 / np.sqrt(xd)), (yr, 1.0 / xd)):
+        want = exact.astype(np.float32)                           # correctly rounded
+        ulp = np.spacing(np.abs(want)).astype(np.float64)
+        err = (got.astype(np.float64) - exact) / ulp
+        assert (np.abs(got.astype(np.float64) - want.astype(np.float64)) <= ulp).all(), "more than one ulp"
+        assert abs(err.mean()) < 0.01, err.mean()                 # no systematic part
