@@ -250,6 +250,36 @@ def rohf_measure(args, torch, dev, local, p, s_closed):
             "per_kernel_ms": per, "note": "inputs and outputs on the device; Delta U not unpacked"}
 
 
+def fullrank_measure(args, torch, dev, local, p, per_kernel_closed):
+    """The N=120 workload with a random full-rank density (eigenvalues in [0.05, 1], a random
+    eigenbasis: a correlated-density stand-in): one warm-up and one timed build, inputs and outputs
+    on the device, Delta U formed but not unpacked; step (d) time against the rank-7 build's."""
+    import synth
+    from paper_2304_07006_gb300 import Context
+
+    N = p.n_orb
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    grid, w, phi = t(p.grid), t(p.weights), t(p.phi)
+    gam = t(synth.random_density(N, 120))
+    dh = torch.empty((N, N), dtype=torch.float64, device=dev)
+    e0 = torch.empty(1, dtype=torch.float64, device=dev)
+    with Context(args.precision, device=local, timing=True) as c:
+        c.set_jastrow(p.nuc_xyz, p.nuc_set, p.terms, p.coef)
+        c.build(grid, w, phi, gam, dh=dh, e0=e0, want_dU=False)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        c.build(grid, w, phi, gam, dh=dh, e0=e0, want_dU=False)
+        torch.cuda.synchronize(dev)
+        sec = time.perf_counter() - t0
+        tm = c.timings()
+    d_ms = tm["assemble"][0] + tm["aux"][0]
+    d_closed = per_kernel_closed["assemble"]["ms_per_step"] + per_kernel_closed["aux"]["ms_per_step"]
+    return {"density": f"random, rank {N} ({(N + 15) // 16} groups of factors in step (c))", "seconds_per_build": sec,
+            "fields_ms": tm["fields"][0], "step_d_ms": d_ms, "step_d_vs_rank7_build": d_ms / d_closed,
+            "note": "wall time of one build, inputs on the device, Delta U not unpacked; step_d_ms = the step (d) "
+                    "GEMM with its row splits and adds into M (aux also holds the V writes of step (b))"}
+
+
 def large_measure(args, torch, dev, local):
     """The large workload (4 heavy atoms + 4 H, N=200, 200,000 grid points, 8 Jastrow centres in
     2 sets, 14 doubly occupied orbitals): one warm-up and one timed build (CUDA events), inputs and
@@ -504,6 +534,7 @@ def main():
         if args.rohf:
             line["rohf"] = rohf_measure(args, torch, dev, local, p, ms_step / 1e3)
         line["three_body_L"] = three_body_measure(args, torch, dev, local)
+        line["full_rank_density"] = fullrank_measure(args, torch, dev, local, p, per_kernel)
         if args.large:
             free, _ = torch.cuda.mem_get_info(dev)
             line["large"] = (large_measure(args, torch, dev, local) if free > 100e9

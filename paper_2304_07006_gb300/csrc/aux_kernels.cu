@@ -102,7 +102,8 @@ __device__ __forceinline__ int col_exponent(const unsigned int* colmax, int pq, 
 // fp16 (2 parts, exact split): warp w of the CTA handles pair pq = 8 * blockIdx.y + w over one
 // accumulation range of the GEMM, points j0 + lane + 32 s (s < kd, j0 = 32 kd blockIdx.x); the
 // range shares one quantum (largest |value| of the range, `bits` bits).  Layout: the two parts of a
-// 32-point block share one 128-byte row, [pq][j / 32][part][j % 32].
+// 32-point block share one 128-byte row, [pq][j / 32][part][j % 32]; then the plane [pq][j] of the
+// value rounded to fp16.
 __global__ void rho_split_f16_kernel(const double* __restrict__ phiT, const double* __restrict__ w, int64_t n_grid,
                                      int64_t n_pad, int n_pair, const int* __restrict__ pp,
                                      const int* __restrict__ pq_, const unsigned int* __restrict__ colmax, int kd,
@@ -124,6 +125,7 @@ __global__ void rho_split_f16_kernel(const double* __restrict__ phiT, const doub
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   const int qe = exact_quantum(m, bits);
+  uint16_t* out16 = out + static_cast<int64_t>(n_pair) * 2 * n_pad;  // the fp16(rho) plane
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const int64_t j = j0 + 32 * s + lane;
@@ -133,6 +135,7 @@ __global__ void rho_split_f16_kernel(const double* __restrict__ phiT, const doub
     const int64_t o = static_cast<int64_t>(pq) * 2 * n_pad + (j >> 5) * 64 + (j & 31);
     out[o] = __half_as_ushort(h);
     out[o + 32] = __half_as_ushort(l);
+    out16[static_cast<int64_t>(pq) * n_pad + j] = __half_as_ushort(__double2half(v[s]));
   }
 }
 

@@ -20,7 +20,10 @@
 // A CTA owns `pts` consecutive outer points (lane-contiguous, so every global read of V is a
 // contiguous run of the outer index) and all orbital pairs; H for its points lives in shared
 // memory.  Outputs, per point and pair, are L = (rho, Vx, Vy, Vz) and R = (A, Bx, By, Bz), written
-// as the K-major operands of step (d): three bf16 parts [part][pq][4*gcp] or FP64 [4*gcp][pq].
+// as the operands of step (d): FP32 rows [pq][4*gcp], FP64 [4*gcp][pq] or three bf16 parts
+// [part][pq][4*gcp].  L does not depend on the density and R is linear in its factors, so a
+// density of more factors than one pass holds runs several passes: the first writes L and R, the
+// next ones add their R (FP32 and FP64 outputs).
 // Points past the chunk end are written as zeros.
 #include <cuda_bf16.h>
 
@@ -88,18 +91,31 @@ __device__ __forceinline__ void split3_bf16(float v, __nv_bfloat16& h, __nv_bflo
   l = __float2bfloat16_rn(r1 - __bfloat162float(m));
 }
 
+// add: FP64 and FP32 outputs are added to what the buffer holds (the R of a further group of
+// density factors; R is linear in the factors), else stored.
 template <typename TC, int OUT_PARTS>
 __device__ __forceinline__ void write4(void* base, int64_t n_pair, int64_t gcp, int q, int64_t il,
-                                       const TC (&v)[4]) {
+                                       const TC (&v)[4], bool add = false) {
   if (OUT_PARTS == 0) {
     double* o = static_cast<double*>(base);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) o[(4 * il + c) * n_pair + q] = static_cast<double>(v[c]);
+    for (int c = 0; c < 4; ++c) {
+      double* e = o + (4 * il + c) * n_pair + q;
+      *e = add ? *e + static_cast<double>(v[c]) : static_cast<double>(v[c]);
+    }
   } else if (OUT_PARTS == 1) {
     // FP32 rows [pq][4*gcp] (split afterwards with a per-row scale)
     float* o = static_cast<float*>(base) + static_cast<int64_t>(q) * 4 * gcp + 4 * il;
-    *reinterpret_cast<float4*>(o) = make_float4(static_cast<float>(v[0]), static_cast<float>(v[1]),
-                                                static_cast<float>(v[2]), static_cast<float>(v[3]));
+    float4 w = make_float4(static_cast<float>(v[0]), static_cast<float>(v[1]), static_cast<float>(v[2]),
+                           static_cast<float>(v[3]));
+    if (add) {
+      const float4 old = *reinterpret_cast<const float4*>(o);
+      w.x += old.x;
+      w.y += old.y;
+      w.z += old.z;
+      w.w += old.w;
+    }
+    *reinterpret_cast<float4*>(o) = w;
   } else {
     __nv_bfloat16* o = static_cast<__nv_bfloat16*>(base);
     __nv_bfloat16 h[4], m[4], l[4];
@@ -265,9 +281,9 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
         }
       }
     }
-    write4<TC, OUT_PARTS>(a.L, a.n_pair, a.gcp, q, il, Lv);
-    write4<TC, OUT_PARTS>(a.R, a.n_pair, a.gcp, q, il, Rv);
-    if (SPIN) write4<TC, OUT_PARTS>(a.R2, a.n_pair, a.gcp, q, il, R2v);
+    if (a.write_L) write4<TC, OUT_PARTS>(a.L, a.n_pair, a.gcp, q, il, Lv);
+    write4<TC, OUT_PARTS>(a.R, a.n_pair, a.gcp, q, il, Rv, a.add_R);
+    if (SPIN) write4<TC, OUT_PARTS>(a.R2, a.n_pair, a.gcp, q, il, R2v, a.add_R);
   }
 }
 

@@ -144,7 +144,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     } else {
       c.take<double>(static_cast<size_t>(N) * NGp);
       c.take<float>(static_cast<size_t>(NGp) * jtab_stride(n_nuc));
-      c.take<uint16_t>(static_cast<size_t>(parts) * NP * NGp);
+      c.take<uint16_t>(static_cast<size_t>(3) * NP * NGp);
       c.take<unsigned int>(NP);
       c.take<int>(NP);
       c.take<float>(static_cast<size_t>(NP) * 3 * gc);
@@ -172,7 +172,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: clearing the error word failed");
   pair_table_kernel<<<N, 128, 0, st>>>(N, pair_p, pair_q);
 
-  CUtensorMap tm{}, tm_gs{}, tm_gl{};
+  CUtensorMap tm{}, tm16{}, tm_gs{}, tm_gl{};
   double* jtab64 = nullptr;
   double* rho64 = nullptr;
   float* jtab = nullptr;
@@ -188,7 +188,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
   } else {
     double* phiT = cz.take<double>(static_cast<size_t>(N) * NGp);
     jtab = cz.take<float>(static_cast<size_t>(NGp) * jtab_stride(n_nuc));
-    rho = cz.take<uint16_t>(static_cast<size_t>(parts) * NP * NGp);
+    rho = cz.take<uint16_t>(static_cast<size_t>(3) * NP * NGp);  // fp16: split rows + fp16 plane
     unsigned int* colmax = cz.take<unsigned int>(NP);
     colexp = cz.take<int>(NP);
     Vbuf = cz.take<float>(static_cast<size_t>(NP) * 3 * gc);
@@ -215,6 +215,17 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     };
     if (!map(&tm, rho, NP, vf_bn(parts)) || !map(&tm_gs, G, 3 * gc, 32) || !map(&tm_gl, G, 3 * gc, VF_BM))
       return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: cuTensorMapEncodeTiled failed");
+    if (wide) {
+      // the fp16(rho^T) plane after the split rows: [pq][j], boxes 32 x vf_bn (64-byte swizzle)
+      const cuuint64_t dims[3] = {static_cast<cuuint64_t>(NGp), static_cast<cuuint64_t>(NP), 1};
+      const cuuint64_t strides[2] = {static_cast<cuuint64_t>(NGp) * 2, static_cast<cuuint64_t>(NGp) * NP * 2};
+      const cuuint32_t box[3] = {static_cast<cuuint32_t>(VF_BK), static_cast<cuuint32_t>(vf_bn(2)), 1};
+      const cuuint32_t es[3] = {1, 1, 1};
+      if (encode(&tm16, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, static_cast<uint16_t*>(rho) + 2 * static_cast<size_t>(NP) * NGp,
+                 dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: cuTensorMapEncodeTiled failed");
+    }
   }
 
   // ---- chunks of outer points: steps (a)+(b), then V -> caller's buffer [k][x][pq] (FP64)
@@ -260,7 +271,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
       a.xper = 64;
       a.unscale_g = std::ldexp(1.0f, -sg);
       a.err = err;
-      launch_vfield_tc(&tm_gl, &tm, a, parts, 1, st);
+      launch_vfield_tc(&tm_gl, &tm, &tm16, a, parts, 1, st);
     }
     launch_vfield_export(Vbuf, f64, 1, NP, n_i, gc, V + (c0 - outer_begin) * 3 * NP, st);
   }

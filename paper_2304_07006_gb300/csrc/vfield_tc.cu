@@ -15,20 +15,23 @@
 // The tensor core's FP32 accumulator truncates toward zero at every MMA, which biases a long sum
 // by a relative ~2^-24 per MMA, always toward zero; the hi x hi sums of a range are exact, so they
 // go, one range at a time, into an accumulator E, which the drain warps add into FP32 running sums
-// (round to nearest) after every range.  The cross products hi x lo and lo x hi (about 2^-9 of the
-// total, signs that follow the rounding remainders rather than the data) go into a second
-// accumulator X, drained every `xper` stages; their truncation is 2^-9 smaller and does not
-// accumulate one-sided.  lo x lo is dropped (it matters only for values far below their range's
-// maximum in both operands; measured on the whole N=120 workload it moves no output by more than
-// 1e-8 Eh).
+// (round to nearest) after every range.  The cross products (about 2^-9 of the total, signs that
+// follow the rounding remainders rather than the data) go into a second accumulator X, drained
+// every `xper` stages; their truncation is 2^-9 smaller and does not accumulate one-sided.  They
+// must include lo_a x lo_b: where both operands hold values far below their range's maximum, hi is
+// 0 and lo is the whole value.  Step (d) issues hi_a x lo_b, lo_a x hi_b and lo_a x lo_b.  Step (b)
+// issues hi_a x lo_b and lo_a x fp16(b), with fp16(b) a third plane of rho^T: lo_a x (hi_b + lo_b)
+// to within fp16's rounding of b (a relative 2^-12 of a term that is itself 2^-10 of the product),
+// one product where two would be needed.
 //
 // Tile 128 A rows x 128 columns, 32 K values per stage, both parts of a row of a block in one
-// 128-byte row (128-byte swizzle; one TMA box per operand and stage), 7 stages of 32 KB.  Measured
+// 128-byte row (128-byte swizzle; one TMA box per operand part and stage).  Measured
 // on GB300: one thread issues a 128 x 128 x 16 MMA every ~50 cycles (the pipe takes 64), an MMA
 // and its commit round-trip in ~360 cycles, and a range's round trip (its MMAs complete, the
 // commit arrives, the drains read E, E is handed back) takes on the order of a thousand cycles.
-// So ranges span two stages (12 MMAs), and two issuers alternate ranges, each with its own
-// accumulator pair (TMEM: E0, X0, E1, X1 = 4 x 128 of 512 columns).  Warp roles:
+// So ranges span two stages (12 MMAs, 16 in step (d)), and two issuers alternate ranges, each with
+// its own accumulator pair (TMEM: E0, X0, E1, X1 = 4 x 128 of 512 columns).  Step (b) stages hold
+// 40 KB (A, B hi/lo, fp16(B): 5 stages), step (d) stages 32 KB (7 stages).  Warp roles:
 //   * warp 0 (one lane): TMA loads; a range's slots are reloaded once its commit has arrived;
 //   * warps 1 and 2 (one lane each): the MMAs of the even / odd ranges, one commit per range;
 //   * warps 3..18: after every range, drains of E_k, and every `xper` stages of X_k, into FP32
@@ -86,15 +89,19 @@ constexpr int XB_DRAIN_WARPS = 16;                // four per TMEM lane quarter,
 constexpr int XB_HC = XB_BN / 4;                  // running-sum columns per drain thread
 constexpr int XB_A_BYTES = VF_BM * 128;           // 128 rows of 128 bytes (hi and lo of 32 values)
 constexpr int XB_B_BYTES = XB_BN * 128;
-constexpr int XB_STAGE = XB_A_BYTES + XB_B_BYTES; // 32 KB, a multiple of the 1024-byte swizzle atom
-constexpr int XB_STAGES = 7;
+constexpr int XB_B16_BYTES = XB_BN * 64;          // step (b): fp16(rho) of the B rows, 64-byte rows
+// stage bytes and pipeline depth: step (b) 40 KB (A, B hi/lo, B fp16) x 5, step (d) 32 KB x 7
+__host__ __device__ constexpr int xb_stage(int mode) { return XB_A_BYTES + XB_B_BYTES + (mode == 0 ? XB_B16_BYTES : 0); }
+__host__ __device__ constexpr int xb_stages(int mode) { return mode == 0 ? 5 : 7; }
+constexpr int XB_STAGES = 7;                      // the larger depth (barrier arrays)
 constexpr int XB_WARP_I0 = 1, XB_WARP_I1 = 2;      // issuers of the even / odd ranges; drains 3..18
 constexpr int XB_THREADS = (3 + XB_DRAIN_WARPS) * 32;  // TMA warp, two MMA warps, drains
-constexpr int XB_SMEM = XB_STAGES * XB_STAGE + 1024 + 256;  // + alignment slack, barriers
+__host__ __device__ constexpr int xb_smem(int mode) { return xb_stages(mode) * xb_stage(mode) + 1024 + 256; }
 static_assert(XB_BN == vf_bn(2), "tile width of the fp16 engine");
 static_assert(4 * XB_BN <= 512, "E0, X0, E1, X1 in 512 TMEM columns");
 static_assert(XB_HC == 32, "drain columns per thread (one 32-column load)");
-static_assert(XB_SMEM <= 232448, "shared memory per CTA");
+static_assert(xb_smem(0) <= 232448 && xb_smem(1) <= 232448, "shared memory per CTA");
+static_assert(xb_stages(0) <= XB_STAGES && xb_stages(1) <= XB_STAGES, "barrier arrays");
 // a wait for range r must not alias range r + NRB: the producer waits for the range of stage
 // k - XB_STAGES before loading stage k, and range r + NRB starts past stage k
 static_assert(NRB > XB_STAGES, "range barriers");
@@ -104,14 +111,17 @@ static_assert((XB_STAGES + NRB + 5) * 8 + 8 <= 256, "barrier area");
 // below 2^18: the constant fields plus the address in 16-byte units (a plain add per stage and
 // K step, no re-encoding in the issue loop).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) { return sdesc_kmajor_sw128(0) + (saddr >> 4); }
+// The same for 64-byte rows in the 64-byte swizzle.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) { return sdesc_kmajor_sw64(0) + (saddr >> 4); }
 
 template <int MODE>
 __global__ void __launch_bounds__(XB_THREADS, 1)
     xgemm_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
-                 const VfieldArgs args) {
+                 const __grid_constant__ CUtensorMap tm_b16, const VfieldArgs args) {
+  constexpr int XB_STAGE = xb_stage(MODE), STAGES = xb_stages(MODE);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + XB_STAGES * XB_STAGE);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * XB_STAGE);
   uint64_t* tma_full = bars;                  // [XB_STAGES] the stage's loads landed
   uint64_t* rdone = bars + XB_STAGES;         // [NRB] every MMA of range r (r % NRB) completed
   uint64_t* e_free = rdone + NRB;             // [2] the drains released E_k (issuer k)
@@ -136,7 +146,7 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
   const int xr = max(1, args.xper / (2 * kd));             // ranges of one issuer per X drain
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < XB_STAGES; ++s) mbar_init(&tma_full[s], 1);
+    for (int s = 0; s < STAGES; ++s) mbar_init(&tma_full[s], 1);
     for (int r = 0; r < NRB; ++r) mbar_init(&rdone[r], 1);
     for (int k = 0; k < 2; ++k) {
       mbar_init(&e_free[k], XB_DRAIN_WARPS);
@@ -147,6 +157,7 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
     fence_mbar_init();
     tma_prefetch_desc(&tm_a);
     tma_prefetch_desc(&tm_b);
+    if (MODE == 0) tma_prefetch_desc(&tm_b16);
   }
   if (warp == 0) {
     tmem_alloc(tmem_slot, 512);
@@ -164,9 +175,9 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
       int seen = 0;  // ranges known to have completed (their slots are free again)
       int issued = 0;
       for (int it = 0; it < n_it; ++it) {
-        const int s = it % XB_STAGES;
-        if (it >= XB_STAGES) {
-          const int need = (it - XB_STAGES) / kd;  // range holding the slot's previous stage
+        const int s = it % STAGES;
+        if (it >= STAGES) {
+          const int need = (it - STAGES) / kd;  // range holding the slot's previous stage
           bool ok = true;
           for (; seen <= need && ok; ++seen)
             ok = mbar_wait(&rdone[seen % NRB], (seen / NRB) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF);
@@ -176,21 +187,23 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
         uint8_t* st = smem + s * XB_STAGE;
         tma_load_3d(st, &tm_a, &tma_full[s], (kb0 + it) * 2 * VF_BK, row0, 0);
         tma_load_3d(st + XB_A_BYTES, &tm_b, &tma_full[s], (kb0 + it) * 2 * VF_BK, t.n_tile * XB_BN, 0);
+        if (MODE == 0)
+          tma_load_3d(st + XB_A_BYTES + XB_B_BYTES, &tm_b16, &tma_full[s], (kb0 + it) * VF_BK, t.n_tile * XB_BN, 0);
         issued = it + 1;
       }
       // the copies still in flight land before the CTA may exit
       int zero = 0;
-      for (int it = max(0, issued - XB_STAGES); it < issued; ++it)
-        mbar_wait(&tma_full[it % XB_STAGES], (it / XB_STAGES) & 1, reinterpret_cast<volatile int*>(&zero),
+      for (int it = max(0, issued - STAGES); it < issued; ++it)
+        mbar_wait(&tma_full[it % STAGES], (it / STAGES) & 1, reinterpret_cast<volatile int*>(&zero),
                   args.err, DEV_ERR_TIMEOUT_VF);
     }
   } else if (warp == XB_WARP_I0 || warp == XB_WARP_I1) {
     if (lane == 0) {
       // ---------------------------------------------------------------- MMA issuers
       // Issuer k takes the ranges r = k, k + 2, ...: per stage the hi x hi products into E_k (a
-      // fresh, exact accumulation per range) and the cross products lo x hi and hi x lo into X_k
-      // (restarted every xr of its ranges); one commit per range, whose arrival frees the range's
-      // slots and starts the drains.  With two issuers one's waits and commit
+      // fresh, exact accumulation per range) and the cross products lo x hi, hi x lo (and in step
+      // (d) lo x lo) into X_k (restarted every xr of its ranges); one commit per range, whose
+      // arrival frees the range's slots and starts the drains.  With two issuers one's waits and commit
       // overlap the other's MMAs, and neither waits for the other's drains.
       constexpr uint32_t idesc = idesc_f16(VF_BM, XB_BN, false);
       const int k = warp == XB_WARP_I0 ? 0 : 1;
@@ -204,18 +217,28 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
           break;
         bool alive = true;
         for (int it = it0; it < it1; ++it) {
-          const int s = it % XB_STAGES;
-          if (!(alive = mbar_spin(&tma_full[s], (it / XB_STAGES) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)))
+          const int s = it % STAGES;
+          if (!(alive = mbar_spin(&tma_full[s], (it / STAGES) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF)))
             break;
           tc_fence_after();
-          const uint64_t da = sw128_desc(smem_base + s * XB_STAGE), db = da + (XB_A_BYTES >> 4);
+          const uint32_t sa = smem_base + s * XB_STAGE;
+          const uint64_t da = sw128_desc(sa), db = da + (XB_A_BYTES >> 4);
           // K steps of 16 values advance 32 bytes (2 descriptor units); lo parts sit 64 bytes on
           tc_mma_f16(e_tmem, da, db, idesc, it > it0 ? 1u : 0u);
           tc_mma_f16(e_tmem, da + 2, db + 2, idesc, 1u);
-          tc_mma_f16(x_tmem, da + 4, db, idesc, (x_start && it == it0) ? 0u : 1u);
-          tc_mma_f16(x_tmem, da + 6, db + 2, idesc, 1u);
-          tc_mma_f16(x_tmem, da, db + 4, idesc, 1u);
+          tc_mma_f16(x_tmem, da, db + 4, idesc, (x_start && it == it0) ? 0u : 1u);   // hi_a x lo_b
           tc_mma_f16(x_tmem, da + 2, db + 6, idesc, 1u);
+          if (MODE == 0) {
+            // lo_a x fp16(b): lo_a x (hi_b + lo_b) to within fp16(b)'s rounding, one product
+            const uint64_t d16 = sw64_desc(sa + XB_A_BYTES + XB_B_BYTES);
+            tc_mma_f16(x_tmem, da + 4, d16, idesc, 1u);
+            tc_mma_f16(x_tmem, da + 6, d16 + 2, idesc, 1u);
+          } else {
+            tc_mma_f16(x_tmem, da + 4, db, idesc, 1u);                                 // lo_a x hi_b
+            tc_mma_f16(x_tmem, da + 6, db + 2, idesc, 1u);
+            tc_mma_f16(x_tmem, da + 4, db + 4, idesc, 1u);                             // lo_a x lo_b
+            tc_mma_f16(x_tmem, da + 6, db + 6, idesc, 1u);
+          }
         }
         if (!alive) break;
         tc_commit(&rdone[r % NRB]);
@@ -576,15 +599,17 @@ int m_tiles_of(const VfieldArgs& a) { return a.mode == 0 ? 3 * a.mt_per_x : (a.r
 
 bool vfield_tc_supported(int n_nuc) { return n_nuc >= 1 && n_nuc <= 8; }
 
-void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int parts,
-                      int splits, cudaStream_t st) {
+void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const CUtensorMap* tm_rho16,
+                      const VfieldArgs& a, int parts, int splits, cudaStream_t st) {
   if (a.n_tiles <= 0 || splits <= 0) return;
   if (a.mode == 1 ? a.rows_a <= 0 : a.mt_per_x <= 0) return;
   dim3 grid(static_cast<unsigned>(m_tiles_of(a) * a.n_tiles), static_cast<unsigned>(splits));
-  if (a.mode == 1 || parts == 2) {
-    auto kern = a.mode == 1 ? xgemm_kernel<1> : xgemm_kernel<0>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, XB_SMEM);
-    kern<<<grid, XB_THREADS, XB_SMEM, st>>>(*tm_g, *tm_rho, a);
+  if (a.mode == 1) {
+    cudaFuncSetAttribute(xgemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, xb_smem(1));
+    xgemm_kernel<1><<<grid, XB_THREADS, xb_smem(1), st>>>(*tm_g, *tm_rho, *tm_rho, a);
+  } else if (parts == 2) {
+    cudaFuncSetAttribute(xgemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, xb_smem(0));
+    xgemm_kernel<0><<<grid, XB_THREADS, xb_smem(0), st>>>(*tm_g, *tm_rho, *tm_rho16, a);
   } else {
     cudaFuncSetAttribute(vfield_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BF_SMEM);
     vfield_bf16_kernel<<<grid, BF_THREADS, BF_SMEM, st>>>(*tm_g, *tm_rho, a);

@@ -538,9 +538,9 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
   } else {
     const int js = jtab_stride(n_nuc);
     if (!ensure(ctx->jtab, sizeof(float) * pl.NGp * js) ||
-        !ensure(ctx->rho, 2ull * pl.parts_b * pl.NGp * pl.NP) || !ensure(ctx->colmax, 4ull * pl.NP) ||
+        !ensure(ctx->rho, 2ull * 3 * pl.NGp * pl.NP) || !ensure(ctx->colmax, 4ull * pl.NP) ||
         !ensure(ctx->colexp, 4ull * pl.NP))
-      return fail(ctx, XTC_ERR_OOM, "grid tables (%.2f GB)", 2.0 * pl.parts_b * pl.NGp * pl.NP / 1e9);
+      return fail(ctx, XTC_ERR_OOM, "grid tables (%.2f GB)", 2.0 * 3 * pl.NGp * pl.NP / 1e9);
   }
   const int nprep = f64 ? 3 : (pl.parts_b == 2 ? 4 : 3);
   timed(ctx, XTC_K_PREP, nprep, [&] {
@@ -576,7 +576,7 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
 // block in one 128-byte row (rows of 2 NGp values, boxes 64 wide, 128-byte swizzle); bf16: one
 // plane per part (rows of NGp values, boxes 32 wide, 64-byte swizzle).
 struct VfMaps {
-  CUtensorMap rho, g_store, g_load;
+  CUtensorMap rho, rho16, g_store, g_load;
 };
 int make_vfield_maps(xtc_ctx* ctx, const Plan& pl, VfMaps& m) {
   if (pl.f64) return XTC_OK;
@@ -585,6 +585,10 @@ int make_vfield_maps(xtc_ctx* ctx, const Plan& pl, VfMaps& m) {
   const uint32_t bk = wide ? 2 * VF_BK : VF_BK;
   int rc;
   if ((rc = make_tmap_3d(ctx, &m.rho, ctx->rho.p, bf, cols, pl.NP, planes, bk, vf_bn(pl.parts_b), wide))) return rc;
+  // fp16: the plane of fp16(rho^T) after the split rows, boxes 32 wide (64-byte swizzle)
+  if (wide && (rc = make_tmap_3d(ctx, &m.rho16, ctx->rho.as<uint16_t>() + 2 * pl.NP * pl.NGp, false, pl.NGp, pl.NP, 1,
+                                 VF_BK, vf_bn(2))))
+    return rc;
   if ((rc = make_tmap_3d(ctx, &m.g_store, ctx->G.p, bf, cols, 3 * pl.gc, planes, bk, 32, wide))) return rc;
   return make_tmap_3d(ctx, &m.g_load, ctx->G.p, bf, cols, 3 * pl.gc, planes, bk, VF_BM, wide);
 }
@@ -641,7 +645,7 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   a.err = ctx->err_dev.as<int>();
   const int splits = (a.n_kb + a.kb_per_split - 1) / a.kb_per_split;  // every slice non-empty
   // the GEMM, then (FP64 flushes) the kernel that writes V from the FP64 sums
-  timed(ctx, XTC_K_VFIELD, 1, [&] { launch_vfield_tc(&maps.g_load, &maps.rho, a, pl.parts_b, splits, st); });
+  timed(ctx, XTC_K_VFIELD, 1, [&] { launch_vfield_tc(&maps.g_load, &maps.rho, &maps.rho16, a, pl.parts_b, splits, st); });
   if (a.flush > 0) timed(ctx, XTC_K_AUX, 1, [&] { launch_vfield_tc_finalize(a, pl.parts_b, splits, st); });
   return XTC_OK;
 }
@@ -837,6 +841,10 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
       const int groups = std::max(1, (ps.rank + RANK_GROUP - 1) / RANK_GROUP);
       double* M = ps.M->as<double>();
       double* M2 = ps.M2 ? ps.M2->as<double>() : nullptr;
+      // L does not depend on the density and R is linear in its factors: with FP32 or FP64
+      // operands step (c) runs once per group of factors, adding into R, and step (d) once per
+      // chunk; the bf16 x3 operands (split in step (c)) take one step (d) per group
+      const bool accum = pl.f64 || d16;
       for (int gi = 0; gi < groups; ++gi) {
         const int k0 = ps.k0 + gi * RANK_GROUP;
         const int rg = std::max(0, std::min(RANK_GROUP, ps.rank - gi * RANK_GROUP));
@@ -863,52 +871,55 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
         fa.R2 = M2 ? (d16 ? ctx->R32b.p : ctx->R2.p) : nullptr;
         fa.lam2 = M2 ? ctx->lam2.as<double>() + k0 : nullptr;
         fa.out_parts = pl.f64 ? 0 : (d16 ? 1 : 3);
+        fa.write_L = (!accum || gi == 0) ? 1 : 0;
+        fa.add_R = (accum && gi > 0) ? 1 : 0;
         timed(ctx, XTC_K_FIELDS, 1, [&] { launch_fields(fa, pl.f64, st); });
-        if (d16) {
-          VfieldArgs da{};
-          da.mode = 1;
-          da.rows_a = NP;
-          da.n_pair = NP;
-          da.n_tiles = (NP + vf_bn(2) - 1) / vf_bn(2);
-          da.n_kb = static_cast<int>(kdim / VF_BK);
-          da.kb_per_split = da.n_kb;
-          da.kd = f16_range(ctx->as_kd);
-          da.xper = ctx->x_period;
-          da.flush = flush_ranges(ctx->vf_flush > 0 ? ctx->vf_flush : 8192, da.kd);
-          da.Vacc = ctx->Vacc.as<double>();
-          da.M = M;
-          da.ldm = m_stride(NP);
-          da.exp_a = ctx->eL.as<int>();
-          da.exp_b = ctx->eR.as<int>();
-          da.err = ctx->err_dev.as<int>();
-          timed(ctx, XTC_K_AUX, M2 ? 3 : 2, [&] {
-            launch_lr_split(ctx->L32.as<float>(), NP, kdim, 4, da.kd, ctx->L.as<uint16_t>(), ctx->eL.as<int>(), st);
-            launch_lr_split(ctx->R32.as<float>(), NP, kdim, 4, da.kd, ctx->R.as<uint16_t>(), ctx->eR.as<int>(), st);
-            if (M2)
-              launch_lr_split(ctx->R32b.as<float>(), NP, kdim, 4, da.kd, ctx->R2.as<uint16_t>(), ctx->eR2.as<int>(), st);
-          });
-          timed(ctx, XTC_K_ASSEMBLE, 1, [&] { launch_vfield_tc(&tm_L, &tm_R, da, 2, 1, st); });
-          timed(ctx, XTC_K_AUX, 1, [&] { launch_vfield_tc_finalize(da, 2, 1, st); });
-          if (M2) {  // the tile sums buffer is reused after the finalize above, in stream order
-            VfieldArgs db = da;
-            db.M = M2;
-            db.exp_b = ctx->eR2.as<int>();
-            timed(ctx, XTC_K_ASSEMBLE, 1, [&] { launch_vfield_tc(&tm_L, &tm_R2, db, 2, 1, st); });
-            timed(ctx, XTC_K_AUX, 1, [&] { launch_vfield_tc_finalize(db, 2, 1, st); });
-          }
-          continue;
-        }
-        timed(ctx, XTC_K_ASSEMBLE, M2 ? 2 : 1, [&] {
-          if (pl.f64) {
-            launch_assemble_f64(ctx->L.as<double>(), ctx->R.as<double>(), NP, static_cast<int>(kdim), M, st);
-            if (M2) launch_assemble_f64(ctx->L.as<double>(), ctx->R2.as<double>(), NP, static_cast<int>(kdim), M2, st);
-          } else {
+        if (!accum) {
+          timed(ctx, XTC_K_ASSEMBLE, M2 ? 2 : 1, [&] {
             launch_assemble_tc(&tm_L, &tm_R, NP, static_cast<int>(kdim), std::min(ctx->as_kd, 3), M,
                                ctx->err_dev.as<int>(), st);
             if (M2)
               launch_assemble_tc(&tm_L, &tm_R2, NP, static_cast<int>(kdim), std::min(ctx->as_kd, 3), M2,
                                  ctx->err_dev.as<int>(), st);
-          }
+          });
+        }
+      }
+      if (d16) {
+        VfieldArgs da{};
+        da.mode = 1;
+        da.rows_a = NP;
+        da.n_pair = NP;
+        da.n_tiles = (NP + vf_bn(2) - 1) / vf_bn(2);
+        da.n_kb = static_cast<int>(kdim / VF_BK);
+        da.kb_per_split = da.n_kb;
+        da.kd = f16_range(ctx->as_kd);
+        da.xper = ctx->x_period;
+        da.flush = flush_ranges(ctx->vf_flush > 0 ? ctx->vf_flush : 8192, da.kd);
+        da.Vacc = ctx->Vacc.as<double>();
+        da.M = M;
+        da.ldm = m_stride(NP);
+        da.exp_a = ctx->eL.as<int>();
+        da.exp_b = ctx->eR.as<int>();
+        da.err = ctx->err_dev.as<int>();
+        timed(ctx, XTC_K_AUX, M2 ? 3 : 2, [&] {
+          launch_lr_split(ctx->L32.as<float>(), NP, kdim, 4, da.kd, ctx->L.as<uint16_t>(), ctx->eL.as<int>(), st);
+          launch_lr_split(ctx->R32.as<float>(), NP, kdim, 4, da.kd, ctx->R.as<uint16_t>(), ctx->eR.as<int>(), st);
+          if (M2)
+            launch_lr_split(ctx->R32b.as<float>(), NP, kdim, 4, da.kd, ctx->R2.as<uint16_t>(), ctx->eR2.as<int>(), st);
+        });
+        timed(ctx, XTC_K_ASSEMBLE, 1, [&] { launch_vfield_tc(&tm_L, &tm_R, nullptr, da, 2, 1, st); });
+        timed(ctx, XTC_K_AUX, 1, [&] { launch_vfield_tc_finalize(da, 2, 1, st); });
+        if (M2) {  // the tile sums buffer is reused after the finalize above, in stream order
+          VfieldArgs db = da;
+          db.M = M2;
+          db.exp_b = ctx->eR2.as<int>();
+          timed(ctx, XTC_K_ASSEMBLE, 1, [&] { launch_vfield_tc(&tm_L, &tm_R2, nullptr, db, 2, 1, st); });
+          timed(ctx, XTC_K_AUX, 1, [&] { launch_vfield_tc_finalize(db, 2, 1, st); });
+        }
+      } else if (pl.f64) {
+        timed(ctx, XTC_K_ASSEMBLE, M2 ? 2 : 1, [&] {
+          launch_assemble_f64(ctx->L.as<double>(), ctx->R.as<double>(), NP, static_cast<int>(kdim), M, st);
+          if (M2) launch_assemble_f64(ctx->L.as<double>(), ctx->R2.as<double>(), NP, static_cast<int>(kdim), M2, st);
         });
       }
     }

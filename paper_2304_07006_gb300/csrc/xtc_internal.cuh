@@ -85,8 +85,9 @@ void launch_jtab(const double* grid, int64_t n_grid, int64_t n_grid_pad, const J
 // Pair products rho^T[pq][j] = w_j phi_p(j) phi_q(j) split into parts.  fp16 (2 parts): each pair's
 // row scaled by a power of 2 (colexp[pq] receives the exponent; colmax is scratch) and split exactly
 // with one quantum per range of kd blocks of 32 points (gemm_bits_b(kd) bits), the two parts of a
-// block in one 128-byte row: [pq][j / 32][part][j % 32].  bf16 (3 parts): per-element split,
-// unscaled (colexp = 0), [part][pq][j].  n_pad must be a multiple of 32 kd.
+// block in one 128-byte row: [pq][j / 32][part][j % 32], followed by a plane of the scaled value
+// rounded to fp16, [pq][j] (2 x n_pair x n_pad values, then n_pair x n_pad).  bf16 (3 parts):
+// per-element split, unscaled (colexp = 0), [part][pq][j].  n_pad must be a multiple of 32 kd.
 void launch_rho_split(const double* phiT, const double* w, int64_t n_grid, int64_t n_pad, int n_orb, int parts, int kd,
                       const int* pair_p, const int* pair_q, unsigned int* colmax, int* colexp, void* out,
                       cudaStream_t st);
@@ -150,8 +151,10 @@ struct VfieldArgs {
 };
 bool vfield_tc_supported(int n_nuc);
 // Launches the GEMM.
-void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const VfieldArgs& a, int parts,
-                      int splits, cudaStream_t st);
+// tm_rho16: the fp16(rho^T) plane of the fp16 precision (box 32 x 128, 64-byte swizzle); step (d)
+// (mode 1) and the bf16 precision ignore it.
+void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const CUtensorMap* tm_rho16,
+                      const VfieldArgs& a, int parts, int splits, cudaStream_t st);
 // Then, with FP64 sums (a.flush > 0): mode 0 writes V from them, mode 1 adds the tiles into M.
 void launch_vfield_tc_finalize(const VfieldArgs& a, int parts, int splits, cudaStream_t st);
 
@@ -190,6 +193,8 @@ struct FieldsArgs {
   void* R2;                    // spin builds: R for electron-2 spin beta (R is alpha); nullptr otherwise
   const double* lam2;          // spin builds: beta exchange weights (lam holds the alpha ones)
   int out_parts;               // 0 = FP64 [4*gcp][pq]; 1 = FP32 [pq][4*gcp]; 3 = bf16 x3 split [part][pq][4*gcp]
+  int write_L;                 // write L (the first pass over a density's factors)
+  int add_R;                   // add R (and R2) to the buffer's contents (later passes; out_parts 0 or 1)
 };
 size_t fields_smem_bytes(int n_orb, int rank, int pts, bool f64, bool spin);
 void launch_fields(const FieldsArgs& a, bool f64, cudaStream_t st);  // f64: FP64 V, compute and output

@@ -107,6 +107,20 @@ def test_four_nuclei_full_rank_density_in_two_groups(prec):
     assert max_err(out, ref) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp16x2"])
+@pytest.mark.parametrize("n_orb,rank", [(40, 40), (30, 30), (40, 17)])
+def test_correlated_density_of_any_rank(prec, n_orb, rank):
+    """Densities of more factors than one step (c) pass holds (16): step (c) runs once per group of
+    factors, adding into R (linear in the factors), and step (d) once per chunk (Theory, approximate
+    use of correlated densities)."""
+    p = synth.make_small(n_orb=n_orb, n_rad=6, n_theta=4, n_phi=5, n_atoms=2, seed=31)
+    g = synth.random_density(n_orb, 40 + rank, rank=rank)
+    ref = direct.build(p, g)
+    with ctx_for(p, prec) as c:
+        out = c.build(p.grid, p.weights, p.phi, g)
+    assert max_err(out, ref) < TOL[prec], max_err(out, ref)
+
+
 def test_single_orbital_and_single_nucleus():
     p = synth.make_small(n_orb=1, n_rad=5, n_theta=3, n_phi=4, n_atoms=1, seed=3)
     ref = direct.build(p)
