@@ -200,6 +200,32 @@ XTC_API int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* gr
  * XTC_ERR_TIMEOUT.  The context stays usable.  XTC_ERR_ARG for a limit out of range. */
 XTC_API int xtc_selftest_wait_timeout(xtc_ctx* ctx, int limit_ms);
 
+/* Frozen-core folding of the xTC corrections, xTC-FC (Results section "Frozen core
+ * approximation"): the corrections of the whole orbital space are folded over a set C of doubly
+ * occupied core orbitals with the standard closed-shell frozen-core equations,
+ *   e_core        = sum_{c in C} 2 dh[c][c] + sum_{c,d in C} (2 dU[c][c][d][d] - dU[c][d][d][c])
+ *   dh_fc[a][b]   = dh[p][q] + sum_{c in C} (2 dU[p][q][c][c] - dU[p][c][c][q])
+ *   dU_act[a][b][e][f] = dU[p][q][r][s]
+ * where p = act[a], q = act[b], r = act[e], s = act[f] and act lists the orbitals outside C in
+ * ascending order (n_act = n_orb - n_core of them).  The folding is linear in (dh, dU): these are
+ * the xTC parts of the folded one-body integrals, two-body integrals and core energy, and the
+ * caller adds the folding of its own one-electron integrals and of V - K the same way.  The
+ * equations need only the pair symmetry dU[p][q][r][s] = dU[r][s][p][q], so they also fold a
+ * caller's non-hermitian integrals.  (FC-xTC, the other convention of that section, is
+ * xtc_build_1b2b run on the active orbitals alone.)
+ *   n_orb  1..320
+ *   dU     [n_orb]^4 FP64, dh [n_orb][n_orb] FP64 -- e.g. the outputs of xtc_build_1b2b
+ *   core   [n_core] distinct orbital indices in 0..n_orb-1, host memory; 0 <= n_core <= n_orb
+ *   dh_fc  [n_act][n_act] FP64 (required unless n_act = 0)
+ *   dU_act [n_act]^4 FP64 or NULL
+ *   e_core [1] FP64 (required)
+ * dU, dh, dh_fc, dU_act and e_core may be host or device memory; host inputs are staged through
+ * the context's workspace (n_orb^4 doubles for dU).  Returns when the outputs are complete.
+ * Every sum is taken in FP64, the core energy in a fixed order.  Errors: XTC_ERR_ARG (sizes, null
+ * pointers, a core index out of range or repeated), XTC_ERR_OOM, XTC_ERR_CUDA. */
+XTC_API int xtc_frozen_core_fold(xtc_ctx* ctx, int n_orb, const double* dU, const double* dh, int n_core,
+                                 const int* core, double* dh_fc, double* dU_act, double* e_core);
+
 /* Self-test of the reciprocal square root and reciprocal that the tensor-core precisions use in
  * step (a) (the unit vectors and the b = r12/(1+r12) factors of nabla_1 u): the hardware
  * approximation refined by one Newton-Raphson step, in the packed and the scalar form.  Reads

@@ -12,6 +12,9 @@ from its equations and sharing nothing with the CUDA library:
 * ``spin``        -- Route 2 for two spin densities: the restricted open-shell
                      working equations of Appendix A (Delta U^{aa}, ^{ab}, ^{bb},
                      Delta h^a, Delta h^b, <Psi0|L|Psi0>).
+* ``frozen_core`` -- xTC-FC: the standard closed-shell frozen-core folding of
+                     Delta U and Delta h over a core orbital set (Results section,
+                     "Frozen core approximation").
 * ``bruteforce``  -- Route 1: the six-index L from eq. (Ldecomp) or from the
                      literal triple quadrature of its definition, normal-ordered
                      explicitly in spin orbitals with eqs. (dU), (Delta h with the
@@ -24,5 +27,7 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU baseline leg of
 Parity status: every function here is pinned by CPU tests
 (``tests/test_oracle_*.py``) against finite differences, the literal triple
 quadrature, the paper's own identities between its two routes, symmetry and
-homogeneity invariants and a closed form for a separable Jastrow factor.
+homogeneity invariants, a closed form for a separable Jastrow factor and, for
+the frozen-core folding, Fock-space matrix elements of the second-quantised
+operator with the core filled.
 """

@@ -95,6 +95,7 @@ struct xtc_ctx {
   DBuf lamd, gamma_b, M2, M3;  // direct weights; spin builds: beta density, f^b, Delta U^{ab}
   DBuf lam2, R2, R32b, eR2;    // spin builds: beta exchange weights, R for electron-2 beta
   DBuf Lv, T3;                 // explicit three-body L: V of the outer points, the packed T
+  DBuf fc_U, fc_h, fc_hout, fc_Uout;  // frozen-core folding: staged host inputs and outputs
   // prepared state key (pair tables)
   int pair_n = -1;
   // timers
@@ -115,7 +116,8 @@ struct xtc_ctx {
   std::vector<DBuf*> buffers() {
     return {&jp_dev, &err_dev, &flag_dev, &grid, &w, &phi, &gamma, &phiT, &pair_p, &pair_q, &jtab, &jtab64,
             &rho, &colmax, &colexp, &G, &V, &Vacc, &L, &R, &L32, &R32, &eL, &eR, &M, &evec, &lam, &dU_tmp,
-            &dh_tmp, &e0_tmp, &vout, &r1, &r2, &lamd, &gamma_b, &M2, &M3, &lam2, &R2, &R32b, &eR2, &Lv, &T3};
+            &dh_tmp, &e0_tmp, &vout, &r1, &r2, &lamd, &gamma_b, &M2, &M3, &lam2, &R2, &R32b, &eR2, &Lv, &T3,
+            &fc_U, &fc_h, &fc_hout, &fc_Uout};
   }
 };
 
@@ -1099,6 +1101,56 @@ extern "C" int xtc_selftest_wait_timeout(xtc_ctx* ctx, int limit_ms) {
   CUDA_OK(cudaMemsetAsync(ctx->err_dev.p, 0, 16, ctx->st));
   CUDA_OK(cudaStreamSynchronize(ctx->st));
   return rc;
+}
+
+// ====================================================================== frozen-core folding
+extern "C" int xtc_frozen_core_fold(xtc_ctx* ctx, int n_orb, const double* dU, const double* dh, int n_core,
+                                    const int* core, double* dh_fc, double* dU_act, double* e_core) {
+  if (!ctx) return XTC_ERR_ARG;
+  if (n_orb < 1 || n_orb > FC_MAX_ORB || n_core < 0 || n_core > n_orb || !dU || !dh || !e_core ||
+      (n_core > 0 && !core) || (n_core < n_orb && !dh_fc))
+    return fail(ctx, XTC_ERR_ARG, "frozen_core_fold: null pointer or bad size");
+  FcIndex ix{};
+  std::vector<char> frozen(static_cast<size_t>(n_orb), 0);
+  for (int k = 0; k < n_core; ++k) {
+    if (core[k] < 0 || core[k] >= n_orb || frozen[core[k]])
+      return fail(ctx, XTC_ERR_ARG, "frozen_core_fold: core index %d out of range or repeated", core[k]);
+    frozen[core[k]] = 1;
+  }
+  for (int p = 0; p < n_orb; ++p) (frozen[p] ? ix.core[ix.n_core++] : ix.act[ix.n_act++]) = p;
+  CUDA_OK(cudaSetDevice(ctx->prm.device));
+  reset_timers(ctx);
+  cudaStream_t st = ctx->st;
+  const size_t n4 = static_cast<size_t>(n_orb) * n_orb * n_orb * n_orb;
+  const size_t na2 = static_cast<size_t>(ix.n_act) * ix.n_act, na4 = na2 * na2;
+  const double *d_U = nullptr, *d_h = nullptr;
+  int rc;
+  if ((rc = stage_input(ctx, ctx->fc_U, dU, n4, &d_U))) return rc;
+  if ((rc = stage_input(ctx, ctx->fc_h, dh, static_cast<size_t>(n_orb) * n_orb, &d_h))) return rc;
+  // small outputs go through one staging buffer unless both are device memory
+  const bool small_dev = is_device_ptr(e_core) && (na2 == 0 || is_device_ptr(dh_fc));
+  const bool big_dev = !dU_act || is_device_ptr(dU_act);
+  double *o_h = dh_fc, *o_e = e_core, *o_U = dU_act;
+  if (!small_dev) {
+    if (!ensure(ctx->fc_hout, (na2 + 1) * sizeof(double))) return fail(ctx, XTC_ERR_OOM, "output staging");
+    o_e = ctx->fc_hout.as<double>();
+    o_h = o_e + 1;
+  }
+  if (!big_dev && na4 > 0) {
+    if (!ensure(ctx->fc_Uout, na4 * sizeof(double))) return fail(ctx, XTC_ERR_OOM, "output staging");
+    o_U = ctx->fc_Uout.as<double>();
+  }
+  timed(ctx, XTC_K_AUX, 1 + (na2 > 0) + (na2 > 0 && dU_act), [&] {
+    launch_frozen_core(d_U, d_h, n_orb, ix, o_h, na4 > 0 ? o_U : nullptr, o_e, ctx->n_sm, st);
+  });
+  CUDA_OK(cudaGetLastError());
+  if (!small_dev) {
+    CUDA_OK(cudaMemcpyAsync(e_core, o_e, sizeof(double), cudaMemcpyDefault, st));
+    if (na2) CUDA_OK(cudaMemcpyAsync(dh_fc, o_h, na2 * sizeof(double), cudaMemcpyDefault, st));
+  }
+  if (!big_dev && na4 > 0) CUDA_OK(cudaMemcpyAsync(dU_act, o_U, na4 * sizeof(double), cudaMemcpyDefault, st));
+  CUDA_OK(cudaStreamSynchronize(st));
+  return XTC_OK;
 }
 
 // ====================================================================== reciprocal self-test

@@ -55,6 +55,18 @@ void launch_wait_timeout_selftest(int* err, unsigned long long limit_ns, cudaStr
 // Self-test of the gradient kernel's refined 1/sqrt(x) and 1/x (simt_pack.cuh) on x[0..n).
 void launch_recip_selftest(const float* x, int64_t n, float* y_rsqrt, float* y_rcp, cudaStream_t st);
 
+// Frozen-core folding (frozen_core.cu): core and active orbital lists, passed by value.
+constexpr int FC_MAX_ORB = 320;
+struct FcIndex {
+  int n_core, n_act;
+  int core[FC_MAX_ORB];
+  int act[FC_MAX_ORB];
+};
+// e_core (one FP64), dh_fc [n_act]^2 and, unless NULL, dU_act [n_act]^4 from the device arrays
+// dU [N]^4 and dh [N]^2.
+void launch_frozen_core(const double* dU, const double* dh, int N, const FcIndex& ix, double* dh_fc,
+                        double* dU_act, double* e_core, int n_sm, cudaStream_t st);
+
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // Row stride of the FP64 accumulator M[pq][rs]: a multiple of 32 (the bf16 step (d) kernel writes
 // whole 32-column groups of its 128-column tiles) with room for every pair.

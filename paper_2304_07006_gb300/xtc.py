@@ -22,7 +22,7 @@ EXPORTED = ("xtc_default_params", "xtc_create", "xtc_destroy", "xtc_strerror", "
             "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b", "xtc_jastrow_grad", "xtc_vfield",
             "xtc_get_timings", "xtc_vfield_noalloc", "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf",
             "xtc_three_body_L", "xtc_autotune_chunk", "xtc_selftest_wait_timeout", "xtc_engine_revision",
-            "xtc_selftest_reciprocals")
+            "xtc_selftest_reciprocals", "xtc_frozen_core_fold")
 
 
 class XtcParams(ctypes.Structure):
@@ -86,10 +86,12 @@ def load(path: str = LIB_PATH):
     lib.xtc_selftest_wait_timeout.argtypes = [P, I]
     lib.xtc_engine_revision.argtypes = []
     lib.xtc_selftest_reciprocals.argtypes = [P, I64, D, D, D]
+    lib.xtc_frozen_core_fold.argtypes = [P, I, D, D, I, ctypes.POINTER(ctypes.c_int), D, D, D]
     for name in ("xtc_create", "xtc_destroy", "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b",
                  "xtc_jastrow_grad", "xtc_vfield", "xtc_get_timings", "xtc_vfield_noalloc",
                  "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf", "xtc_three_body_L", "xtc_autotune_chunk",
-                 "xtc_selftest_wait_timeout", "xtc_engine_revision", "xtc_selftest_reciprocals"):
+                 "xtc_selftest_wait_timeout", "xtc_engine_revision", "xtc_selftest_reciprocals",
+                 "xtc_frozen_core_fold"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -269,6 +271,31 @@ class Context:
             _ptr(res["dU_aa"]), _ptr(res["dU_ab"]), _ptr(res["dU_bb"]), _ptr(res["dh_a"]), _ptr(res["dh_b"]),
             _ptr(res["e0"])))
         return res
+
+    def frozen_core_fold(self, dU, dh, core, dh_fc=None, dU_act=None, e_core=None, want_dU=False):
+        """xTC-FC folding of (dU, dh) over the core orbital list ``core`` (xtc_frozen_core_fold):
+        returns dh_fc [n_act][n_act], e_core [1] and, with want_dU or a given dU_act, the active
+        block dU_act [n_act]^4.  Missing outputs are allocated as numpy arrays."""
+        dU, dh = _f64(dU), _f64(dh)
+        n_orb = int(dh.shape[0])
+        _need(dU, n_orb ** 4, "dU")
+        _need(dh, n_orb ** 2, "dh")
+        idx = np.ascontiguousarray(np.asarray(core, dtype=np.int32).reshape(-1))
+        n_act = n_orb - int(idx.size)
+        if dh_fc is None:
+            dh_fc = np.empty((max(n_act, 0),) * 2)
+        if e_core is None:
+            e_core = np.empty(1)
+        if dU_act is None and want_dU:
+            dU_act = np.empty((max(n_act, 0),) * 4)
+        _need(dh_fc, max(n_act, 0) ** 2, "dh_fc")
+        _need(dU_act, max(n_act, 0) ** 4, "dU_act")
+        _need(e_core, 1, "e_core")
+        core_ptr = idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if idx.size else None
+        self._check(self._lib.xtc_frozen_core_fold(self._h, n_orb, _ptr(dU), _ptr(dh), int(idx.size), core_ptr,
+                                                   _ptr(dh_fc) if n_act > 0 else None, _ptr(dU_act),
+                                                   _ptr(e_core)))
+        return {"dh_fc": dh_fc, "dU_act": dU_act, "e_core": e_core}
 
     def selftest_reciprocals(self, x):
         """The refined 1/sqrt(x) and 1/x of the step (a) kernel on float32 x (xtc_selftest_reciprocals)."""
