@@ -34,6 +34,8 @@ namespace {
 
 constexpr int THREADS = 256;
 constexpr int RMAX = 16;
+constexpr int U1 = 8;  // phase 1: V loads in flight per thread
+constexpr int U2 = 2;  // phase 2: pairs per iteration
 
 template <typename TC>
 struct FieldsSmem {
@@ -79,8 +81,9 @@ __host__ __device__ inline size_t carve(FieldsSmem<TC>* s, uint8_t* base, int N,
 
 template <typename TV>
 __device__ __forceinline__ TV vload(const TV* V, int splits, int64_t split_stride, int64_t idx) {
-  TV v = V[idx];
-  for (int z = 1; z < splits; ++z) v += V[z * split_stride + idx];
+  // V is read-only while this kernel runs: the non-coherent path lets loads run ahead of stores
+  TV v = __ldg(V + idx);
+  for (int z = 1; z < splits; ++z) v += __ldg(V + z * split_stride + idx);
   return v;
 }
 
@@ -180,30 +183,30 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
   }
 
   // ---------------------------------------------------------------- phase 1: H_xk = V_x c_k, h_x
+  // Row (x, p) of the symmetric V_x, read U1 values at a time (all loads of a group issued before
+  // their products) in the order s = 0..N-1; (p, s) is pair idx(min, max).
   for (int row = sub; row < 3 * N; row += nsub) {
     const int x = row / N, p = row % N;
     TC acc[RMAX];
 #pragma unroll
     for (int kk = 0; kk < RMAX; ++kk) acc[kk] = 0;
-    int q = p;  // pair index of (s, p) for s = 0
-    for (int s = 0; s < N; ++s) {
-      int qi;
-      if (s < p) {
-        qi = q;
-        q += N - s - 1;
-      } else if (s == p) {
-        q = p * N - p * (p - 1) / 2;
-        qi = q;
-        ++q;
-      } else {
-        qi = q;
-        ++q;
-      }
-      const TC v = live ? static_cast<TC>(vload<TV>(V, a.splits, sstride, (static_cast<int64_t>(qi) * 3 + x) * a.gcp + il))
-                        : TC(0);
+    const int row_base = p * N - p * (p - 1) / 2 - p;  // pair (p, s) for s >= p: row_base + s
+    for (int s0 = 0; s0 < N; s0 += U1) {
+      TC v[U1];
 #pragma unroll
-      for (int kk = 0; kk < RMAX; ++kk)
-        if (kk < R) acc[kk] += v * sm.cs[kk * N + s];
+      for (int u = 0; u < U1; ++u) {
+        const int s = s0 + u;
+        const int qi = s < p ? s * N - s * (s - 1) / 2 + (p - s) : row_base + s;
+        v[u] = (live && s < N) ? static_cast<TC>(vload<TV>(V, a.splits, sstride, (static_cast<int64_t>(qi) * 3 + x) * a.gcp + il))
+                               : TC(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U1; ++u) {
+        const int s = min(s0 + u, N - 1);  // v[u] = 0 past the last orbital
+#pragma unroll
+        for (int kk = 0; kk < RMAX; ++kk)
+          if (kk < R) acc[kk] += v[u] * sm.cs[kk * N + s];
+      }
     }
     TC h = 0, h2 = 0;
 #pragma unroll
@@ -237,53 +240,68 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
   const TC w = sm.ws[pt];
   const TC wt = sm.Wt[pt];
   const TC W0 = sm.Wv[pt], W1 = sm.Wv[P + pt], W2 = sm.Wv[2 * P + pt];
-  for (int q = sub; q < a.n_pair; q += nsub) {
-    TC Lv[4] = {0, 0, 0, 0}, Rv[4] = {0, 0, 0, 0}, R2v[4] = {0, 0, 0, 0};
-    if (live) {
-      const int p = __ldg(a.pair_p + q), s = __ldg(a.pair_q + q);
-      TC v[3];
+  // U2 pairs per iteration, their V loads issued first
+  for (int q0 = sub; q0 < a.n_pair; q0 += U2 * nsub) {
+    TC v[U2][3];
+    int pp[U2], ss[U2];
+#pragma unroll
+    for (int j = 0; j < U2; ++j) {
+      const int q = q0 + j * nsub;
+      const bool ok = live && q < a.n_pair;
+      pp[j] = ok ? __ldg(a.pair_p + q) : 0;
+      ss[j] = ok ? __ldg(a.pair_q + q) : 0;
 #pragma unroll
       for (int x = 0; x < 3; ++x)
-        v[x] = static_cast<TC>(vload<TV>(V, a.splits, sstride, (static_cast<int64_t>(q) * 3 + x) * a.gcp + il));
-      TC zt = 0, zt2 = 0;
-      for (int x = 0; x < 3; ++x) {
-        const TC* Hp = sm.Hs + (x * R * N + p) * P + pt;
-        const TC* Hq = sm.Hs + (x * R * N + s) * P + pt;
+        v[j][x] = ok ? static_cast<TC>(vload<TV>(V, a.splits, sstride, (static_cast<int64_t>(q) * 3 + x) * a.gcp + il))
+                     : TC(0);
+    }
+#pragma unroll
+    for (int j = 0; j < U2; ++j) {
+      const int q = q0 + j * nsub;
+      if (q >= a.n_pair) break;
+      TC Lv[4] = {0, 0, 0, 0}, Rv[4] = {0, 0, 0, 0}, R2v[4] = {0, 0, 0, 0};
+      if (live) {
+        const int p = pp[j], s = ss[j];
+        TC zt = 0, zt2 = 0;
+        for (int x = 0; x < 3; ++x) {
+          const TC* Hp = sm.Hs + (x * R * N + p) * P + pt;
+          const TC* Hq = sm.Hs + (x * R * N + s) * P + pt;
 #pragma unroll 4
-        for (int kk = 0; kk < R; ++kk) {
-          if (SPIN) {
-            const TC hh = Hp[kk * N * P] * Hq[kk * N * P];
-            zt += sm.lam[kk] * hh;
-            zt2 += sm.lam2[kk] * hh;
-          } else {
-            zt += sm.lam[kk] * Hp[kk * N * P] * Hq[kk * N * P];
+          for (int kk = 0; kk < R; ++kk) {
+            if (SPIN) {
+              const TC hh = Hp[kk * N * P] * Hq[kk * N * P];
+              zt += sm.lam[kk] * hh;
+              zt2 += sm.lam2[kk] * hh;
+            } else {
+              zt += sm.lam[kk] * Hp[kk * N * P] * Hq[kk * N * P];
+            }
+          }
+        }
+        const TC vt = W0 * v[j][0] + W1 * v[j][1] + W2 * v[j][2];
+        const TC php = sm.phis[p * P + pt], phs = sm.phis[s * P + pt];
+        Lv[0] = w * php * phs;
+        Lv[1] = v[j][0];
+        Lv[2] = v[j][1];
+        Lv[3] = v[j][2];
+        Rv[0] = vt - zt;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          const TC zx = w * (php * sm.hs[(x * N + s) * P + pt] + sm.hs[(x * N + p) * P + pt] * phs);
+          Rv[1 + x] = TC(0.5) * wt * v[j][x] - zx;
+        }
+        if (SPIN) {
+          R2v[0] = vt - zt2;
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            const TC zx = w * (php * sm.hs2[(x * N + s) * P + pt] + sm.hs2[(x * N + p) * P + pt] * phs);
+            R2v[1 + x] = TC(0.5) * wt * v[j][x] - zx;
           }
         }
       }
-      const TC vt = W0 * v[0] + W1 * v[1] + W2 * v[2];
-      const TC php = sm.phis[p * P + pt], phs = sm.phis[s * P + pt];
-      Lv[0] = w * php * phs;
-      Lv[1] = v[0];
-      Lv[2] = v[1];
-      Lv[3] = v[2];
-      Rv[0] = vt - zt;
-#pragma unroll
-      for (int x = 0; x < 3; ++x) {
-        const TC zx = w * (php * sm.hs[(x * N + s) * P + pt] + sm.hs[(x * N + p) * P + pt] * phs);
-        Rv[1 + x] = TC(0.5) * wt * v[x] - zx;
-      }
-      if (SPIN) {
-        R2v[0] = vt - zt2;
-#pragma unroll
-        for (int x = 0; x < 3; ++x) {
-          const TC zx = w * (php * sm.hs2[(x * N + s) * P + pt] + sm.hs2[(x * N + p) * P + pt] * phs);
-          R2v[1 + x] = TC(0.5) * wt * v[x] - zx;
-        }
-      }
+      if (a.write_L) write4<TC, OUT_PARTS>(a.L, a.n_pair, a.gcp, q, il, Lv);
+      write4<TC, OUT_PARTS>(a.R, a.n_pair, a.gcp, q, il, Rv, a.add_R);
+      if (SPIN) write4<TC, OUT_PARTS>(a.R2, a.n_pair, a.gcp, q, il, R2v, a.add_R);
     }
-    if (a.write_L) write4<TC, OUT_PARTS>(a.L, a.n_pair, a.gcp, q, il, Lv);
-    write4<TC, OUT_PARTS>(a.R, a.n_pair, a.gcp, q, il, Rv, a.add_R);
-    if (SPIN) write4<TC, OUT_PARTS>(a.R2, a.n_pair, a.gcp, q, il, R2v, a.add_R);
   }
 }
 
