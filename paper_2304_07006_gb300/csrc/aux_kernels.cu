@@ -301,6 +301,8 @@ __global__ void __launch_bounds__(256) vfield_f64_kernel(const double* __restric
                                                           const double* __restrict__ jtab64,
                                                           const double* __restrict__ rho, int64_t n_pad, int n_pair,
                                                           int64_t i0, int64_t n_i, int64_t gcp,
+                                                          const int* __restrict__ pair_p,
+                                                          const int* __restrict__ pair_q, int n_orb,
                                                           double* __restrict__ V) {
   extern __shared__ double sm64[];
   const int n_nuc = jp->n_nuc;
@@ -365,8 +367,12 @@ __global__ void __launch_bounds__(256) vfield_f64_kernel(const double* __restric
     for (int b = 0; b < 2; ++b) {
       const int pq = pb + tx + 32 * b;
       if (pq >= n_pair) continue;
+      const int p = pair_p[pq], q = pair_q[pq];
 #pragma unroll
-      for (int x = 0; x < 3; ++x) V[(static_cast<int64_t>(pq) * 3 + x) * gcp + il] = acc[a][b][x];
+      for (int x = 0; x < 3; ++x) {
+        V[v_index(il, p, q, x, n_orb)] = acc[a][b][x];
+        V[v_index(il, q, p, x, n_orb)] = acc[a][b][x];
+      }
     }
   }
 }
@@ -560,15 +566,18 @@ __global__ void constant_kernel(const double* __restrict__ dh, const double* __r
 }
 
 template <typename TV>
-__global__ void vfield_export_kernel(const TV* __restrict__ V, int splits, int n_pair, int64_t n_i, int64_t gcp,
-                                     double* __restrict__ out) {
+__global__ void vfield_export_kernel(const TV* __restrict__ V, int splits, int n_pair, int n_orb,
+                                     const int* __restrict__ pair_p, const int* __restrict__ pair_q, int64_t n_i,
+                                     int64_t gcp, double* __restrict__ out) {
   const int64_t total = n_i * 3 * n_pair;
-  const int64_t sstride = static_cast<int64_t>(n_pair) * 3 * gcp;
+  const int64_t sstride = v_slice(gcp, n_orb);
   for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < total;
        k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t pq = k % n_pair, x = (k / n_pair) % 3, i = k / (3 * n_pair);
+    const int64_t pq = k % n_pair, i = k / (3 * n_pair);
+    const int x = static_cast<int>((k / n_pair) % 3);
+    const int64_t idx = v_index(i, pair_p[pq], pair_q[pq], x, n_orb);
     double v = 0.0;
-    for (int z = 0; z < splits; ++z) v += static_cast<double>(V[z * sstride + (pq * 3 + x) * gcp + i]);
+    for (int z = 0; z < splits; ++z) v += static_cast<double>(V[z * sstride + idx]);
     out[k] = v;
   }
 }
@@ -636,11 +645,12 @@ void launch_jtab64(const double* grid, int64_t n_grid, int64_t n_pad, const Jast
 
 void launch_vfield_f64_impl(const double* grid, const JastrowParams* jp, int n_nuc, const double* jtab64,
                             const double* rho, int64_t n_pad, int n_pair, int64_t i0, int64_t n_i, int64_t gcp,
-                            double* V, cudaStream_t st) {
+                            const int* pair_p, const int* pair_q, int n_orb, double* V, cudaStream_t st) {
   const size_t smem = sizeof(double) * (F64_TI * (PT_COEF + NUC_COEF * n_nuc) + F64_KJ * 3 * F64_TI + F64_KJ * F64_TP);
   cudaFuncSetAttribute(vfield_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem());
   dim3 g(blocks_for(n_i, F64_TI), blocks_for(n_pair, F64_TP));
-  vfield_f64_kernel<<<g, 256, smem, st>>>(grid, jp, jtab64, rho, n_pad, n_pair, i0, n_i, gcp, V);
+  vfield_f64_kernel<<<g, 256, smem, st>>>(grid, jp, jtab64, rho, n_pad, n_pair, i0, n_i, gcp, pair_p, pair_q, n_orb,
+                                          V);
 }
 
 void launch_assemble_f64(const double* L, const double* R, int n_pair, int kdim, double* M, cudaStream_t st) {
@@ -683,13 +693,15 @@ void launch_onebody_spin(const double* Uaa, const double* Uab, const double* Ubb
   constant_spin_kernel<<<1, 256, 0, st>>>(dh_a, ga, dh_b, gb, n_orb * n_orb, e0);
 }
 
-void launch_vfield_export(const void* V, bool f64, int splits, int n_pair, int64_t n_i, int64_t gcp, double* out,
-                          cudaStream_t st) {
+void launch_vfield_export(const void* V, bool f64, int splits, int n_pair, int n_orb, const int* pair_p,
+                          const int* pair_q, int64_t n_i, int64_t gcp, double* out, cudaStream_t st) {
   const unsigned int b = std::min<unsigned int>(blocks_for(n_i * 3 * n_pair, 256), 8192u);
   if (f64)
-    vfield_export_kernel<double><<<b, 256, 0, st>>>(static_cast<const double*>(V), splits, n_pair, n_i, gcp, out);
+    vfield_export_kernel<double><<<b, 256, 0, st>>>(static_cast<const double*>(V), splits, n_pair, n_orb, pair_p,
+                                                    pair_q, n_i, gcp, out);
   else
-    vfield_export_kernel<float><<<b, 256, 0, st>>>(static_cast<const float*>(V), splits, n_pair, n_i, gcp, out);
+    vfield_export_kernel<float><<<b, 256, 0, st>>>(static_cast<const float*>(V), splits, n_pair, n_orb, pair_p,
+                                                   pair_q, n_i, gcp, out);
 }
 
 }  // namespace xtc

@@ -17,9 +17,10 @@
 // and a.lam2 the beta ones (zero on the other spin's factors); L is written once, R for alpha and
 // R2 for beta.
 //
-// A CTA owns `pts` consecutive outer points (lane-contiguous, so every global read of V is a
-// contiguous run of the outer index) and all orbital pairs; H for its points lives in shared
-// memory.  Outputs, per point and pair, are L = (rho, Vx, Vy, Vz) and R = (A, Bx, By, Bz), written
+// A CTA owns `pts` (8 or fewer) consecutive outer points of one block of V (v_index: the block
+// holds the whole N x N matrices of its points, a row p of them one contiguous run) and all orbital
+// pairs; lanes run over the points, so a warp reads whole 32-byte pieces of a row.  H for its
+// points lives in shared memory.  Outputs, per point and pair, are L = (rho, Vx, Vy, Vz) and R = (A, Bx, By, Bz), written
 // as the operands of step (d): FP32 rows [pq][4*gcp], FP64 [4*gcp][pq] or three bf16 parts
 // [part][pq][4*gcp].  L does not depend on the density and R is linear in its factors, so a
 // density of more factors than one pass holds runs several passes: the first writes L and R, the
@@ -34,7 +35,7 @@ namespace {
 
 constexpr int THREADS = 256;
 constexpr int RMAX = 16;
-constexpr int U1 = 8;  // phase 1: V loads in flight per thread
+constexpr int U1 = 4;  // phase 1: columns per group (3 V loads each in flight)
 constexpr int U2 = 2;  // phase 2: pairs per iteration
 
 template <typename TC>
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
   const int64_t il = static_cast<int64_t>(blockIdx.x) * P + pt;  // chunk-local outer point
   const bool live = il < a.n_i;
   const TV* V = static_cast<const TV*>(a.V);
-  const int64_t sstride = static_cast<int64_t>(a.n_pair) * 3 * a.gcp;
+  const int64_t sstride = v_slice(a.gcp, N);  // split slices of V
 
   // ---------------------------------------------------------------- phase 0: orbitals and gamma factors
   for (int k = t; k < N * P; k += THREADS) {
@@ -183,41 +184,50 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
   }
 
   // ---------------------------------------------------------------- phase 1: H_xk = V_x c_k, h_x
-  // Row (x, p) of the symmetric V_x, read U1 values at a time (all loads of a group issued before
-  // their products) in the order s = 0..N-1; (p, s) is pair idx(min, max).
-  for (int row = sub; row < 3 * N; row += nsub) {
-    const int x = row / N, p = row % N;
-    TC acc[RMAX];
+  // A thread takes row p of the three V_x of its point, one contiguous run of the point block
+  // (v_index), U1 columns s at a time (their loads issued before the products), s = 0..N-1 in order.
+  const TV* vrow0 = V + (il / VB) * static_cast<int64_t>(N) * N * 3 * VB + (il % VB);
+  for (int p = sub; p < N; p += nsub) {
+    TC acc[3][RMAX];
 #pragma unroll
-    for (int kk = 0; kk < RMAX; ++kk) acc[kk] = 0;
-    const int row_base = p * N - p * (p - 1) / 2 - p;  // pair (p, s) for s >= p: row_base + s
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+      for (int kk = 0; kk < RMAX; ++kk) acc[x][kk] = 0;
+    const TV* vrow = vrow0 + static_cast<int64_t>(p) * N * 3 * VB;
     for (int s0 = 0; s0 < N; s0 += U1) {
-      TC v[U1];
+      TC v[U1][3];
 #pragma unroll
       for (int u = 0; u < U1; ++u) {
         const int s = s0 + u;
-        const int qi = s < p ? s * N - s * (s - 1) / 2 + (p - s) : row_base + s;
-        v[u] = (live && s < N) ? static_cast<TC>(vload<TV>(V, a.splits, sstride, (static_cast<int64_t>(qi) * 3 + x) * a.gcp + il))
-                               : TC(0);
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+          v[u][x] = (live && s < N) ? static_cast<TC>(vload<TV>(vrow, a.splits, sstride, s * 3 * VB + x * VB)) : TC(0);
       }
 #pragma unroll
       for (int u = 0; u < U1; ++u) {
         const int s = min(s0 + u, N - 1);  // v[u] = 0 past the last orbital
 #pragma unroll
         for (int kk = 0; kk < RMAX; ++kk)
-          if (kk < R) acc[kk] += v[u] * sm.cs[kk * N + s];
+          if (kk < R) {
+            const TC c = sm.cs[kk * N + s];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) acc[x][kk] += v[u][x] * c;
+          }
       }
     }
-    TC h = 0, h2 = 0;
 #pragma unroll
-    for (int kk = 0; kk < RMAX; ++kk)
-      if (kk < R) {
-        sm.Hs[((x * R + kk) * N + p) * P + pt] = acc[kk];
-        h += sm.lam[kk] * sm.cph[kk * P + pt] * acc[kk];
-        if (SPIN) h2 += sm.lam2[kk] * sm.cph[kk * P + pt] * acc[kk];
-      }
-    sm.hs[(x * N + p) * P + pt] = h;
-    if (SPIN) sm.hs2[(x * N + p) * P + pt] = h2;
+    for (int x = 0; x < 3; ++x) {
+      TC h = 0, h2 = 0;
+#pragma unroll
+      for (int kk = 0; kk < RMAX; ++kk)
+        if (kk < R) {
+          sm.Hs[((x * R + kk) * N + p) * P + pt] = acc[x][kk];
+          h += sm.lam[kk] * sm.cph[kk * P + pt] * acc[x][kk];
+          if (SPIN) h2 += sm.lam2[kk] * sm.cph[kk * P + pt] * acc[x][kk];
+        }
+      sm.hs[(x * N + p) * P + pt] = h;
+      if (SPIN) sm.hs2[(x * N + p) * P + pt] = h2;
+    }
   }
   __syncthreads();
   // W_x = sum_k lamd_k sum_p c_k[p] H_xk[p]  (deterministic two-level sum)
@@ -250,10 +260,10 @@ __global__ void __launch_bounds__(THREADS) fields_kernel(const FieldsArgs a) {
       const bool ok = live && q < a.n_pair;
       pp[j] = ok ? __ldg(a.pair_p + q) : 0;
       ss[j] = ok ? __ldg(a.pair_q + q) : 0;
+      const int64_t vo = (static_cast<int64_t>(pp[j]) * N + ss[j]) * 3 * VB;
 #pragma unroll
       for (int x = 0; x < 3; ++x)
-        v[j][x] = ok ? static_cast<TC>(vload<TV>(V, a.splits, sstride, (static_cast<int64_t>(q) * 3 + x) * a.gcp + il))
-                     : TC(0);
+        v[j][x] = ok ? static_cast<TC>(vload<TV>(vrow0, a.splits, sstride, vo + x * VB)) : TC(0);
     }
 #pragma unroll
     for (int j = 0; j < U2; ++j) {

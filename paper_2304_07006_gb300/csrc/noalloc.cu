@@ -140,14 +140,14 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     if (f64) {
       c.take<double>(static_cast<size_t>(NGp) * (3 + n_nuc));
       c.take<double>(static_cast<size_t>(NGp) * NP);
-      c.take<double>(static_cast<size_t>(NP) * 3 * gc);
+      c.take<double>(static_cast<size_t>(v_slice(gc, N)));
     } else {
       c.take<double>(static_cast<size_t>(N) * NGp);
       c.take<float>(static_cast<size_t>(NGp) * jtab_stride(n_nuc));
       c.take<uint16_t>(static_cast<size_t>(3) * NP * NGp);
       c.take<unsigned int>(NP);
       c.take<int>(NP);
-      c.take<float>(static_cast<size_t>(NP) * 3 * gc);
+      c.take<float>(static_cast<size_t>(v_slice(gc, N)));
       c.take<uint16_t>(static_cast<size_t>(parts) * 3 * gc * NGp);
     }
     return c.off;
@@ -182,7 +182,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
   if (f64) {
     jtab64 = cz.take<double>(static_cast<size_t>(NGp) * (3 + n_nuc));
     rho64 = cz.take<double>(static_cast<size_t>(NGp) * NP);
-    Vbuf = cz.take<double>(static_cast<size_t>(NP) * 3 * gc);
+    Vbuf = cz.take<double>(static_cast<size_t>(v_slice(gc, N)));
     launch_jtab64(grid_xyz, n_grid, NGp, cv.jp_dev, n_nuc, jtab64, st);
     launch_rho_f64(phi, weights, n_grid, NGp, N, pair_p, pair_q, rho64, st);
   } else {
@@ -191,7 +191,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     rho = cz.take<uint16_t>(static_cast<size_t>(3) * NP * NGp);  // fp16: split rows + fp16 plane
     unsigned int* colmax = cz.take<unsigned int>(NP);
     colexp = cz.take<int>(NP);
-    Vbuf = cz.take<float>(static_cast<size_t>(NP) * 3 * gc);
+    Vbuf = cz.take<float>(static_cast<size_t>(v_slice(gc, N)));
     void* G = cz.take<uint16_t>(static_cast<size_t>(parts) * 3 * gc * NGp);
     launch_transpose_phi(phi, n_grid, NGp, N, phiT, st);
     launch_jtab(grid_xyz, n_grid, NGp, cv.jp_dev, n_nuc, jtab_stride(n_nuc), jtab, st);
@@ -233,7 +233,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
   for (int64_t c0 = outer_begin; c0 < outer_end; c0 += gc) {
     const int64_t n_i = std::min<int64_t>(gc, outer_end - c0);
     if (f64) {
-      launch_vfield_f64_impl(grid_xyz, cv.jp_dev, n_nuc, jtab64, rho64, NGp, NP, c0, n_i, gc,
+      launch_vfield_f64_impl(grid_xyz, cv.jp_dev, n_nuc, jtab64, rho64, NGp, NP, c0, n_i, gc, pair_p, pair_q, N,
                              static_cast<double*>(Vbuf), st);
     } else {
       int sg = 0;
@@ -258,6 +258,9 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
       VfieldArgs a{};
       a.colexp = colexp;
       a.V = static_cast<float*>(Vbuf);
+      a.pair_p = pair_p;
+      a.pair_q = pair_q;
+      a.n_orb = N;
       a.Vacc = nullptr;
       a.flush = 0;  // FP32 running sums only: the fixed scratch has no room for FP64 tiles
       a.n_i = n_i;
@@ -273,7 +276,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
       a.err = err;
       launch_vfield_tc(&tm_gl, &tm, &tm16, a, parts, 1, st);
     }
-    launch_vfield_export(Vbuf, f64, 1, NP, n_i, gc, V + (c0 - outer_begin) * 3 * NP, st);
+    launch_vfield_export(Vbuf, f64, 1, NP, N, pair_p, pair_q, n_i, gc, V + (c0 - outer_begin) * 3 * NP, st);
   }
   if (cudaGetLastError() != cudaSuccess) return xtc_internal_fail(ctx, XTC_ERR_CUDA, "noalloc: kernel launch failed");
   int h = 0;

@@ -32,8 +32,9 @@
 // So ranges span two stages (12 MMAs, 16 in step (d)), and two issuers alternate ranges, each with
 // its own accumulator pair (TMEM: E0, X0, E1, X1 = 4 x 128 of 512 columns).  Step (b) stages hold
 // 40 KB (A, B hi/lo, fp16(B): 5 stages), step (d) stages 32 KB (7 stages).  Warp roles:
-//   * warp 0 (one lane): TMA loads; a range's slots are reloaded once its commit has arrived;
-//   * warps 1 and 2 (one lane each): the MMAs of the even / odd ranges, one commit per range;
+//   * warp 0 (one lane): TMA loads; a slot is reloaded once the MMAs of its stage have completed;
+//   * warps 1 and 2 (one lane each): the MMAs of the even / odd ranges, a commit per stage (it
+//     frees the slot) and one per range (it starts the drains);
 //   * warps 3..18: after every range, drains of E_k, and every `xper` stages of X_k, into FP32
 //     running sums held in registers (four warps per TMEM lane quarter, 32 columns each).  The
 //     sums move into an FP64 accumulator in HBM, private to the CTA and column-major in its tile,
@@ -127,7 +128,8 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
   uint64_t* e_free = rdone + NRB;             // [2] the drains released E_k (issuer k)
   uint64_t* x_free = e_free + 2;              // [2] the drains released X_k
   uint64_t* fin_bar = x_free + 2;             // every MMA of both issuers completed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin_bar + 1);
+  uint64_t* sfree = fin_bar + 1;              // [XB_STAGES] the stage's MMAs completed (slot free)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sfree + XB_STAGES);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -146,7 +148,10 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
   const int xr = max(1, args.xper / (2 * kd));             // ranges of one issuer per X drain
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) mbar_init(&tma_full[s], 1);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&tma_full[s], 1);
+      mbar_init(&sfree[s], 1);
+    }
     for (int r = 0; r < NRB; ++r) mbar_init(&rdone[r], 1);
     for (int k = 0; k < 2; ++k) {
       mbar_init(&e_free[k], XB_DRAIN_WARPS);
@@ -172,17 +177,14 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------------------------------------------------------- TMA producer
-      int seen = 0;  // ranges known to have completed (their slots are free again)
+      // a slot is refilled as soon as the MMAs of the stage it held have completed (one commit
+      // per stage), not when the whole range has
       int issued = 0;
       for (int it = 0; it < n_it; ++it) {
         const int s = it % STAGES;
-        if (it >= STAGES) {
-          const int need = (it - STAGES) / kd;  // range holding the slot's previous stage
-          bool ok = true;
-          for (; seen <= need && ok; ++seen)
-            ok = mbar_wait(&rdone[seen % NRB], (seen / NRB) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF);
-          if (!ok) break;
-        }
+        if (it >= STAGES &&
+            !mbar_wait(&sfree[s], ((it / STAGES) - 1) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF))
+          break;
         mbar_arrive_expect_tx(&tma_full[s], XB_STAGE);
         uint8_t* st = smem + s * XB_STAGE;
         tma_load_3d(st, &tm_a, &tma_full[s], (kb0 + it) * 2 * VF_BK, row0, 0);
@@ -202,9 +204,9 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
       // ---------------------------------------------------------------- MMA issuers
       // Issuer k takes the ranges r = k, k + 2, ...: per stage the hi x hi products into E_k (a
       // fresh, exact accumulation per range) and the cross products lo x hi, hi x lo (and in step
-      // (d) lo x lo) into X_k (restarted every xr of its ranges); one commit per range, whose
-      // arrival frees the range's slots and starts the drains.  With two issuers one's waits and commit
-      // overlap the other's MMAs, and neither waits for the other's drains.
+      // (d) lo x lo) into X_k (restarted every xr of its ranges); a commit after each stage frees
+      // its slot for the next load, one after each range starts the drains.  With two issuers
+      // one's waits and commits overlap the other's MMAs, and neither waits for the other's drains.
       constexpr uint32_t idesc = idesc_f16(VF_BM, XB_BN, false);
       const int k = warp == XB_WARP_I0 ? 0 : 1;
       const uint32_t e_tmem = tmem + 2 * k * XB_BN, x_tmem = e_tmem + XB_BN;
@@ -239,6 +241,7 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
             tc_mma_f16(x_tmem, da + 4, db + 4, idesc, 1u);                             // lo_a x lo_b
             tc_mma_f16(x_tmem, da + 6, db + 6, idesc, 1u);
           }
+          tc_commit(&sfree[s]);
         }
         if (!alive) break;
         tc_commit(&rdone[r % NRB]);
@@ -317,19 +320,21 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
         }
       }
     } else if (MODE == 0) {
-      // FP32 sums straight to V: row = outer point ib + row of component x -> V[split][pq][x][il]
+      // FP32 sums straight to V: row = outer point ib + row of component x, both (p, s) and (s, p)
       const int row = quarter * 32 + lane;
       const int64_t il = static_cast<int64_t>(ib) + row;
-      const int64_t col_off = static_cast<int64_t>(x) * args.gcp + il;
       const int pq0 = t.n_tile * XB_BN + static_cast<int>(c_base);
       if (ok && !*abort_flag && il < args.n_i && n_it > 0) {
-        float* Vz = args.V + static_cast<int64_t>(split) * args.n_pair * 3 * args.gcp;
+        float* Vz = args.V + split * v_slice(args.gcp, args.n_orb);
 #pragma unroll
         for (int k = 0; k < XB_HC; ++k) {
           const int pq = pq0 + k;
-          if (pq < args.n_pair)
-            Vz[static_cast<int64_t>(pq) * 3 * args.gcp + col_off] =
-                ldexpf(S[k] * args.unscale_g, -__ldg(args.colexp + pq));
+          if (pq < args.n_pair) {
+            const int p = __ldg(args.pair_p + pq), q = __ldg(args.pair_q + pq);
+            const float v = ldexpf(S[k] * args.unscale_g, -__ldg(args.colexp + pq));
+            Vz[v_index(il, p, q, x, args.n_orb)] = v;
+            Vz[v_index(il, q, p, x, args.n_orb)] = v;
+          }
         }
       }
     }
@@ -531,16 +536,18 @@ __global__ void __launch_bounds__(BF_THREADS, 1)
     } else {
       const int row = quarter * 32 + lane;
       const int64_t il = static_cast<int64_t>(ib) + row;
-      const int64_t col_off = static_cast<int64_t>(x) * args.gcp + il;
       const int pq0 = t.n_tile * BF_BN + static_cast<int>(c_base);
       if (ok && !*abort_flag && il < args.n_i && n_it > 0) {
-        float* Vz = args.V + static_cast<int64_t>(split) * args.n_pair * 3 * args.gcp;
+        float* Vz = args.V + split * v_slice(args.gcp, args.n_orb);
 #pragma unroll
         for (int k = 0; k < BF_HC; ++k) {
           const int pq = pq0 + k;
-          if (pq < args.n_pair)
-            Vz[static_cast<int64_t>(pq) * 3 * args.gcp + col_off] =
-                ldexpf(S[k] * args.unscale_g, -__ldg(args.colexp + pq));
+          if (pq < args.n_pair) {
+            const int p = __ldg(args.pair_p + pq), q = __ldg(args.pair_q + pq);
+            const float v = ldexpf(S[k] * args.unscale_g, -__ldg(args.colexp + pq));
+            Vz[v_index(il, p, q, x, args.n_orb)] = v;
+            Vz[v_index(il, q, p, x, args.n_orb)] = v;
+          }
         }
       }
     }
@@ -566,12 +573,15 @@ __global__ void __launch_bounds__(VF_BM) vfield_finalize_kernel(const VfieldArgs
   const int64_t il = static_cast<int64_t>(t.m_tile - x * args.mt_per_x) * VF_BM + row;
   if (il >= args.n_i) return;
   const double* acc = args.Vacc + (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x) * VF_BM * BN + row;
-  float* v = args.V + static_cast<int64_t>(blockIdx.y) * args.n_pair * 3 * args.gcp + x * args.gcp + il;
+  float* v = args.V + blockIdx.y * v_slice(args.gcp, args.n_orb);
   const int ncol = min(BN, args.n_pair - t.n_tile * BN);
   for (int c = 0; c < ncol; ++c) {
     const int pq = t.n_tile * BN + c;
-    v[static_cast<int64_t>(pq) * 3 * args.gcp] =
+    const int p = __ldg(args.pair_p + pq), q = __ldg(args.pair_q + pq);
+    const float val =
         ldexpf(static_cast<float>(acc[static_cast<int64_t>(c) * VF_BM]) * args.unscale_g, -__ldg(args.colexp + pq));
+    v[v_index(il, p, q, x, args.n_orb)] = val;
+    v[v_index(il, q, p, x, args.n_orb)] = val;
   }
 }
 

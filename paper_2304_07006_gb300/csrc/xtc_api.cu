@@ -260,13 +260,14 @@ struct Plan {
 // budget_scale < 1 shrinks the memory budgets (the autotuner's smaller candidates).
 int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t NGp, int parts, int64_t n_outer, bool f64,
                    double budget_scale = 1.0) {
-  // memory budgets: 10 GB for V and the step (d) operands, 16 GB for the step (a) gradient table;
+  // memory budgets: 12 GB for V and the step (d) operands, 16 GB for the step (a) gradient table;
   // then the chunk that fills whole waves of the step (b) GEMM best
   const double vbytes = f64 ? 3.0 * 8 : 3.0 * 4;
   // step (d) operands per pair and outer point: FP64 L, R; bf16 x3 L, R; or FP32 L, R + fp16 x2 split
   const double lrbytes = f64 ? 2 * 4 * 8.0 : (parts == 2 ? 2 * 4 * (4.0 + 4.0) : 2 * 3 * 4 * 2.0);
-  const double per_point = NP * (vbytes + lrbytes);
-  int64_t cap = static_cast<int64_t>(budget_scale * 10.0e9 / per_point);
+  // V holds the whole N x N matrix per point (N^2 < 2 NP)
+  const double per_point = NP * (2.0 * vbytes + lrbytes);
+  int64_t cap = static_cast<int64_t>(budget_scale * 12.0e9 / per_point);
   if (!f64) cap = std::min<int64_t>(cap, static_cast<int64_t>(budget_scale * 16.0e9 / (3.0 * parts * 2.0 * NGp)));
   cap = std::max<int64_t>(128, std::min<int64_t>(cap, static_cast<int64_t>(budget_scale * 32768)) / 128 * 128);
   const int64_t need = round_up(n_outer, 128);
@@ -441,7 +442,7 @@ int xtc_set_outer_range(xtc_ctx* ctx, int64_t begin, int64_t end) {
 // 1: one accumulator per range of kd stages, truncating FP32 accumulation (192-column tiles);
 // 2: block-exact fp16 split, exact hi x hi accumulator pair plus a cross-product accumulator
 //    (160-column tiles).
-int xtc_engine_revision(void) { return 2; }
+int xtc_engine_revision(void) { return 3; }
 
 int xtc_get_timings(xtc_ctx* ctx, double* ms, int64_t* launches, int n) {
   if (!ctx || n < XTC_N_KERNELS) return XTC_ERR_ARG;
@@ -559,7 +560,7 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
                        ctx->colexp.as<int>(), ctx->rho.p, st);
     }
   });
-  const size_t vbytes = static_cast<size_t>(pl.splits) * pl.NP * 3 * pl.gc * (f64 ? 8 : 4);
+  const size_t vbytes = static_cast<size_t>(pl.splits) * v_slice(pl.gc, pl.N) * (f64 ? 8 : 4);
   if (!ensure(ctx->V, vbytes)) return fail(ctx, XTC_ERR_OOM, "V chunk (%.2f GB)", vbytes / 1e9);
   if (!f64) {
     const size_t gbytes = 2ull * pl.parts_b * 3 * pl.gc * pl.NGp;
@@ -601,7 +602,8 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   if (pl.f64) {
     timed(ctx, XTC_K_VFIELD, 1, [&] {
       launch_vfield_f64_impl(d_grid, ctx->jp_dev.as<JastrowParams>(), ctx->jp.n_nuc, ctx->jtab64.as<double>(),
-                             ctx->rho.as<double>(), pl.NGp, pl.NP, i0, n_i, pl.gc, ctx->V.as<double>(), st);
+                             ctx->rho.as<double>(), pl.NGp, pl.NP, i0, n_i, pl.gc, ctx->pair_p.as<int>(),
+                             ctx->pair_q.as<int>(), pl.N, ctx->V.as<double>(), st);
     });
     return XTC_OK;
   }
@@ -632,6 +634,9 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   VfieldArgs a{};
   a.colexp = ctx->colexp.as<int>();
   a.V = ctx->V.as<float>();
+  a.pair_p = ctx->pair_p.as<int>();
+  a.pair_q = ctx->pair_q.as<int>();
+  a.n_orb = pl.N;
   a.Vacc = ctx->Vacc.as<double>();
   a.n_i = n_i;
   a.gcp = pl.gc;
@@ -1077,7 +1082,8 @@ extern "C" int xtc_vfield(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double*
       if (!ensure(ctx->vout, n_i * per_point * 8)) return fail(ctx, XTC_ERR_OOM, "V staging");
       dst = ctx->vout.as<double>();
     }
-    launch_vfield_export(ctx->V.p, pl.f64, pl.f64 ? 1 : pl.splits, pl.NP, n_i, pl.gc, dst, st);
+    launch_vfield_export(ctx->V.p, pl.f64, pl.f64 ? 1 : pl.splits, pl.NP, pl.N, ctx->pair_p.as<int>(),
+                         ctx->pair_q.as<int>(), n_i, pl.gc, dst, st);
     CUDA_OK(cudaGetLastError());
     if (!out_dev)
       CUDA_OK(cudaMemcpyAsync(V + (c0 - pl.ob) * per_point, dst, n_i * per_point * 8, cudaMemcpyDeviceToHost, st));

@@ -67,6 +67,19 @@ struct FcIndex {
 void launch_frozen_core(const double* dU, const double* dh, int N, const FcIndex& ix, double* dh_fc,
                         double* dU_act, double* e_core, int n_sm, cudaStream_t st);
 
+// V of a chunk (written by step (b), read by step (c)): blocks of VB consecutive outer points, each
+// holding the whole symmetric N x N matrix of the three components, V_x,ps(i) at
+// [i / VB][p][s][x][i % VB]; both (p, s) and (s, p) are written.  A row p of a block is one
+// contiguous run of 3 * VB * N values, so step (c) streams rows instead of gathering pairs.  One
+// split slice holds gcp * N * N * 3 values.
+constexpr int VB = 8;
+__host__ __device__ inline int64_t v_index(int64_t i, int p, int s, int x, int n_orb) {
+  return (((i / VB) * n_orb + p) * n_orb + s) * (3 * VB) + x * VB + (i % VB);
+}
+__host__ __device__ inline int64_t v_slice(int64_t gcp, int n_orb) {
+  return gcp * static_cast<int64_t>(n_orb) * n_orb * 3;
+}
+
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // Row stride of the FP64 accumulator M[pq][rs]: a multiple of 32 (the bf16 step (d) kernel writes
 // whole 32-column groups of its 128-column tiles) with room for every pair.
@@ -137,7 +150,10 @@ void launch_gfield(const CUtensorMap* tm_g_store, const GfieldArgs& a, int parts
 // chunk, from the G table (tm_g: box rows 128) and the split rho^T (tm_rho: box rows vf_bn(parts)).
 struct VfieldArgs {
   const int* colexp;           // per-pair exponent of the rho scaling (0 when unscaled)
-  float* V;                    // output base (mode 0)
+  float* V;                    // output base (mode 0), layout v_index
+  const int* pair_p;           // mode 0: orbitals (p, s) of pair pq
+  const int* pair_q;
+  int n_orb;
   double* Vacc;                // FP64 partial sums, [splits][grid CTAs][BN][128] (used when flush > 0)
   int flush;                   // ranges summed in FP32 registers between FP64 flushes (0: no flush)
   int64_t n_i;                 // outer points of this chunk
@@ -170,18 +186,18 @@ void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const 
 // Then, with FP64 sums (a.flush > 0): mode 0 writes V from them, mode 1 adds the tiles into M.
 void launch_vfield_tc_finalize(const VfieldArgs& a, int parts, int splits, cudaStream_t st);
 
-// Steps (a)+(b), FP64 SIMT twin.  V[pq][x][il] (FP64).  jtab64[n_grid_pad][3 + n_nuc].
+// Steps (a)+(b), FP64 SIMT twin.  V in the layout of v_index (FP64).  jtab64[n_grid_pad][3 + n_nuc].
 void launch_jtab64(const double* grid, int64_t n_grid, int64_t n_pad, const JastrowParams* jp, int n_nuc,
                    double* jtab, cudaStream_t st);
 void launch_vfield_f64_impl(const double* grid, const JastrowParams* jp, int n_nuc, const double* jtab64,
                             const double* rho, int64_t n_pad, int n_pair, int64_t i0, int64_t n_i, int64_t gcp,
-                            double* V, cudaStream_t st);
+                            const int* pair_p, const int* pair_q, int n_orb, double* V, cudaStream_t st);
 
 // Step (a) alone in FP64.
 void launch_jastrow_grad(const JastrowParams* jp, const double* r1, const double* r2, int64_t n, double* out,
                          cudaStream_t st);
 
-// Step (c).  Reads V (T = float or double, [splits][pq][x][gcp]), writes L = (rho, Vx, Vy, Vz) and
+// Step (c).  Reads V (T = float or double, [splits] slices in the layout of v_index), writes L = (rho, Vx, Vy, Vz) and
 // R = (A, Bx, By, Bz) per outer point, either as split parts [part][pq][4*gcp] (fp16/bf16) or as FP64
 // [4*gcp][pq].
 struct FieldsArgs {
@@ -243,9 +259,9 @@ void launch_onebody_spin(const double* Uaa, const double* Uab, const double* Ubb
 void launch_onebody(const double* M, const double* gamma, int n_orb, int n_pair, double* dh, double* e0,
                     cudaStream_t st);
 
-// V (FP32 or FP64, [splits][pq][x][gcp]) -> FP64 [n_i][3][pq] (for xtc_vfield).
-void launch_vfield_export(const void* V, bool f64, int splits, int n_pair, int64_t n_i, int64_t gcp,
-                          double* out, cudaStream_t st);
+// V (FP32 or FP64, [splits] slices in the layout of v_index) -> FP64 [n_i][3][pq] (for xtc_vfield).
+void launch_vfield_export(const void* V, bool f64, int splits, int n_pair, int n_orb, const int* pair_p,
+                          const int* pair_q, int64_t n_i, int64_t gcp, double* out, cudaStream_t st);
 
 // Read-only view of a context for entry points implemented outside xtc_api.cu.
 struct CtxView {
