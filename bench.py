@@ -116,7 +116,7 @@ class Clocks:
 # ncu on the first VFIELD_CAPTURE_OUTER outer points of the workload (`--ncu-case`), for GEMM
 # engine revision VFIELD_CAPTURE_REVISION; with another revision the traffic is reported as null
 VFIELD_CAPTURE_REVISION = 3
-VFIELD_DRAM_BYTES_CAPTURED = None
+VFIELD_DRAM_BYTES_CAPTURED = 29_676_537_856 + 2_914_678_528
 VFIELD_CAPTURE_OUTER = 1184
 
 
@@ -333,6 +333,37 @@ def three_body_measure(args, torch, dev, local):
             "note": "wall time per call with steps (a)+(b) in FP64; L is written densely on the device"}
 
 
+def frozen_core_measure(args, torch, dev, local, peaks):
+    """The xTC-FC folding at N=120 (two core orbitals, the 1s pair of the N2-like workload) of
+    device-resident Delta U / Delta h: one warm-up and five timed calls.  The fold is a gather of
+    the active block (8 B read + 8 B written per element) plus O(N^2 n_core) sums."""
+    from paper_2304_07006_gb300 import Context
+
+    N, core = 120, [0, 1]
+    n_act = N - len(core)
+    gen = torch.Generator(device=dev).manual_seed(11)
+    a = torch.randn((N,) * 4, dtype=torch.float64, device=dev, generator=gen)
+    dU = (a + a.permute(2, 3, 0, 1)) * 0.5
+    del a
+    dh = torch.randn((N, N), dtype=torch.float64, device=dev, generator=gen)
+    dh_fc = torch.empty((n_act, n_act), dtype=torch.float64, device=dev)
+    dU_act = torch.empty((n_act,) * 4, dtype=torch.float64, device=dev)
+    e = torch.empty(1, dtype=torch.float64, device=dev)
+    with Context(args.precision, device=local) as c:
+        c.frozen_core_fold(dU, dh, core, dh_fc=dh_fc, dU_act=dU_act, e_core=e)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(5):
+            c.frozen_core_fold(dU, dh, core, dh_fc=dh_fc, dU_act=dU_act, e_core=e)
+        torch.cuda.synchronize(dev)
+        sec = (time.perf_counter() - t0) / 5
+    nbytes = 16.0 * n_act ** 4
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    return {"workload": f"N={N}, core {core}, Delta U and Delta h on the device", "seconds_per_call": sec,
+            "achieved_gbs": nbytes / sec / 1e9, "frac_hbm": nbytes / sec / 1e9 / hbm,
+            "note": "wall time per C-ABI call (three kernels, synchronous); bytes = 16 x n_act^4"}
+
+
 def synth_config(name):
     import synth
     return synth.make_config(name)
@@ -537,6 +568,7 @@ def main():
             line["rohf"] = rohf_measure(args, torch, dev, local, p, ms_step / 1e3)
         line["three_body_L"] = three_body_measure(args, torch, dev, local)
         line["full_rank_density"] = fullrank_measure(args, torch, dev, local, p, per_kernel)
+        line["frozen_core_fold"] = frozen_core_measure(args, torch, dev, local, peaks)
         if args.large:
             free, _ = torch.cuda.mem_get_info(dev)
             line["large"] = (large_measure(args, torch, dev, local) if free > 100e9
