@@ -23,9 +23,10 @@
  *
  * Beside this closed-shell build the library offers the build for separate alpha and beta
  * densities of Appendix A (xtc_build_1b2b_rohf), a batched build of many instances
- * (xtc_build_1b2b_batched), the explicit L of eq. Ldecomp for small orbital sets as a validation
- * aid (xtc_three_body_L), steps (a) and (b) alone (xtc_jastrow_grad, xtc_vfield, and
- * xtc_vfield_noalloc, which allocates nothing) and a chunk autotuner (xtc_autotune_chunk).
+ * (xtc_build_1b2b_batched), the frozen-core folding of the corrections (xtc_frozen_core_fold),
+ * the explicit L of eq. Ldecomp for small orbital sets as a validation aid (xtc_three_body_L),
+ * steps (a) and (b) alone (xtc_jastrow_grad, xtc_vfield, and xtc_vfield_noalloc, which allocates
+ * nothing) and a chunk autotuner (xtc_autotune_chunk).
  *
  * Units are Hartree atomic units (bohr, Eh).  Conventions:
  *   - gamma is the per-spin (alpha) density matrix; the spin factor 2 is explicit
@@ -81,15 +82,17 @@ typedef enum {
 
 typedef enum {
   XTC_PREC_FP64 = 0,   /* all four steps in FP64 (SIMT) */
-  XTC_PREC_FP16X2 = 1, /* steps (b) and (d): block-exact 2-term FP16 split (3 tensor-core products)
-                          with power-of-2 scaling (per pair column of rho in step b, per row of L
-                          and R in step d): per block of 32 inner values hi = an integer of at most
-                          10 bits times the block's power-of-2 quantum, lo = the FP16 remainder, so
-                          the hi x hi products of a block sum exactly in the tensor core's FP32
-                          accumulator (no truncation bias); the cross products accumulate apart.
-                          FP32 running sums (round to nearest) flushed to FP64 every 8,192 inner
-                          points; FP64 accumulation of Delta U across grid chunks, of Delta h and
-                          of e0 */
+  XTC_PREC_FP16X2 = 1, /* steps (b) and (d): range-exact 2-term FP16 split with power-of-2 scaling
+                          (per pair column of rho in step b, per row of L and R in step d): per
+                          accumulation range (range_stages blocks of 32 inner values, default 2)
+                          hi = an integer times the range's power-of-2 quantum (step b: 9 bits for
+                          the gradient, 10 - log2(range) for rho; step d: (19 - log2(range)) / 2
+                          each), lo = the FP16 remainder, so the hi x hi products of a range sum
+                          exactly in the tensor core's FP32 accumulator (no truncation bias); the
+                          cross products (step b: hi x lo and lo x FP16(rho), step d: hi x lo,
+                          lo x hi, lo x lo) accumulate apart.  FP32 running sums (round to
+                          nearest) flushed to FP64 every 8,192 inner points; FP64 accumulation of
+                          Delta U across grid chunks, of Delta h and of e0 */
   XTC_PREC_BF16X3 = 2  /* steps (b) and (d): 3-term BF16 split (6 products) accumulated in the tensor
                           cores over short ranges (range_stages), otherwise as FP16X2; its FP32
                           accumulation truncates toward zero at every MMA, a one-signed error that
@@ -103,11 +106,13 @@ typedef struct {
   int64_t grid_chunk;  /* outer grid points per chunk (multiple of 128); 0 = automatic */
   int split_k;         /* inner-grid slices of step (b) accumulated separately (1..16); 0 = automatic */
   int timing;          /* non-zero: record CUDA events around every kernel (see xtc_get_timings) */
-  int range_stages;    /* XTC_PREC_BF16X3: inner-sum stages of 32 points accumulated in the tensor
-                          cores before a round-to-nearest FP32 add (1..4; at most 2 in step b and
-                          3 in step d).  That accumulator truncates toward zero, so the error grows
-                          with the range.  0 = default (1).  XTC_PREC_FP16X2 ignores it: its exact
-                          hi x hi ranges are one 32-point block */
+  int range_stages;    /* stages of 32 inner points per tensor-core accumulation range, 1..4;
+                          0 = default (2).  XTC_PREC_FP16X2: the range of the exact hi x hi sums
+                          (1, 2 or 4: the hi parts carry fewer bits on longer ranges so that every
+                          range sum stays exact; longer ranges mean fewer drains and larger lo
+                          parts).  XTC_PREC_BF16X3: stages accumulated in the tensor cores before a
+                          round-to-nearest FP32 add (at most 2 in step b and 3 in step d); that
+                          accumulator truncates toward zero, so the error grows with the range */
   /* Caller allocator for the device workspace (for instance a framework's caching allocator), or
    * both NULL for cudaMalloc / cudaFree.  alloc returns `bytes` of device memory of p->device
    * usable on p->stream, or NULL when it cannot (the call then fails with XTC_ERR_OOM); release

@@ -294,7 +294,9 @@ void launch_rb(const CUtensorMap* tm, const GfieldArgs& a, cudaStream_t st) {
 }
 template <int PARTS, int NNUC>
 void launch_t(const CUtensorMap* tm, const GfieldArgs& a, cudaStream_t st) {
-  if (PARTS == 2 && a.range_blocks == 2)
+  if (PARTS == 2 && a.range_blocks == 4)
+    launch_rb<PARTS, NNUC, 4>(tm, a, st);
+  else if (PARTS == 2 && a.range_blocks == 2)
     launch_rb<PARTS, NNUC, 2>(tm, a, st);
   else
     launch_rb<PARTS, NNUC, 1>(tm, a, st);

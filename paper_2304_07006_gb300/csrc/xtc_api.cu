@@ -287,10 +287,9 @@ int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t NGp, int parts, int64_t n_o
 }
 
 // Stages per exact accumulation range of the fp16 engine: the largest of 1, 2, 4 not above k (the
-// split tables hold one quantum per range, and chunk and grid lengths are multiples of 128 points);
-// step (b) at most 2 (the gradient kernel stages a whole range of its tiles in shared memory).
+// split tables hold one quantum per range, and chunk and grid lengths are multiples of 128 points).
 int f16_range(int k) { return k >= 4 ? 4 : (k >= 2 ? 2 : 1); }
-int f16_range_b(int k) { return std::min(f16_range(k), 2); }
+int f16_range_b(int k) { return f16_range(k); }
 
 // Ranges of kd stages (32 K values each) between FP64 flushes for a flush interval of `points` K
 // values (0: no flushes).

@@ -43,7 +43,7 @@ constexpr int GEMM_BITS_A = 9;
 __host__ __device__ constexpr int log2_kd(int kd) { return kd >= 8 ? 3 : kd >= 4 ? 2 : kd >= 2 ? 1 : 0; }
 __host__ __device__ constexpr int gemm_bits_b(int kd) { return 24 - 5 - GEMM_BITS_A - log2_kd(kd); }
 __host__ __device__ constexpr int gemm_bits_lr(int kd) { return (24 - 5 - log2_kd(kd)) / 2; }
-static_assert(GEMM_BITS_A + gemm_bits_b(2) + 5 + 1 <= 24 && 2 * gemm_bits_lr(4) + 5 + 2 <= 24, "exact ranges");
+static_assert(GEMM_BITS_A + gemm_bits_b(4) + 5 + 2 <= 24 && 2 * gemm_bits_lr(4) + 5 + 2 <= 24, "exact ranges");
 
 // Error codes written by kernels into the context's device error word.
 constexpr int DEV_ERR_TIMEOUT_VF = 1;

@@ -291,10 +291,12 @@ def test_n2_workload_sampled_outer_points(n2_sampled, prec):
     assert err < TOL[prec], err
 
 
-@pytest.mark.parametrize("stages", [2, 3, 4])
+@pytest.mark.parametrize("stages", [1, 3, 4])
 @pytest.mark.parametrize("prec", MIXED)
 def test_accumulation_range_lengths(small, prec, stages):
-    """Every tensor-core accumulation range length the parameter accepts (1 is the default)."""
+    """Every other tensor-core accumulation range length the parameter accepts (2, the default,
+    runs in every other test); fp16x2 takes 1, 2 or 4 (3 runs as 2), with the exact split's bits
+    shrinking as the range grows."""
     p, g, ref = small
     with ctx_for(p, prec, range_stages=stages) as c:
         out = c.build(p.grid, p.weights, p.phi, g)
