@@ -490,9 +490,9 @@ def main():
                 "ms_per_chunk": vf_ms, "algorithmic_flops_per_chunk": vf_flops_launch}
     asm_ms = kern_ms[3] / args.steps / n_vf
     asm_ach = F["d"] / n_vf / (asm_ms * 1e-3) / 1e12
-    # fp16x2 step (d) issues four split products per algorithmic one (hi x hi, hi x lo, lo x hi,
-    # lo x lo), step (b) three (hi x hi, hi x lo, lo x fp16(rho)); bf16x3 six in both
-    asm_factor = 4 if args.precision == "fp16x2" else 6
+    # fp16x2 issues three split products per algorithmic one in both GEMMs (hi x hi, hi x lo,
+    # lo x fp16(B)); bf16x3 six
+    asm_factor = 3 if args.precision == "fp16x2" else 6
     aux_ms = kern_ms[KERNEL_NAMES.index("aux")] / args.steps / n_vf
     assemble = {"kernel": "step d GEMM per chunk (fp16x2: vfield_tc in mode 1 on the split rows of L and R)",
                 "bound": "tensor", "achieved": asm_ach, "issued_tflops": asm_ach * asm_factor,

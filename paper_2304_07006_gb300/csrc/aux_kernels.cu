@@ -76,19 +76,6 @@ __global__ void check_finite_kernel(const double* __restrict__ x, int64_t n, int
 
 // ------------------------------------------------------------------ pair products rho
 // colmax[pq] = max_j |w_j phi_p(j) phi_q(j)| (as float bits; values are non-negative)
-__global__ void rho_colmax_kernel(const double* __restrict__ phiT, const double* __restrict__ w, int64_t n_grid,
-                                  int64_t n_pad, int n_pair, const int* __restrict__ pp, const int* __restrict__ pq_,
-                                  unsigned int* __restrict__ colmax) {
-  const int pq = blockIdx.y;
-  const int p = pp[pq], q = pq_[pq];
-  float m = 0.0f;
-  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n_grid;
-       j += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    m = fmaxf(m, static_cast<float>(fabs(w[j] * phiT[p * n_pad + j] * phiT[q * n_pad + j])));
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(colmax + pq, __float_as_uint(m));
-}
-
 // power-of-2 exponent that brings the column maximum near 2^14 (fp16 split); 0 when unscaled
 __device__ __forceinline__ int col_exponent(const unsigned int* colmax, int pq, bool scale) {
   if (!scale) return 0;
@@ -99,15 +86,64 @@ __device__ __forceinline__ int col_exponent(const unsigned int* colmax, int pq, 
   return min(max(14 - e, -60), 60);
 }
 
+// Orbitals and weights as FP32 pairs hi + lo (hi = the value rounded to FP32, lo = the FP32
+// rounding of the rest): row r < n_orb of dst is phi_r, row n_orb the weights; dst[part][row][j].
+__global__ void split_phi_f32_kernel(const double* __restrict__ phiT, const double* __restrict__ w, int64_t n_grid,
+                                     int64_t n_pad, int n_orb, float* __restrict__ dst) {
+  const int64_t rows = static_cast<int64_t>(n_orb) + 1, total = rows * n_pad;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < total;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = k / n_pad, j = k % n_pad;
+    const double v = r < n_orb ? phiT[k] : (j < n_grid ? w[j] : 0.0);
+    const float hi = static_cast<float>(v);
+    dst[k] = hi;
+    dst[total + k] = static_cast<float>(v - static_cast<double>(hi));
+  }
+}
+
+// w phi_p phi_q from the FP32 pairs of split_phi_f32_kernel as an unevaluated sum rh + rl (error-
+// free products by fma, then one renormalisation): about 2^-44 of the value, on the FP32 pipes.
+__device__ __forceinline__ void rho_pair_f32(const float* __restrict__ f32, int64_t total, int64_t n_pad, int n_orb,
+                                             int p, int q, int64_t j, float& rh, float& rl) {
+  const float ah = f32[p * n_pad + j], al = f32[total + p * n_pad + j];
+  const float bh = f32[q * n_pad + j], bl = f32[total + q * n_pad + j];
+  const float wh = f32[n_orb * n_pad + j], wl = f32[total + n_orb * n_pad + j];
+  const float xh = ah * bh;
+  const float xl = fmaf(ah, bh, -xh) + fmaf(ah, bl, al * bh);
+  const float yh = xh * wh;
+  const float yl = fmaf(xh, wh, -yh) + fmaf(xh, wl, xl * wh);
+  rh = yh + yl;
+  rl = yl - (rh - yh);
+}
+
+// Largest |rho| of each pair over the grid (FP32; it only picks the pair's power-of-2 scale).
+__global__ void rho_colmax_f32_kernel(const float* __restrict__ f32, int64_t n_grid, int64_t n_pad, int n_orb,
+                                      const int* __restrict__ pp, const int* __restrict__ pq_,
+                                      unsigned int* __restrict__ colmax) {
+  const int pq = blockIdx.y;
+  const int p = pp[pq], q = pq_[pq];
+  const int64_t total = (static_cast<int64_t>(n_orb) + 1) * n_pad;
+  float m = 0.0f;
+  for (int64_t j = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; j < n_grid;
+       j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float rh, rl;
+    rho_pair_f32(f32, total, n_pad, n_orb, p, q, j, rh, rl);
+    m = fmaxf(m, fabsf(rh));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(colmax + pq, __float_as_uint(m));
+}
+
 // fp16 (2 parts, exact split): warp w of the CTA handles pair pq = 8 * blockIdx.y + w over one
 // accumulation range of the GEMM, points j0 + lane + 32 s (s < kd, j0 = 32 kd blockIdx.x); the
-// range shares one quantum (largest |value| of the range, `bits` bits).  Layout: the two parts of a
-// 32-point block share one 128-byte row, [pq][j / 32][part][j % 32]; then the plane [pq][j] of the
-// value rounded to fp16.
-__global__ void rho_split_f16_kernel(const double* __restrict__ phiT, const double* __restrict__ w, int64_t n_grid,
-                                     int64_t n_pad, int n_pair, const int* __restrict__ pp,
-                                     const int* __restrict__ pq_, const unsigned int* __restrict__ colmax, int kd,
-                                     int bits, int* __restrict__ colexp, uint16_t* __restrict__ out) {
+// range shares one quantum (largest |value| of the range, `bits` bits).  rho = rh + rl in FP32
+// pairs (rho_pair_f32); hi = rh rounded to the quantum (exact), lo = fp16((rh - hi) + rl), whose
+// rounding error is far below fp16's.  Layout: the two parts of a 32-point block share one 128-byte
+// row, [pq][j / 32][part][j % 32]; then the plane [pq][j] of the value rounded to fp16.
+__global__ void rho_split_f16_kernel(const float* __restrict__ f32, int64_t n_grid, int64_t n_pad, int n_orb,
+                                     int n_pair, const int* __restrict__ pp, const int* __restrict__ pq_,
+                                     const unsigned int* __restrict__ colmax, int kd, int bits,
+                                     int* __restrict__ colexp, uint16_t* __restrict__ out) {
   const int lane = threadIdx.x & 31;
   const int pq = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (pq >= n_pair) return;  // whole warp
@@ -115,27 +151,34 @@ __global__ void rho_split_f16_kernel(const double* __restrict__ phiT, const doub
   if (blockIdx.x == 0 && lane == 0) colexp[pq] = e;
   const int p = pp[pq], q = pq_[pq];
   const int64_t j0 = static_cast<int64_t>(blockIdx.x) * 32 * kd;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  double m = 0.0;
+  const int64_t total = (static_cast<int64_t>(n_orb) + 1) * n_pad;
+  const float sc = pow2f(e);  // |e| <= 60: exact scaling
+  float vh[4] = {0.0f, 0.0f, 0.0f, 0.0f}, vl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  float m = 0.0f;
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const int64_t j = j0 + 32 * s + lane;
-    if (s < kd && j < n_grid) v[s] = ldexp(w[j] * phiT[p * n_pad + j] * phiT[q * n_pad + j], e);
-    m = fmax(m, fabs(v[s]));
+    if (s < kd && j < n_grid) {
+      float rh, rl;
+      rho_pair_f32(f32, total, n_pad, n_orb, p, q, j, rh, rl);
+      vh[s] = rh * sc;
+      vl[s] = rl * sc;
+    }
+    m = fmaxf(m, fabsf(vh[s]));
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   const int qe = exact_quantum(m, bits);
   uint16_t* out16 = out + static_cast<int64_t>(n_pair) * 2 * n_pad;  // the fp16(rho) plane
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
     const int64_t j = j0 + 32 * s + lane;
     if (s >= kd || j >= n_pad) break;
-    __half h, l;
-    split_exact(v[s], qe, h, l);
+    float h = 0.0f;
+    if (qe >= -24) h = rintf(vh[s] * pow2f(-qe)) * pow2f(qe);  // both products exact (powers of 2)
     const int64_t o = static_cast<int64_t>(pq) * 2 * n_pad + (j >> 5) * 64 + (j & 31);
-    out[o] = __half_as_ushort(h);
-    out[o + 32] = __half_as_ushort(l);
-    out16[static_cast<int64_t>(pq) * n_pad + j] = __half_as_ushort(__double2half(v[s]));
+    out[o] = __half_as_ushort(__float2half_rn(h));                      // exact: at most 10 bits
+    out[o + 32] = __half_as_ushort(__float2half_rn((vh[s] - h) + vl[s]));  // vh - h is exact
+    out16[static_cast<int64_t>(pq) * n_pad + j] = __half_as_ushort(__float2half_rn(vh[s]));
   }
 }
 
@@ -172,7 +215,8 @@ __global__ void rho_split_bf16_kernel(const double* __restrict__ phiT, const dou
 // (k = kc * i + c) and the split row is written component-major (k' = c * (kdim / kc) + i), so that
 // a range never mixes components; with kc = 1 the order is kept.
 __global__ void __launch_bounds__(256) lr_split_kernel(const float* __restrict__ src, int64_t kdim, int kc, int kd,
-                                                       int bits, uint16_t* __restrict__ dst, int* __restrict__ exps) {
+                                                       int bits, uint16_t* __restrict__ dst, int* __restrict__ exps,
+                                                       uint16_t* __restrict__ dst16) {
   __shared__ float red[8];
   const int64_t r = blockIdx.x;
   const float* s = src + r * kdim;
@@ -228,9 +272,11 @@ __global__ void __launch_bounds__(256) lr_split_kernel(const float* __restrict__
         if (t >= kd) break;
         __half h, l;
         split_exact(v[t][c], qe, h, l);
-        const int64_t blk = (c * per_c + 32 * (kd * g + t)) >> 5;  // 32-value block of the split row
+        const int64_t kk = c * per_c + 32 * (kd * g + t);  // first value of the 32-value block
+        const int64_t blk = kk >> 5;
         d[blk * 64 + lane] = __half_as_ushort(h);
         d[blk * 64 + 32 + lane] = __half_as_ushort(l);
+        if (dst16) dst16[r * kdim + kk + lane] = __half_as_ushort(__float2half_rn(v[t][c]));
       }
     }
   }
@@ -604,15 +650,19 @@ void launch_check_finite(const double* x, int64_t n, int* flag, cudaStream_t st)
 }
 
 void launch_rho_split(const double* phiT, const double* w, int64_t n_grid, int64_t n_pad, int n_orb, int parts, int kd,
-                      const int* pp, const int* pq, unsigned int* colmax, int* colexp, void* out, cudaStream_t st) {
+                      const int* pp, const int* pq, unsigned int* colmax, int* colexp, float* phi32, void* out,
+                      cudaStream_t st) {
   const int n_pair = n_orb * (n_orb + 1) / 2;
   if (parts == 2) {
+    const int64_t total = (static_cast<int64_t>(n_orb) + 1) * n_pad;
+    split_phi_f32_kernel<<<std::min<unsigned int>(blocks_for(total, 256), 8192u), 256, 0, st>>>(phiT, w, n_grid,
+                                                                                                n_pad, n_orb, phi32);
     cudaMemsetAsync(colmax, 0, sizeof(unsigned int) * n_pair, st);
     dim3 g(std::min<unsigned int>(blocks_for(n_grid, 256), 64u), n_pair);
-    rho_colmax_kernel<<<g, 256, 0, st>>>(phiT, w, n_grid, n_pad, n_pair, pp, pq, colmax);
+    rho_colmax_f32_kernel<<<g, 256, 0, st>>>(phi32, n_grid, n_pad, n_orb, pp, pq, colmax);
     dim3 g2(static_cast<unsigned int>(n_pad / (32 * kd)), blocks_for(n_pair, 8));
-    rho_split_f16_kernel<<<g2, 256, 0, st>>>(phiT, w, n_grid, n_pad, n_pair, pp, pq, colmax, kd, gemm_bits_b(kd),
-                                              colexp, static_cast<uint16_t*>(out));
+    rho_split_f16_kernel<<<g2, 256, 0, st>>>(phi32, n_grid, n_pad, n_orb, n_pair, pp, pq, colmax, kd,
+                                              gemm_bits_b(kd), colexp, static_cast<uint16_t*>(out));
   } else {
     dim3 g2(blocks_for(n_pad, 256), blocks_for(n_pair, 8));
     rho_split_bf16_kernel<<<g2, 256, 0, st>>>(phiT, w, n_grid, n_pad, n_pair, pp, pq, colexp,
@@ -621,9 +671,9 @@ void launch_rho_split(const double* phiT, const double* w, int64_t n_grid, int64
 }
 
 void launch_lr_split(const float* src, int rows, int64_t kdim, int kc, int kd, uint16_t* dst, int* exps,
-                     cudaStream_t st) {
+                     uint16_t* dst16, cudaStream_t st) {
   if (rows <= 0) return;
-  lr_split_kernel<<<rows, 256, 0, st>>>(src, kdim, kc, kd, gemm_bits_lr(kd), dst, exps);
+  lr_split_kernel<<<rows, 256, 0, st>>>(src, kdim, kc, kd, gemm_bits_lr(kd), dst, exps, dst16);
 }
 
 void launch_rho_f64(const double* phi, const double* w, int64_t n_grid, int64_t n_pad, int n_orb, const int* pp,

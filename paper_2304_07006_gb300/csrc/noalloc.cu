@@ -147,6 +147,7 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
       c.take<uint16_t>(static_cast<size_t>(3) * NP * NGp);
       c.take<unsigned int>(NP);
       c.take<int>(NP);
+      c.take<float>(static_cast<size_t>(2) * (N + 1) * NGp);
       c.take<float>(static_cast<size_t>(v_slice(gc, N)));
       c.take<uint16_t>(static_cast<size_t>(parts) * 3 * gc * NGp);
     }
@@ -191,11 +192,12 @@ extern "C" XTC_API int xtc_vfield_noalloc(xtc_ctx* ctx, int64_t n_grid, int n_or
     rho = cz.take<uint16_t>(static_cast<size_t>(3) * NP * NGp);  // fp16: split rows + fp16 plane
     unsigned int* colmax = cz.take<unsigned int>(NP);
     colexp = cz.take<int>(NP);
+    float* phi32 = cz.take<float>(static_cast<size_t>(2) * (N + 1) * NGp);
     Vbuf = cz.take<float>(static_cast<size_t>(v_slice(gc, N)));
     void* G = cz.take<uint16_t>(static_cast<size_t>(parts) * 3 * gc * NGp);
     launch_transpose_phi(phi, n_grid, NGp, N, phiT, st);
     launch_jtab(grid_xyz, n_grid, NGp, cv.jp_dev, n_nuc, jtab_stride(n_nuc), jtab, st);
-    launch_rho_split(phiT, weights, n_grid, NGp, N, parts, kd_b, pair_p, pair_q, colmax, colexp, rho, st);
+    launch_rho_split(phiT, weights, n_grid, NGp, N, parts, kd_b, pair_p, pair_q, colmax, colexp, phi32, rho, st);
     // rho^T (box rows vf_bn) and the gradient table [part][x * gc + il][j] (boxes 32 x 32
     // for the step (a) stores and 32 x 128 for the step (b) loads)
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(cv.encode_tiled);

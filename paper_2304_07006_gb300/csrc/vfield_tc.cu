@@ -19,19 +19,19 @@
 // follow the rounding remainders rather than the data) go into a second accumulator X, drained
 // every `xper` stages; their truncation is 2^-9 smaller and does not accumulate one-sided.  They
 // must include lo_a x lo_b: where both operands hold values far below their range's maximum, hi is
-// 0 and lo is the whole value.  Step (d) issues hi_a x lo_b, lo_a x hi_b and lo_a x lo_b.  Step (b)
-// issues hi_a x lo_b and lo_a x fp16(b), with fp16(b) a third plane of rho^T: lo_a x (hi_b + lo_b)
-// to within fp16's rounding of b (a relative 2^-12 of a term that is itself 2^-10 of the product),
-// one product where two would be needed.
+// 0 and lo is the whole value.  Both steps issue hi_a x lo_b and lo_a x fp16(b), with fp16(b) a
+// third plane of the B operand (rho^T in step (b), R in step (d)): lo_a x (hi_b + lo_b) to within
+// fp16's rounding of b (a relative 2^-12 of a term that is itself 2^-10 of the product), one
+// product where two would be needed.
 //
 // Tile 128 A rows x 128 columns, 32 K values per stage, both parts of a row of a block in one
 // 128-byte row (128-byte swizzle; one TMA box per operand part and stage).  Measured
 // on GB300: one thread issues a 128 x 128 x 16 MMA every ~50 cycles (the pipe takes 64), an MMA
 // and its commit round-trip in ~360 cycles, and a range's round trip (its MMAs complete, the
 // commit arrives, the drains read E, E is handed back) takes on the order of a thousand cycles.
-// So ranges span two stages (12 MMAs, 16 in step (d)), and two issuers alternate ranges, each with
-// its own accumulator pair (TMEM: E0, X0, E1, X1 = 4 x 128 of 512 columns).  Step (b) stages hold
-// 40 KB (A, B hi/lo, fp16(B): 5 stages), step (d) stages 32 KB (7 stages).  Warp roles:
+// So ranges span two stages (12 MMAs), and two issuers alternate ranges, each with its own
+// accumulator pair (TMEM: E0, X0, E1, X1 = 4 x 128 of 512 columns).  A stage holds 40 KB (A and B
+// hi/lo, fp16(B)); 5 stages.  Warp roles:
 //   * warp 0 (one lane): TMA loads; a slot is reloaded once the MMAs of its stage have completed;
 //   * warps 1 and 2 (one lane each): the MMAs of the even / odd ranges, a commit per stage (it
 //     frees the slot) and one per range (it starts the drains);
@@ -90,10 +90,10 @@ constexpr int XB_DRAIN_WARPS = 16;                // four per TMEM lane quarter,
 constexpr int XB_HC = XB_BN / 4;                  // running-sum columns per drain thread
 constexpr int XB_A_BYTES = VF_BM * 128;           // 128 rows of 128 bytes (hi and lo of 32 values)
 constexpr int XB_B_BYTES = XB_BN * 128;
-constexpr int XB_B16_BYTES = XB_BN * 64;          // step (b): fp16(rho) of the B rows, 64-byte rows
-// stage bytes and pipeline depth: step (b) 40 KB (A, B hi/lo, B fp16) x 5, step (d) 32 KB x 7
-__host__ __device__ constexpr int xb_stage(int mode) { return XB_A_BYTES + XB_B_BYTES + (mode == 0 ? XB_B16_BYTES : 0); }
-__host__ __device__ constexpr int xb_stages(int mode) { return mode == 0 ? 5 : 7; }
+constexpr int XB_B16_BYTES = XB_BN * 64;          // fp16(B) of the B rows, 64-byte rows
+// stage bytes and pipeline depth: 40 KB (A, B hi/lo, B fp16) x 5
+__host__ __device__ constexpr int xb_stage(int) { return XB_A_BYTES + XB_B_BYTES + XB_B16_BYTES; }
+__host__ __device__ constexpr int xb_stages(int) { return 5; }
 constexpr int XB_STAGES = 7;                      // the larger depth (barrier arrays)
 constexpr int XB_WARP_I0 = 1, XB_WARP_I1 = 2;      // issuers of the even / odd ranges; drains 3..18
 constexpr int XB_THREADS = (3 + XB_DRAIN_WARPS) * 32;  // TMA warp, two MMA warps, drains
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
     fence_mbar_init();
     tma_prefetch_desc(&tm_a);
     tma_prefetch_desc(&tm_b);
-    if (MODE == 0) tma_prefetch_desc(&tm_b16);
+    tma_prefetch_desc(&tm_b16);
   }
   if (warp == 0) {
     tmem_alloc(tmem_slot, 512);
@@ -189,8 +189,7 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
         uint8_t* st = smem + s * XB_STAGE;
         tma_load_3d(st, &tm_a, &tma_full[s], (kb0 + it) * 2 * VF_BK, row0, 0);
         tma_load_3d(st + XB_A_BYTES, &tm_b, &tma_full[s], (kb0 + it) * 2 * VF_BK, t.n_tile * XB_BN, 0);
-        if (MODE == 0)
-          tma_load_3d(st + XB_A_BYTES + XB_B_BYTES, &tm_b16, &tma_full[s], (kb0 + it) * VF_BK, t.n_tile * XB_BN, 0);
+        tma_load_3d(st + XB_A_BYTES + XB_B_BYTES, &tm_b16, &tma_full[s], (kb0 + it) * VF_BK, t.n_tile * XB_BN, 0);
         issued = it + 1;
       }
       // the copies still in flight land before the CTA may exit
@@ -230,17 +229,10 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
           tc_mma_f16(e_tmem, da + 2, db + 2, idesc, 1u);
           tc_mma_f16(x_tmem, da, db + 4, idesc, (x_start && it == it0) ? 0u : 1u);   // hi_a x lo_b
           tc_mma_f16(x_tmem, da + 2, db + 6, idesc, 1u);
-          if (MODE == 0) {
-            // lo_a x fp16(b): lo_a x (hi_b + lo_b) to within fp16(b)'s rounding, one product
-            const uint64_t d16 = sw64_desc(sa + XB_A_BYTES + XB_B_BYTES);
-            tc_mma_f16(x_tmem, da + 4, d16, idesc, 1u);
-            tc_mma_f16(x_tmem, da + 6, d16 + 2, idesc, 1u);
-          } else {
-            tc_mma_f16(x_tmem, da + 4, db, idesc, 1u);                                 // lo_a x hi_b
-            tc_mma_f16(x_tmem, da + 6, db + 2, idesc, 1u);
-            tc_mma_f16(x_tmem, da + 4, db + 4, idesc, 1u);                             // lo_a x lo_b
-            tc_mma_f16(x_tmem, da + 6, db + 6, idesc, 1u);
-          }
+          // lo_a x fp16(b): lo_a x (hi_b + lo_b) to within fp16(b)'s rounding, one product
+          const uint64_t d16 = sw64_desc(sa + XB_A_BYTES + XB_B_BYTES);
+          tc_mma_f16(x_tmem, da + 4, d16, idesc, 1u);
+          tc_mma_f16(x_tmem, da + 6, d16 + 2, idesc, 1u);
           tc_commit(&sfree[s]);
         }
         if (!alive) break;
@@ -616,7 +608,7 @@ void launch_vfield_tc(const CUtensorMap* tm_g, const CUtensorMap* tm_rho, const 
   dim3 grid(static_cast<unsigned>(m_tiles_of(a) * a.n_tiles), static_cast<unsigned>(splits));
   if (a.mode == 1) {
     cudaFuncSetAttribute(xgemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, xb_smem(1));
-    xgemm_kernel<1><<<grid, XB_THREADS, xb_smem(1), st>>>(*tm_g, *tm_rho, *tm_rho, a);
+    xgemm_kernel<1><<<grid, XB_THREADS, xb_smem(1), st>>>(*tm_g, *tm_rho, *tm_rho16, a);
   } else if (parts == 2) {
     cudaFuncSetAttribute(xgemm_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, xb_smem(0));
     xgemm_kernel<0><<<grid, XB_THREADS, xb_smem(0), st>>>(*tm_g, *tm_rho, *tm_rho16, a);

@@ -89,7 +89,7 @@ struct xtc_ctx {
   char detail[512] = {0};
   // device workspace
   DBuf jp_dev, err_dev, flag_dev;
-  DBuf grid, w, phi, gamma, phiT, pair_p, pair_q;
+  DBuf grid, w, phi, gamma, phiT, phi32, pair_p, pair_q;
   DBuf jtab, jtab64, rho, colmax, colexp, G;
   DBuf V, Vacc, L, R, L32, R32, eL, eR, M, evec, lam, dU_tmp, dh_tmp, e0_tmp, vout, r1, r2;
   DBuf lamd, gamma_b, M2, M3;  // direct weights; spin builds: beta density, f^b, Delta U^{ab}
@@ -114,7 +114,7 @@ struct xtc_ctx {
   std::vector<cudaStream_t> lane_streams;
 
   std::vector<DBuf*> buffers() {
-    return {&jp_dev, &err_dev, &flag_dev, &grid, &w, &phi, &gamma, &phiT, &pair_p, &pair_q, &jtab, &jtab64,
+    return {&jp_dev, &err_dev, &flag_dev, &grid, &w, &phi, &gamma, &phiT, &phi32, &pair_p, &pair_q, &jtab, &jtab64,
             &rho, &colmax, &colexp, &G, &V, &Vacc, &L, &R, &L32, &R32, &eL, &eR, &M, &evec, &lam, &dU_tmp,
             &dh_tmp, &e0_tmp, &vout, &r1, &r2, &lamd, &gamma_b, &M2, &M3, &lam2, &R2, &R32b, &eR2, &Lv, &T3,
             &fc_U, &fc_h, &fc_hout, &fc_Uout};
@@ -264,7 +264,8 @@ int64_t auto_chunk(const xtc_ctx* c, int NP, int64_t NGp, int parts, int64_t n_o
   // then the chunk that fills whole waves of the step (b) GEMM best
   const double vbytes = f64 ? 3.0 * 8 : 3.0 * 4;
   // step (d) operands per pair and outer point: FP64 L, R; bf16 x3 L, R; or FP32 L, R + fp16 x2 split
-  const double lrbytes = f64 ? 2 * 4 * 8.0 : (parts == 2 ? 2 * 4 * (4.0 + 4.0) : 2 * 3 * 4 * 2.0);
+  // and the fp16(R) plane
+  const double lrbytes = f64 ? 2 * 4 * 8.0 : (parts == 2 ? 2 * 4 * (4.0 + 4.0) + 4 * 2.0 : 2 * 3 * 4 * 2.0);
   // V holds the whole N x N matrix per point (N^2 < 2 NP)
   const double per_point = NP * (2.0 * vbytes + lrbytes);
   int64_t cap = static_cast<int64_t>(budget_scale * 12.0e9 / per_point);
@@ -541,10 +542,10 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
     const int js = jtab_stride(n_nuc);
     if (!ensure(ctx->jtab, sizeof(float) * pl.NGp * js) ||
         !ensure(ctx->rho, 2ull * 3 * pl.NGp * pl.NP) || !ensure(ctx->colmax, 4ull * pl.NP) ||
-        !ensure(ctx->colexp, 4ull * pl.NP))
+        !ensure(ctx->colexp, 4ull * pl.NP) || !ensure(ctx->phi32, 8ull * (n_orb + 1) * pl.NGp))
       return fail(ctx, XTC_ERR_OOM, "grid tables (%.2f GB)", 2.0 * 3 * pl.NGp * pl.NP / 1e9);
   }
-  const int nprep = f64 ? 3 : (pl.parts_b == 2 ? 4 : 3);
+  const int nprep = f64 ? 3 : (pl.parts_b == 2 ? 5 : 3);
   timed(ctx, XTC_K_PREP, nprep, [&] {
     launch_transpose_phi(*d_phi, n_grid, pl.NGp, n_orb, ctx->phiT.as<double>(), st);
     if (f64) {
@@ -556,7 +557,7 @@ int prepare(xtc_ctx* ctx, Plan& pl, int64_t n_grid, int n_orb, const double* gri
       launch_jtab(*d_grid, n_grid, pl.NGp, ctx->jp_dev.as<JastrowParams>(), n_nuc, js, ctx->jtab.as<float>(), st);
       launch_rho_split(ctx->phiT.as<double>(), *d_w, n_grid, pl.NGp, n_orb, pl.parts_b, f16_range_b(ctx->vf_kd),
                        ctx->pair_p.as<int>(), ctx->pair_q.as<int>(), ctx->colmax.as<unsigned int>(),
-                       ctx->colexp.as<int>(), ctx->rho.p, st);
+                       ctx->colexp.as<int>(), ctx->phi32.as<float>(), ctx->rho.p, st);
     }
   });
   const size_t vbytes = static_cast<size_t>(pl.splits) * v_slice(pl.gc, pl.N) * (f64 ? 8 : 4);
@@ -795,7 +796,9 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
   const int64_t kdim = 4 * pl.gc;
   const bool d16 = !pl.f64 && pl.parts_b == 2;
   const size_t lr_bytes = pl.f64 ? 8ull * kdim * NP : (d16 ? 4ull * kdim * NP : 2ull * 3 * kdim * NP);
-  if (!ensure(ctx->L, lr_bytes) || !ensure(ctx->R, lr_bytes) || (spin && !ensure(ctx->R2, lr_bytes)))
+  // fp16x2: R (and R2) carry the plane fp16(R) after the split rows
+  const size_t r_bytes = lr_bytes + (d16 ? 2ull * kdim * NP : 0);
+  if (!ensure(ctx->L, lr_bytes) || !ensure(ctx->R, r_bytes) || (spin && !ensure(ctx->R2, r_bytes)))
     return fail(ctx, XTC_ERR_OOM, "step (d) operands (%.2f GB)", (spin ? 3.0 : 2.0) * lr_bytes / 1e9);
   if (d16) {
     const size_t ebytes = 4ull * m_stride(NP);
@@ -811,12 +814,18 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
     if (spin) CUDA_OK(cudaMemsetAsync(ctx->eR2.p, 0, ebytes, st));
   }
   VfMaps maps{};
-  CUtensorMap tm_L{}, tm_R{}, tm_R2{};
+  CUtensorMap tm_L{}, tm_R{}, tm_R2{}, tm_R16{}, tm_R216{};
   if ((rc = make_vfield_maps(ctx, pl, maps))) return rc;
   if (d16) {
     if ((rc = make_tmap_3d(ctx, &tm_L, ctx->L.p, false, 2 * kdim, NP, 1, 2 * VF_BK, VF_BM, true))) return rc;
     if ((rc = make_tmap_3d(ctx, &tm_R, ctx->R.p, false, 2 * kdim, NP, 1, 2 * VF_BK, vf_bn(2), true))) return rc;
     if (spin && (rc = make_tmap_3d(ctx, &tm_R2, ctx->R2.p, false, 2 * kdim, NP, 1, 2 * VF_BK, vf_bn(2), true)))
+      return rc;
+    // the fp16(R) planes, boxes 32 wide (64-byte swizzle)
+    if ((rc = make_tmap_3d(ctx, &tm_R16, ctx->R.as<uint16_t>() + 2 * kdim * NP, false, kdim, NP, 1, VF_BK, vf_bn(2))))
+      return rc;
+    if (spin &&
+        (rc = make_tmap_3d(ctx, &tm_R216, ctx->R2.as<uint16_t>() + 2 * kdim * NP, false, kdim, NP, 1, VF_BK, vf_bn(2))))
       return rc;
   } else if (!pl.f64) {
     if ((rc = make_tmap_3d(ctx, &tm_L, ctx->L.p, true, kdim, NP, 3, AS_BK, AS_BM))) return rc;
@@ -908,18 +917,21 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
         da.exp_b = ctx->eR.as<int>();
         da.err = ctx->err_dev.as<int>();
         timed(ctx, XTC_K_AUX, M2 ? 3 : 2, [&] {
-          launch_lr_split(ctx->L32.as<float>(), NP, kdim, 4, da.kd, ctx->L.as<uint16_t>(), ctx->eL.as<int>(), st);
-          launch_lr_split(ctx->R32.as<float>(), NP, kdim, 4, da.kd, ctx->R.as<uint16_t>(), ctx->eR.as<int>(), st);
+          launch_lr_split(ctx->L32.as<float>(), NP, kdim, 4, da.kd, ctx->L.as<uint16_t>(), ctx->eL.as<int>(), nullptr,
+                          st);
+          launch_lr_split(ctx->R32.as<float>(), NP, kdim, 4, da.kd, ctx->R.as<uint16_t>(), ctx->eR.as<int>(),
+                          ctx->R.as<uint16_t>() + 2 * kdim * NP, st);
           if (M2)
-            launch_lr_split(ctx->R32b.as<float>(), NP, kdim, 4, da.kd, ctx->R2.as<uint16_t>(), ctx->eR2.as<int>(), st);
+            launch_lr_split(ctx->R32b.as<float>(), NP, kdim, 4, da.kd, ctx->R2.as<uint16_t>(), ctx->eR2.as<int>(),
+                            ctx->R2.as<uint16_t>() + 2 * kdim * NP, st);
         });
-        timed(ctx, XTC_K_ASSEMBLE, 1, [&] { launch_vfield_tc(&tm_L, &tm_R, nullptr, da, 2, 1, st); });
+        timed(ctx, XTC_K_ASSEMBLE, 1, [&] { launch_vfield_tc(&tm_L, &tm_R, &tm_R16, da, 2, 1, st); });
         timed(ctx, XTC_K_AUX, 1, [&] { launch_vfield_tc_finalize(da, 2, 1, st); });
         if (M2) {  // the tile sums buffer is reused after the finalize above, in stream order
           VfieldArgs db = da;
           db.M = M2;
           db.exp_b = ctx->eR2.as<int>();
-          timed(ctx, XTC_K_ASSEMBLE, 1, [&] { launch_vfield_tc(&tm_L, &tm_R2, nullptr, db, 2, 1, st); });
+          timed(ctx, XTC_K_ASSEMBLE, 1, [&] { launch_vfield_tc(&tm_L, &tm_R2, &tm_R216, db, 2, 1, st); });
           timed(ctx, XTC_K_AUX, 1, [&] { launch_vfield_tc_finalize(db, 2, 1, st); });
         }
       } else if (pl.f64) {

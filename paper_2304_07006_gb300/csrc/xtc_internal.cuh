@@ -111,11 +111,12 @@ void launch_jtab(const double* grid, int64_t n_grid, int64_t n_grid_pad, const J
 // row scaled by a power of 2 (colexp[pq] receives the exponent; colmax is scratch) and split exactly
 // with one quantum per range of kd blocks of 32 points (gemm_bits_b(kd) bits), the two parts of a
 // block in one 128-byte row: [pq][j / 32][part][j % 32], followed by a plane of the scaled value
-// rounded to fp16, [pq][j] (2 x n_pair x n_pad values, then n_pair x n_pad).  bf16 (3 parts):
+// rounded to fp16, [pq][j] (2 x n_pair x n_pad values, then n_pair x n_pad); the products are
+// taken in FP32 pairs hi + lo from phi32, scratch of 2 (n_orb + 1) n_pad floats.  bf16 (3 parts):
 // per-element split, unscaled (colexp = 0), [part][pq][j].  n_pad must be a multiple of 32 kd.
 void launch_rho_split(const double* phiT, const double* w, int64_t n_grid, int64_t n_pad, int n_orb, int parts, int kd,
-                      const int* pair_p, const int* pair_q, unsigned int* colmax, int* colexp, void* out,
-                      cudaStream_t st);
+                      const int* pair_p, const int* pair_q, unsigned int* colmax, int* colexp, float* phi32,
+                      void* out, cudaStream_t st);
 
 // FP64 pair products rho[j][pq] for the FP64 path (n_grid_pad rows, zero padded).
 void launch_rho_f64(const double* phi, const double* w, int64_t n_grid, int64_t n_grid_pad, int n_orb,
@@ -232,9 +233,10 @@ void launch_fields(const FieldsArgs& a, bool f64, cudaStream_t st);  // f64: FP6
 // blocks of 32 values (gemm_bits_lr(kd) bits), both parts of a block in one 128-byte row:
 // dst[r][k' / 32][part][k' % 32].  kc = 4: the source holds 4 values per outer point (k = 4 i + c)
 // and k' = c * kdim / 4 + i (component-major, so that a range never mixes components); kc = 1:
-// k' = k.  kdim / kc must be a multiple of 32 kd.
+// k' = k.  kdim / kc must be a multiple of 32 kd.  dst16 (or NULL): the scaled values rounded to
+// fp16, dst16[r][k'] (the plane of the B operand, for the lo x fp16(B) product).
 void launch_lr_split(const float* src, int rows, int64_t kdim, int kc, int kd, uint16_t* dst, int* exps,
-                     cudaStream_t st);
+                     uint16_t* dst16, cudaStream_t st);
 
 // Step (d), tensor cores, bf16 x3: M[pq][rs] += sum_k L[pq][k] R[rs][k] over k < kdim (FP64 accumulator).
 void launch_assemble_tc(const CUtensorMap* tm_L, const CUtensorMap* tm_R, int n_pair, int kdim, int kd, double* M,
