@@ -115,7 +115,7 @@ class Clocks:
 # dram__bytes_read.sum + dram__bytes_write.sum of one step (b) GEMM launch (fp16x2) captured with
 # ncu on the first VFIELD_CAPTURE_OUTER outer points of the workload (`--ncu-case`), for GEMM
 # engine revision VFIELD_CAPTURE_REVISION; with another revision the traffic is reported as null
-VFIELD_CAPTURE_REVISION = 3
+VFIELD_CAPTURE_REVISION = 4
 VFIELD_DRAM_BYTES_CAPTURED = 29_676_537_856 + 2_914_678_528
 VFIELD_CAPTURE_OUTER = 1184
 

@@ -89,8 +89,8 @@ typedef enum {
                           the gradient, 10 - log2(range) for rho; step d: (19 - log2(range)) / 2
                           each), lo = the FP16 remainder, so the hi x hi products of a range sum
                           exactly in the tensor core's FP32 accumulator (no truncation bias); the
-                          cross products (step b: hi x lo and lo x FP16(rho), step d: hi x lo,
-                          lo x hi, lo x lo) accumulate apart.  FP32 running sums (round to
+                          cross products hi x lo and lo x FP16(B) (B = rho in step b, R in step d)
+                          accumulate apart.  FP32 running sums (round to
                           nearest) flushed to FP64 every 8,192 inner points; FP64 accumulation of
                           Delta U across grid chunks, of Delta h and of e0 */
   XTC_PREC_BF16X3 = 2  /* steps (b) and (d): 3-term BF16 split (6 products) accumulated in the tensor

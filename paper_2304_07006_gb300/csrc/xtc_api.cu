@@ -442,7 +442,7 @@ int xtc_set_outer_range(xtc_ctx* ctx, int64_t begin, int64_t end) {
 // 1: one accumulator per range of kd stages, truncating FP32 accumulation (192-column tiles);
 // 2: block-exact fp16 split, exact hi x hi accumulator pair plus a cross-product accumulator
 //    (160-column tiles).
-int xtc_engine_revision(void) { return 3; }
+int xtc_engine_revision(void) { return 4; }
 
 int xtc_get_timings(xtc_ctx* ctx, double* ms, int64_t* launches, int n) {
   if (!ctx || n < XTC_N_KERNELS) return XTC_ERR_ARG;
