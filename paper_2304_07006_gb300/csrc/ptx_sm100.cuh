@@ -66,8 +66,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   return true;
 }
 
-// The same with a non-suspending test in a tight loop: for the single threads that issue MMAs,
-// where the wake-up latency of a suspended wait sits on the critical path.
+// The same with a non-suspending test in a tight loop: for the threads that issue MMAs and the
+// warps that drain their accumulators, where the wake-up latency of a suspended wait sits on the
+// critical path.
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(

@@ -283,8 +283,9 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
       const int k = r & 1, u = r >> 1;
       // X_k is drained at the end of each of its periods and after issuer k's last range
       const bool x_end = u % xr == xr - 1 || r + 2 >= n_ranges;
+      // a non-suspending wait: the drain's wake-up sits on the range round trip
       ok = __all_sync(0xffffffffu,
-                      mbar_wait(&rdone[r % NRB], (r / NRB) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF));
+                      mbar_spin(&rdone[r % NRB], (r / NRB) & 1, abort_flag, args.err, DEV_ERR_TIMEOUT_VF));
       __syncwarp();
       if (!ok) break;
       tc_fence_after();
