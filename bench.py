@@ -116,7 +116,7 @@ class Clocks:
 # ncu on the first VFIELD_CAPTURE_OUTER outer points of the workload (`--ncu-case`), for GEMM
 # engine revision VFIELD_CAPTURE_REVISION; with another revision the traffic is reported as null
 VFIELD_CAPTURE_REVISION = 4
-VFIELD_DRAM_BYTES_CAPTURED = 29_676_537_856 + 2_914_678_528
+VFIELD_DRAM_BYTES_CAPTURED = 24_858_260_480 + 2_878_889_472
 VFIELD_CAPTURE_OUTER = 1184
 
 
