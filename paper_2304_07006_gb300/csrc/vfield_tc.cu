@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(XB_THREADS, 1)
     if (lane == 0) {
       // ---------------------------------------------------------------- MMA issuers
       // Issuer k takes the ranges r = k, k + 2, ...: per stage the hi x hi products into E_k (a
-      // fresh, exact accumulation per range) and the cross products lo x hi, hi x lo (and in step
-      // (d) lo x lo) into X_k (restarted every xr of its ranges); a commit after each stage frees
+      // fresh, exact accumulation per range) and the cross products hi_a x lo_b, lo_a x fp16(b)
+      // into X_k (restarted every xr of its ranges); a commit after each stage frees
       // its slot for the next load, one after each range starts the drains.  With two issuers
       // one's waits and commits overlap the other's MMAs, and neither waits for the other's drains.
       constexpr uint32_t idesc = idesc_f16(VF_BM, XB_BN, false);

@@ -440,8 +440,10 @@ int xtc_set_outer_range(xtc_ctx* ctx, int64_t begin, int64_t end) {
 }
 
 // 1: one accumulator per range of kd stages, truncating FP32 accumulation (192-column tiles);
-// 2: block-exact fp16 split, exact hi x hi accumulator pair plus a cross-product accumulator
-//    (160-column tiles).
+// 2: exact fp16 split on per-range quanta, an exact hi x hi accumulator and a cross-product
+//    accumulator per issuer (128-column tiles);
+// 3: plus the fp16 plane of rho^T in step (b) and a commit per stage that frees its slot;
+// 4: step (d) on an fp16 plane of R as well (three products), drains waiting without suspending.
 int xtc_engine_revision(void) { return 4; }
 
 int xtc_get_timings(xtc_ctx* ctx, double* ms, int64_t* launches, int n) {
