@@ -96,6 +96,10 @@ struct xtc_ctx {
   DBuf lam2, R2, R32b, eR2;    // spin builds: beta exchange weights, R for electron-2 beta
   DBuf Lv, T3;                 // explicit three-body L: V of the outer points, the packed T
   DBuf fc_U, fc_h, fc_hout, fc_Uout;  // frozen-core folding: staged host inputs and outputs
+  DBuf G2;                     // second gradient table: step (a) of the next chunk on stream st2
+  cudaStream_t st2 = nullptr;  // created on first use
+  cudaEvent_t ev_g[2] = {nullptr, nullptr};  // gradient table b written
+  cudaEvent_t ev_b[2] = {nullptr, nullptr};  // step (b) GEMM that read table b done
   // prepared state key (pair tables)
   int pair_n = -1;
   // timers
@@ -117,7 +121,7 @@ struct xtc_ctx {
     return {&jp_dev, &err_dev, &flag_dev, &grid, &w, &phi, &gamma, &phiT, &phi32, &pair_p, &pair_q, &jtab, &jtab64,
             &rho, &colmax, &colexp, &G, &V, &Vacc, &L, &R, &L32, &R32, &eL, &eR, &M, &evec, &lam, &dU_tmp,
             &dh_tmp, &e0_tmp, &vout, &r1, &r2, &lamd, &gamma_b, &M2, &M3, &lam2, &R2, &R32b, &eR2, &Lv, &T3,
-            &fc_U, &fc_h, &fc_hout, &fc_Uout};
+            &fc_U, &fc_h, &fc_hout, &fc_Uout, &G2};
   }
 };
 
@@ -159,18 +163,23 @@ cudaEvent_t next_event(xtc_ctx* c) {
 }
 
 // Runs `fn` (which launches kernels of class `kind`, `count` of them) bracketed by events when timing.
+// The events go on stream `st` (default: the context's stream), the one the launches use.
 template <typename F>
-void timed(xtc_ctx* c, int kind, int count, F&& fn) {
+void timed(xtc_ctx* c, int kind, int count, F&& fn, cudaStream_t st) {
   c->launches[kind] += count;
   if (!c->prm.timing) {
     fn();
     return;
   }
   TimedLaunch t{kind, next_event(c), next_event(c)};
-  cudaEventRecord(t.a, c->st);
+  cudaEventRecord(t.a, st);
   fn();
-  cudaEventRecord(t.b, c->st);
+  cudaEventRecord(t.b, st);
   c->timed.push_back(t);
+}
+template <typename F>
+void timed(xtc_ctx* c, int kind, int count, F&& fn) {
+  timed(c, kind, count, static_cast<F&&>(fn), c->st);
 }
 
 void reset_timers(xtc_ctx* c) {
@@ -384,6 +393,11 @@ int xtc_destroy(xtc_ctx* ctx) {
   for (xtc_ctx* lane : ctx->lanes) xtc_destroy(lane);
   for (cudaStream_t s : ctx->lane_streams) cudaStreamDestroy(s);
   for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+  for (int b = 0; b < 2; ++b) {
+    if (ctx->ev_g[b]) cudaEventDestroy(ctx->ev_g[b]);
+    if (ctx->ev_b[b]) cudaEventDestroy(ctx->ev_b[b]);
+  }
+  if (ctx->st2) cudaStreamDestroy(ctx->st2);
   delete ctx;
   return XTC_OK;
 }
@@ -598,25 +612,18 @@ int make_vfield_maps(xtc_ctx* ctx, const Plan& pl, VfMaps& m) {
   return make_tmap_3d(ctx, &m.g_load, ctx->G.p, bf, cols, 3 * pl.gc, planes, bk, VF_BM, wide);
 }
 
-// Steps (a)+(b) for outer points [i0, i0 + n_i) into ctx->V.
-int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, int64_t n_i, const VfMaps& maps) {
-  cudaStream_t st = ctx->st;
-  if (pl.f64) {
-    timed(ctx, XTC_K_VFIELD, 1, [&] {
-      launch_vfield_f64_impl(d_grid, ctx->jp_dev.as<JastrowParams>(), ctx->jp.n_nuc, ctx->jtab64.as<double>(),
-                             ctx->rho.as<double>(), pl.NGp, pl.NP, i0, n_i, pl.gc, ctx->pair_p.as<int>(),
-                             ctx->pair_q.as<int>(), pl.N, ctx->V.as<double>(), st);
-    });
-    return XTC_OK;
-  }
+// fp16 gradient scale 2^sG keeps |G| below 16384 (bf16 needs none)
+int gradient_scale(const xtc_ctx* ctx, const Plan& pl) {
+  if (pl.parts_b != 2 || !(ctx->g_bound > 0.0)) return 0;
+  const int sg = static_cast<int>(std::floor(std::log2(16384.0 / ctx->g_bound)));
+  return std::max(-30, std::min(30, sg));
+}
+
+// Step (a) for outer points [i0, i0 + n_i): the gradient table behind `maps`, on stream `st`.
+void run_grad(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, int64_t n_i, const VfMaps& maps,
+              cudaStream_t st) {
   const int n_kb = static_cast<int>(pl.NGp / VF_BK);
   const int mt_per_x = static_cast<int>((n_i + VF_BM - 1) / VF_BM);
-  // fp16 gradient scale 2^sG keeps |G| below 16384 (bf16 needs none)
-  int sg = 0;
-  if (pl.parts_b == 2 && ctx->g_bound > 0.0) {
-    sg = static_cast<int>(std::floor(std::log2(16384.0 / ctx->g_bound)));
-    sg = std::max(-30, std::min(30, sg));
-  }
   GfieldArgs g{};
   g.grid = d_grid;
   g.jp = ctx->jp_dev.as<JastrowParams>();
@@ -629,10 +636,15 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   g.kb_per_seg = 32;
   g.n_seg = (n_kb + g.kb_per_seg - 1) / g.kb_per_seg;
   g.n_nuc = ctx->jp.n_nuc;
-  g.g_scale = std::ldexp(1.0f, sg);
+  g.g_scale = std::ldexp(1.0f, gradient_scale(ctx, pl));
   g.range_blocks = f16_range_b(ctx->vf_kd);
-  timed(ctx, XTC_K_GRAD, 1, [&] { launch_gfield(&maps.g_store, g, pl.parts_b, st); });
+  timed(ctx, XTC_K_GRAD, 1, [&] { launch_gfield(&maps.g_store, g, pl.parts_b, st); }, st);
+}
 
+// Step (b) for outer points [i0, i0 + n_i) from the gradient table behind `maps`, into ctx->V.
+void run_gemm_b(xtc_ctx* ctx, const Plan& pl, int64_t n_i, const VfMaps& maps) {
+  cudaStream_t st = ctx->st;
+  const int n_kb = static_cast<int>(pl.NGp / VF_BK);
   VfieldArgs a{};
   a.colexp = ctx->colexp.as<int>();
   a.V = ctx->V.as<float>();
@@ -642,7 +654,7 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   a.Vacc = ctx->Vacc.as<double>();
   a.n_i = n_i;
   a.gcp = pl.gc;
-  a.mt_per_x = mt_per_x;
+  a.mt_per_x = static_cast<int>((n_i + VF_BM - 1) / VF_BM);
   a.n_tiles = (pl.NP + vf_bn(pl.parts_b) - 1) / vf_bn(pl.parts_b);
   a.n_pair = pl.NP;
   a.n_kb = n_kb;
@@ -650,12 +662,27 @@ int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, i
   a.kd = pl.parts_b == 2 ? f16_range_b(ctx->vf_kd) : std::min(ctx->vf_kd, 2);
   a.xper = ctx->x_period;
   a.flush = flush_ranges(ctx->vf_flush, a.kd);
-  a.unscale_g = std::ldexp(1.0f, -sg);
+  a.unscale_g = std::ldexp(1.0f, -gradient_scale(ctx, pl));
   a.err = ctx->err_dev.as<int>();
   const int splits = (a.n_kb + a.kb_per_split - 1) / a.kb_per_split;  // every slice non-empty
   // the GEMM, then (FP64 flushes) the kernel that writes V from the FP64 sums
   timed(ctx, XTC_K_VFIELD, 1, [&] { launch_vfield_tc(&maps.g_load, &maps.rho, &maps.rho16, a, pl.parts_b, splits, st); });
   if (a.flush > 0) timed(ctx, XTC_K_AUX, 1, [&] { launch_vfield_tc_finalize(a, pl.parts_b, splits, st); });
+}
+
+// Steps (a)+(b) for outer points [i0, i0 + n_i) into ctx->V, on the context's stream.
+int run_vfield(xtc_ctx* ctx, const Plan& pl, const double* d_grid, int64_t i0, int64_t n_i, const VfMaps& maps) {
+  cudaStream_t st = ctx->st;
+  if (pl.f64) {
+    timed(ctx, XTC_K_VFIELD, 1, [&] {
+      launch_vfield_f64_impl(d_grid, ctx->jp_dev.as<JastrowParams>(), ctx->jp.n_nuc, ctx->jtab64.as<double>(),
+                             ctx->rho.as<double>(), pl.NGp, pl.NP, i0, n_i, pl.gc, ctx->pair_p.as<int>(),
+                             ctx->pair_q.as<int>(), pl.N, ctx->V.as<double>(), st);
+    });
+    return XTC_OK;
+  }
+  run_grad(ctx, pl, d_grid, i0, n_i, maps, st);
+  run_gemm_b(ctx, pl, n_i, maps);
   return XTC_OK;
 }
 
@@ -845,13 +872,51 @@ int build_impl(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, 
     }
   }
 
-  // ---- chunk loop
+  // ---- chunk loop.  fp16 with several chunks: two gradient tables, and step (a) of chunk k + 1 on
+  // a second stream once chunk k's step (b) GEMM is done, beside the memory-bound steps (c) and
+  // (d) operand splits of chunk k (the GEMMs fill every SM; the gradient kernel shares an SM with
+  // step (c)).  Without room for the second table the chunks run one after another.
+  VfMaps maps2 = maps;
+  bool pipe = !pl.f64 && pl.parts_b == 2 && pl.oe - pl.ob > pl.gc;
+  if (pipe) {
+    pipe = ensure(ctx->G2, ctx->G.n);
+    if (pipe && !ctx->st2) {
+      CUDA_OK(cudaStreamCreateWithFlags(&ctx->st2, cudaStreamNonBlocking));
+      for (int b = 0; b < 2; ++b) {
+        CUDA_OK(cudaEventCreateWithFlags(&ctx->ev_g[b], cudaEventDisableTiming));
+        CUDA_OK(cudaEventCreateWithFlags(&ctx->ev_b[b], cudaEventDisableTiming));
+      }
+    }
+    if (pipe) {
+      const uint64_t cols = 2 * pl.NGp;
+      if ((rc = make_tmap_3d(ctx, &maps2.g_store, ctx->G2.p, false, cols, 3 * pl.gc, 1, 2 * VF_BK, 32, true))) return rc;
+      if ((rc = make_tmap_3d(ctx, &maps2.g_load, ctx->G2.p, false, cols, 3 * pl.gc, 1, 2 * VF_BK, VF_BM, true)))
+        return rc;
+    }
+  }
+  if (pipe) run_grad(ctx, pl, d_grid, pl.ob, std::min<int64_t>(pl.gc, pl.oe - pl.ob), maps, st);
+  int gb = 0;  // gradient table of the current chunk
   for (int64_t c0 = pl.ob; c0 < pl.oe; c0 += pl.gc) {
     NvtxRange nvtx_chunk("chunk");
     const int64_t n_i = std::min<int64_t>(pl.gc, pl.oe - c0);
     {
       NvtxRange nvtx_ab("steps a+b");
-      if ((rc = run_vfield(ctx, pl, d_grid, c0, n_i, maps))) return rc;
+      if (pipe) {
+        const VfMaps& cur = gb ? maps2 : maps;
+        if (c0 > pl.ob) CUDA_OK(cudaStreamWaitEvent(st, ctx->ev_g[gb], 0));
+        run_gemm_b(ctx, pl, n_i, cur);
+        const int64_t c1 = c0 + pl.gc;
+        if (c1 < pl.oe) {
+          // the other table was last read by chunk k - 1's GEMM, which ran before this one
+          CUDA_OK(cudaEventRecord(ctx->ev_b[gb], st));
+          CUDA_OK(cudaStreamWaitEvent(ctx->st2, ctx->ev_b[gb], 0));
+          run_grad(ctx, pl, d_grid, c1, std::min<int64_t>(pl.gc, pl.oe - c1), gb ? maps : maps2, ctx->st2);
+          CUDA_OK(cudaEventRecord(ctx->ev_g[1 - gb], ctx->st2));
+        }
+        gb = 1 - gb;
+      } else if ((rc = run_vfield(ctx, pl, d_grid, c0, n_i, maps))) {
+        return rc;
+      }
     }
     NvtxRange nvtx_cd("steps c+d");
     for (const Pass& ps : passes) {
