@@ -165,6 +165,23 @@ def test_device_inputs_match_host_inputs_bitwise(small):
     assert e0.item() == host["e0"][0]
 
 
+def test_chunk_pipeline_is_deterministic(small):
+    """Several chunks (128 outer points each): step (a) of the next chunk runs on a second stream
+    into a second gradient table while the current chunk finishes; repeated builds, on a user
+    stream as well, must agree bitwise (an ordering slip between the two tables would not)."""
+    torch = pytest.importorskip("torch")
+    p, g, ref = small
+    outs = []
+    s = torch.cuda.Stream()
+    for stream in (None, s.cuda_stream, None):
+        with ctx_for(p, "fp16x2", grid_chunk=128, stream=stream) as c:
+            outs.append(c.build(p.grid, p.weights, p.phi, g))
+    for o in outs[1:]:
+        for k in ("dU", "dh", "e0"):
+            assert np.array_equal(np.asarray(o[k]), np.asarray(outs[0][k])), k
+    assert max_err(outs[0], ref) < TOL["fp16x2"]
+
+
 # ------------------------------------------------------------------ error statuses
 
 def test_error_statuses(small):
