@@ -164,6 +164,11 @@ XTC_API int xtc_set_outer_range(xtc_ctx* ctx, int64_t begin, int64_t end);
  *   gamma [n_orb][n_orb] symmetric per-spin density           -- inputs, FP64
  *   dU     [n_orb]^4 FP64 or NULL; dU_f32 [n_orb]^4 FP32 or NULL -- dU[p][q][r][s] = Delta U_pr^qs
  *   dh     [n_orb][n_orb] FP64 (required), e0 [1] FP64 (required)
+ * The outer grid is processed in chunks (xtc_params.grid_chunk, automatic by default: at most
+ * 16 GB of gradient table and 12 GB of V and step (d) operands per chunk).  With several chunks
+ * and room for a second gradient table, step (a) of the next chunk runs on a second stream of the
+ * library's own while the current chunk finishes (ordered by events; the results do not depend on
+ * it); at N=120 and 100,000 points the workspace is about 50 GB.
  * Errors: XTC_ERR_ARG, XTC_ERR_STATE, XTC_ERR_NOT_SYMMETRIC, XTC_ERR_NONFINITE,
  *         XTC_ERR_OOM, XTC_ERR_CUDA, XTC_ERR_TIMEOUT. */
 XTC_API int xtc_build_1b2b(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
