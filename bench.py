@@ -115,8 +115,8 @@ class Clocks:
 # dram__bytes_read.sum + dram__bytes_write.sum of one step (b) GEMM launch (fp16x2) captured with
 # ncu on the first VFIELD_CAPTURE_OUTER outer points of the workload (`--ncu-case`), for GEMM
 # engine revision VFIELD_CAPTURE_REVISION; with another revision the traffic is reported as null
-VFIELD_CAPTURE_REVISION = 4
-VFIELD_DRAM_BYTES_CAPTURED = 24_858_260_480 + 2_878_889_472
+VFIELD_CAPTURE_REVISION = 5
+VFIELD_DRAM_BYTES_CAPTURED = 21_219_623_424 + 2_889_048_320
 VFIELD_CAPTURE_OUTER = 1184
 
 

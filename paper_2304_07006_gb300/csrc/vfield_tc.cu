@@ -54,7 +54,7 @@ namespace xtc {
 namespace {
 
 constexpr int DRAIN_WARPS = 8;       // two per TMEM lane quarter, half of the columns each
-constexpr int GM = 8;                // row tiles per group (L2 reuse)
+constexpr int GM = 16;               // row tiles per group (L2 reuse of the column panels)
 constexpr int NRB = 8;               // per-stage / per-range barriers (stage or range r uses r % NRB)
 
 __device__ __forceinline__ void red_add_f64(double* p, double v) {
@@ -579,20 +579,32 @@ __global__ void __launch_bounds__(VF_BM) vfield_finalize_kernel(const VfieldArgs
 }
 
 // M[pq][rs] += tile sum * 2^-(exp_a[pq] + exp_b[rs]) for one tile of the step (d) GEMM (mode 1);
-// one CTA per tile, thread = row pq, columns in order (coalesced tile reads; each M element is
-// owned by one tile).
+// one CTA per tile (each M element is owned by one tile), through shared memory in slabs of 32
+// columns: read column-major from the tile sums (thread = row), added row-major into M (warp =
+// row, lane = column), both coalesced.
 template <int BN>
 __global__ void __launch_bounds__(VF_BM) assemble_finalize_kernel(const VfieldArgs args) {
+  __shared__ double slab[32][VF_BM + 1];
   const TileXY t = grouped_tile(blockIdx.x, (args.rows_a + VF_BM - 1) / VF_BM, args.n_tiles);
-  const int pq = t.m_tile * VF_BM + threadIdx.x;
-  if (pq >= args.rows_a) return;
-  const double* acc = args.Vacc + (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x) * VF_BM * BN + threadIdx.x;
-  double* m = args.M + static_cast<int64_t>(pq) * args.ldm + t.n_tile * BN;
-  const int ea = args.exp_a[pq];
+  const double* acc = args.Vacc + (static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x) * VF_BM * BN;
   const int ncol = min(BN, args.n_pair - t.n_tile * BN);
-  for (int c = 0; c < ncol; ++c) {
-    const int e = ea + __ldg(args.exp_b + t.n_tile * BN + c);
-    m[c] += acc[static_cast<int64_t>(c) * VF_BM] * __longlong_as_double(static_cast<long long>(1023 - e) << 52);
+  const int row0 = t.m_tile * VF_BM, col0 = t.n_tile * BN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c0 = 0; c0 < ncol; c0 += 32) {
+    for (int c = 0; c < 32; ++c)
+      slab[c][threadIdx.x] = c0 + c < ncol ? acc[static_cast<int64_t>(c0 + c) * VF_BM + threadIdx.x] : 0.0;
+    __syncthreads();
+    const int c = c0 + lane;
+    if (c < ncol) {
+      const int eb = __ldg(args.exp_b + col0 + c);
+      for (int r = warp; r < VF_BM && row0 + r < args.rows_a; r += VF_BM / 32) {
+        const int pq = row0 + r;
+        const int e = __ldg(args.exp_a + pq) + eb;
+        double* m = args.M + static_cast<int64_t>(pq) * args.ldm + col0 + c;
+        *m += slab[lane][r] * __longlong_as_double(static_cast<long long>(1023 - e) << 52);
+      }
+    }
+    __syncthreads();
   }
 }
 

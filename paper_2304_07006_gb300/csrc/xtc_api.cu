@@ -457,8 +457,9 @@ int xtc_set_outer_range(xtc_ctx* ctx, int64_t begin, int64_t end) {
 // 2: exact fp16 split on per-range quanta, an exact hi x hi accumulator and a cross-product
 //    accumulator per issuer (128-column tiles);
 // 3: plus the fp16 plane of rho^T in step (b) and a commit per stage that frees its slot;
-// 4: step (d) on an fp16 plane of R as well (three products), drains waiting without suspending.
-int xtc_engine_revision(void) { return 4; }
+// 4: step (d) on an fp16 plane of R as well (three products), drains waiting without suspending;
+// 5: tiles ordered in groups of 16 row tiles (8 before).
+int xtc_engine_revision(void) { return 5; }
 
 int xtc_get_timings(xtc_ctx* ctx, double* ms, int64_t* launches, int n) {
   if (!ctx || n < XTC_N_KERNELS) return XTC_ERR_ARG;
