@@ -17,10 +17,15 @@ def _sym8(a):
     return sum(np.einsum("pqrs->" + p, a) for p in perms) / 8.0
 
 
-def _random_operator(n, seed):
+def _random_operator(n, seed, hermitian=True):
+    """Random (U, h): 8-fold symmetric U and symmetric h, or (hermitian=False) U with only the
+    pair symmetry U(pq|rs) = U(rs|pq) and a non-symmetric h, as a transcorrelated V - K has."""
     rng = np.random.default_rng(seed)
     h = rng.standard_normal((n, n))
-    return _sym8(rng.standard_normal((n, n, n, n))), 0.5 * (h + h.T)
+    a = rng.standard_normal((n, n, n, n))
+    if hermitian:
+        return _sym8(a), 0.5 * (h + h.T)
+    return 0.5 * (a + a.transpose(2, 3, 0, 1)), h
 
 
 # ---------------------------------------------------------------- Fock space, one determinant at a time
@@ -92,9 +97,10 @@ def _matrix_element(h, U, core, bra_ops, ket_ops):
     return sb * sk * _h_on(h, U, mk).get(mb, 0.0)
 
 
-@pytest.mark.parametrize("n,core,seed", [(4, [1], 3), (5, [0, 3], 4), (4, [], 5)])
-def test_fold_matches_fock_space_matrix_elements(n, core, seed):
-    U, h = _random_operator(n, seed)
+@pytest.mark.parametrize("n,core,seed,hermitian", [(4, [1], 3, True), (5, [0, 3], 4, True), (4, [], 5, True),
+                                                  (4, [2], 6, False), (5, [1, 4], 7, False)])
+def test_fold_matches_fock_space_matrix_elements(n, core, seed, hermitian):
+    U, h = _random_operator(n, seed, hermitian)
     h_fc, e_core, act = frozen_core.fold(U, h, core)
     assert abs(_matrix_element(h, U, core, [], []) - e_core) < 1e-12 * (1 + abs(e_core))
     up = lambda p: (1, 2 * p)
