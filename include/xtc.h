@@ -341,8 +341,8 @@ XTC_API int xtc_engine_revision(void);
  *     about n_grid * P * (n_orb^2 + 800) bytes for the pair and gradient tables) are rejected
  *     with XTC_ERR_ARG before any device work;
  *   - the call makes no device allocation (no cudaMalloc, cudaFree or allocating library call).
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  Every call reuses the same array, which keeps the
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress).
+ * Every call reuses the same array, which keeps the
  * last call's contents: calls that overlap on the GPU race with each other, so serialise them.
  * The call is synchronous with respect to the host, like the others: it synchronises the
  * context's stream before returning.  The calling thread's current device is restored. */

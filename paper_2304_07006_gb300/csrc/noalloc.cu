@@ -5,10 +5,10 @@
 // caller passes device buffers for the inputs and the output.
 //
 // The array's device address is obtained with cudaGetSymbolAddress on the first call on each
-// device (with that device current); that first call should therefore happen before any stream
-// capture.  Every call reuses the same array and it keeps the last call's contents, so calls
-// that overlap on the GPU (other streams, other threads, other contexts of this process on the
-// same device) race with each other and must be serialised by the caller.  The tensor-core GEMM
+// device (with that device current).  Every call reuses the same array and it keeps the last
+// call's contents, so calls that overlap on the GPU (other streams, other threads, other contexts
+// of this process on the same device) race with each other and must be serialised by the caller.
+// The tensor-core GEMM
 // runs with FP32 running sums only (no FP64 flush: the array has no room for the FP64 tile sums),
 // so over long inner sums its rounding differs slightly from xtc_vfield's.
 #include <cudaTypedefs.h>
