@@ -11,6 +11,7 @@ from .molecules import (  # noqa: F401
     make_batched,
     make_config,
     make_small,
+    orbital_gradients,
     random_density,
     permute_grid,
     CONFIG_NAMES,

@@ -57,6 +57,10 @@ class Problem:
     gamma: np.ndarray
     n_occ: int
     seed: int
+    # the basis (atom index, shell kind, exponent) and the orbital coefficients on the raw
+    # Cartesian Gaussians: phi = basis_values(grid, nuc_xyz, shells) @ orb_coef up to rounding
+    shells: list | None = None
+    orb_coef: np.ndarray | None = None
 
     @property
     def n_grid(self) -> int:
@@ -188,16 +192,49 @@ def basis_values(points, centres, shells):
     return np.stack(cols, axis=1)
 
 
+def basis_gradients(points, centres, shells):
+    """d/dr of every Cartesian Gaussian of basis_values: shape (n_points, n_functions, 3)."""
+    cols = []
+    for a, L, alpha in shells:
+        d = points - centres[a]
+        r2 = np.einsum("ij,ij->i", d, d)
+        g = np.exp(-alpha * r2)
+        for ijk in _CART[L]:
+            mono = [d[:, x] ** ijk[x] for x in range(3)]
+            grad = []
+            for x in range(3):
+                k = ijk[x]
+                # d/dx (x^k e^{-alpha r^2}) = (k x^(k-1) - 2 alpha x^(k+1)) e^{-alpha r^2}
+                dk = (k * d[:, x] ** (k - 1) if k > 0 else 0.0) - 2.0 * alpha * d[:, x] ** (k + 1)
+                others = [mono[y] for y in range(3) if y != x]
+                grad.append(dk * others[0] * others[1] * g)
+            cols.append(np.stack(grad, axis=1))
+    return np.stack(cols, axis=1)
+
+
 def orthonormal_orbitals(chi, weights, n_orb, rng):
+    """Returns (phi, C) with phi = chi @ C up to rounding."""
     norms = np.sqrt(np.einsum("gm,g,gm->m", chi, weights, chi))
     chi = chi / norms
     c = rng.uniform(-1.0, 1.0, size=(chi.shape[1], n_orb))
     phi = chi @ c
+    C = c / norms[:, None]
     for _ in range(3):  # repeated symmetric orthonormalisation (converges to Loewdin)
         s = phi.T @ (weights[:, None] * phi)
         ev, U = np.linalg.eigh(s)
-        phi = phi @ (U @ np.diag(ev ** -0.5) @ U.T)
-    return phi
+        T = U @ np.diag(ev ** -0.5) @ U.T
+        phi = phi @ T
+        C = C @ T
+    return phi, C
+
+
+def orbital_gradients(p: Problem) -> np.ndarray:
+    """Analytic gradients of the orbitals at the grid points, shape (n_grid, n_orb, 3), C-contiguous:
+    the inputs of the two-body integrals K (nabla phi on the grid)."""
+    if p.shells is None or p.orb_coef is None:
+        raise ValueError("problem carries no basis description")
+    dchi = basis_gradients(p.grid, p.nuc_xyz, p.shells)
+    return np.ascontiguousarray(np.einsum("gmx,mo->gox", dchi, p.orb_coef))
 
 
 # ----------------------------------------------------------------------------- configs
@@ -216,13 +253,13 @@ def _build(name, centres, kinds, grid_spec, n_orb, n_occ, nuc_set, n_sets, seed,
     if shells is None:
         shells = _choose_shells(kinds, n_orb)
     chi = basis_values(grid, centres, shells)
-    phi = orthonormal_orbitals(chi, w, n_orb, rng)
+    phi, C = orthonormal_orbitals(chi, w, n_orb, rng)
     coef = rng.uniform(-0.1, 0.1, size=(n_sets, terms.shape[0]))
     return Problem(name=name, nuc_xyz=centres, nuc_set=np.asarray(nuc_set, dtype=np.int32),
                    terms=np.ascontiguousarray(terms, dtype=np.int32), coef=coef,
                    grid=np.ascontiguousarray(grid), weights=np.ascontiguousarray(w),
                    phi=np.ascontiguousarray(phi), gamma=_closed_shell_gamma(n_orb, n_occ),
-                   n_occ=n_occ, seed=seed)
+                   n_occ=n_occ, seed=seed, shells=list(shells), orb_coef=C)
 
 
 def make_config(name: str) -> Problem:
