@@ -335,6 +335,34 @@ def three_body_measure(args, torch, dev, local):
             "note": "wall time per call with steps (a)+(b) in FP64; L is written densely on the device"}
 
 
+def two_body_k_measure(args, torch, dev, local):
+    """The two-body integrals K (Theory section) on the H2-like workload (N=10, 2,000 grid points,
+    FP64 path): one warm-up and three timed calls, inputs and output on the device.  FP64 FLOPs of
+    the two contractions: W = (w F) P (2 n_grid^2 n_pair) and S (2 x 4 n_grid x N^2 x n_pair)."""
+    import synth
+    from paper_2304_07006_gb300 import Context
+
+    p = synth_config("h2")
+    N, NP, NG = p.n_orb, p.n_orb * (p.n_orb + 1) // 2, p.n_grid
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    grid, w, phi, dphi = t(p.grid), t(p.weights), t(p.phi), t(synth.orbital_gradients(p))
+    K = torch.empty((N,) * 4, dtype=torch.float64, device=dev)
+    with Context("fp64", device=local) as c:
+        c.set_jastrow(p.nuc_xyz, p.nuc_set, p.terms, p.coef)
+        c.two_body_K(grid, w, phi, dphi, out=K)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            c.two_body_K(grid, w, phi, dphi, out=K)
+        torch.cuda.synchronize(dev)
+        sec = (time.perf_counter() - t0) / 3
+    flops = 2.0 * NG * NG * NP + 8.0 * NG * N * N * NP
+    return {"workload": f"h2: N={N}, {NG} grid points, FP64", "seconds_per_call": sec,
+            "contraction_flops": flops, "gflops": flops / sec / 1e9,
+            "note": "wall time per call: steps (a)+(b) for V, the Laplacian table (n_grid^2 pairs), the two "
+                    "FP64 contractions and the unpack into K[p][q][r][s]"}
+
+
 def frozen_core_measure(args, torch, dev, local, peaks):
     """The xTC-FC folding at N=120 (two core orbitals, the 1s pair of the N2-like workload) of
     device-resident Delta U / Delta h: one warm-up and five timed calls.  The fold is a gather of
@@ -569,6 +597,7 @@ def main():
         if args.rohf:
             line["rohf"] = rohf_measure(args, torch, dev, local, p, ms_step / 1e3)
         line["three_body_L"] = three_body_measure(args, torch, dev, local)
+        line["two_body_K"] = two_body_k_measure(args, torch, dev, local)
         line["full_rank_density"] = fullrank_measure(args, torch, dev, local, p, per_kernel)
         line["frozen_core_fold"] = frozen_core_measure(args, torch, dev, local, peaks)
         if args.large:

@@ -25,6 +25,7 @@
  * densities of Appendix A (xtc_build_1b2b_rohf), a batched build of many instances
  * (xtc_build_1b2b_batched), the frozen-core folding of the corrections (xtc_frozen_core_fold),
  * the explicit L of eq. Ldecomp for small orbital sets as a validation aid (xtc_three_body_L),
+ * the two-body integrals K of the similarity-transformed Hamiltonian (xtc_two_body_K),
  * steps (a) and (b) alone (xtc_jastrow_grad, xtc_vfield, and xtc_vfield_noalloc, which allocates
  * nothing) and a chunk autotuner (xtc_autotune_chunk).
  *
@@ -267,6 +268,28 @@ XTC_API int xtc_autotune_chunk(xtc_ctx* ctx, int64_t n_grid, int n_orb, const do
 #define XTC_THREE_BODY_MAX_ORB 24
 XTC_API int xtc_three_body_L(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
                      const double* phi, double* L);
+
+/* The non-hermitian two-body integrals K of the similarity-transformed Hamiltonian (Theory
+ * section, next to the Coulomb integrals V; the combined two-body integrals are U = V - K):
+ *   K[p][q][r][s] = K_pr^qs = 1/2 <pr| P12 [ lap_1 u + (grad_1 u)^2 + 2 grad_1 u . grad_1 ] |qs>,
+ *   P12 f(1,2) = f(1,2) + f(2,1),
+ * on the quadrature grid for real spatial orbitals (electron 1: p -> q, electron 2: r -> s; the
+ * index order of Delta U), with u the Jastrow factor of xtc_set_jastrow.  K has the pair-swap
+ * symmetry K[p][q][r][s] = K[r][s][p][q] and is not hermitian.  Coincident grid points contribute
+ * nothing.  Summed over the context's outer range (xtc_set_outer_range): the results of disjoint
+ * ranges add up to the whole grid's.
+ *   n_grid >= 1, 1 <= n_orb <= XTC_TWO_BODY_K_MAX_ORB; grid_xyz, weights, phi as in xtc_build_1b2b
+ *   dphi [n_grid][n_orb][3]  gradients of the orbitals at the grid points (bohr^-1), host or device
+ *   K    [n_orb]^4 FP64, host or device memory (n_orb = 120: 1.66 GB)
+ * The vector pair field V (steps a and b) is formed in the context's precision; the Laplacian
+ * table, its product with the pair densities and the contraction are FP64 (SIMT).  Workspace:
+ * n_orb^2 x n_pair doubles plus about 6 GB per chunk of outer points (the context's grid_chunk,
+ * else chosen by that budget).  Synchronous.  Requires xtc_set_jastrow.  Errors: XTC_ERR_ARG,
+ * XTC_ERR_STATE, XTC_ERR_NONFINITE (grid, weights, orbitals or their gradients), XTC_ERR_OOM,
+ * XTC_ERR_CUDA and those of xtc_vfield. */
+#define XTC_TWO_BODY_K_MAX_ORB 200
+XTC_API int xtc_two_body_K(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz, const double* weights,
+                           const double* phi, const double* dphi, double* K);
 
 /* One instance of a batched build: the arguments of xtc_set_jastrow and xtc_build_1b2b, with the
  * same meanings, layouts and ownership; status receives the instance's own status. */

@@ -97,6 +97,7 @@ struct xtc_ctx {
   DBuf Lv, T3;                 // explicit three-body L: V of the outer points, the packed T
   DBuf fc_U, fc_h, fc_hout, fc_Uout;  // frozen-core folding: staged host inputs and outputs
   DBuf G2;                     // second gradient table: step (a) of the next chunk on stream st2
+  DBuf k_dphi, k_V, k_Ft, k_W, k_S;  // two-body integrals K: staged gradients, V, F table, W, S
   cudaStream_t st2 = nullptr;  // created on first use
   cudaEvent_t ev_g[2] = {nullptr, nullptr};  // gradient table b written
   cudaEvent_t ev_b[2] = {nullptr, nullptr};  // step (b) GEMM that read table b done
@@ -121,7 +122,7 @@ struct xtc_ctx {
     return {&jp_dev, &err_dev, &flag_dev, &grid, &w, &phi, &gamma, &phiT, &phi32, &pair_p, &pair_q, &jtab, &jtab64,
             &rho, &colmax, &colexp, &G, &V, &Vacc, &L, &R, &L32, &R32, &eL, &eR, &M, &evec, &lam, &dU_tmp,
             &dh_tmp, &e0_tmp, &vout, &r1, &r2, &lamd, &gamma_b, &M2, &M3, &lam2, &R2, &R32b, &eR2, &Lv, &T3,
-            &fc_U, &fc_h, &fc_hout, &fc_Uout, &G2};
+            &fc_U, &fc_h, &fc_hout, &fc_Uout, &G2, &k_dphi, &k_V, &k_Ft, &k_W, &k_S};
   }
 };
 
@@ -1349,6 +1350,73 @@ extern "C" int xtc_three_body_L(xtc_ctx* ctx, int64_t n_grid, int n_orb, const d
     CUDA_OK(cudaGetLastError());
   }
   if (!out_dev) CUDA_OK(cudaMemcpyAsync(L, Ld, n6 * 8, cudaMemcpyDeviceToHost, st));
+  if ((rc = check_device_error(ctx))) return rc;
+  return XTC_OK;
+}
+
+// ====================================================================== two-body integrals K
+// K_pr^qs of the Theory section on the grid: per chunk of outer points V (steps a+b, the
+// context's precision), the table w_j (lap_1 u + |grad_1 u|^2), W and the FP64 sum S of
+// two_body_k.cu; then K[p][q][r][s] = S[pq][rs] + S[rs][pq].
+extern "C" int xtc_two_body_K(xtc_ctx* ctx, int64_t n_grid, int n_orb, const double* grid_xyz,
+                              const double* weights, const double* phi, const double* dphi, double* K) {
+  if (!ctx) return XTC_ERR_ARG;
+  if (!K || !dphi || n_orb < 1 || n_orb > XTC_TWO_BODY_K_MAX_ORB || n_grid < 1 || !grid_xyz || !weights || !phi)
+    return fail(ctx, XTC_ERR_ARG, "two_body_K: null pointer, n_grid < 1 or n_orb outside 1..%d",
+                XTC_TWO_BODY_K_MAX_ORB);
+  if (!ctx->jastrow_set) return fail(ctx, XTC_ERR_STATE, "xtc_set_jastrow has not been called");
+  CUDA_OK(cudaSetDevice(ctx->prm.device));
+  cudaStream_t st = ctx->st;
+  const int N = n_orb, NP = N * (N + 1) / 2;
+  const int64_t ob = std::min<int64_t>(ctx->outer_begin, n_grid);
+  const int64_t oe = std::max<int64_t>(ob, ctx->outer_end < 0 ? n_grid : std::min<int64_t>(ctx->outer_end, n_grid));
+  const int64_t n_i = oe - ob;
+  const size_t n4 = static_cast<size_t>(N) * N * N * N;
+  const bool out_dev = is_device_ptr(K);
+  if (!out_dev && !ensure(ctx->dU_tmp, n4 * 8)) return fail(ctx, XTC_ERR_OOM, "K staging (%.2f GB)", n4 * 8e-9);
+  double* Kd = out_dev ? K : ctx->dU_tmp.as<double>();
+  int rc;
+  if (n_i == 0) {
+    CUDA_OK(cudaMemsetAsync(Kd, 0, n4 * 8, st));
+  } else {
+    // chunk of outer points: the caller's grid_chunk, else what keeps F table + V + W near 6 GB
+    const size_t per_point = static_cast<size_t>(n_grid) * 8 + static_cast<size_t>(4) * NP * 8;
+    int64_t ch = ctx->prm.grid_chunk > 0 ? ctx->prm.grid_chunk
+                                         : std::max<int64_t>(64, static_cast<int64_t>(6e9 / per_point));
+    ch = std::min<int64_t>(std::min<int64_t>(ch, n_i), int64_t{65535} * 64);  // grid.y of the W GEMM
+    const size_t s_bytes = static_cast<size_t>(N) * N * NP * 8;
+    if (!ensure(ctx->k_S, s_bytes) || !ensure(ctx->k_V, static_cast<size_t>(ch) * 3 * NP * 8) ||
+        !ensure(ctx->k_W, static_cast<size_t>(ch) * NP * 8) || !ensure(ctx->k_Ft, static_cast<size_t>(ch) * n_grid * 8))
+      return fail(ctx, XTC_ERR_OOM, "two_body_K workspace (%.2f GB)",
+                  (s_bytes + static_cast<size_t>(ch) * per_point) * 1e-9);
+    CUDA_OK(cudaMemsetAsync(ctx->k_S.p, 0, s_bytes, st));
+    for (int64_t c0 = ob; c0 < oe; c0 += ch) {
+      const int64_t n_c = std::min<int64_t>(ch, oe - c0);
+      // steps (a)+(b) for the chunk; this also stages grid, weights and orbitals and checks them
+      if ((rc = xtc_vfield(ctx, n_grid, n_orb, grid_xyz, weights, phi, c0, c0 + n_c, ctx->k_V.as<double>())))
+        return rc;
+      const double *d_grid = nullptr, *d_w = nullptr, *d_phi = nullptr, *d_dphi = nullptr;
+      if ((rc = stage_input(ctx, ctx->grid, grid_xyz, static_cast<size_t>(n_grid) * 3, &d_grid))) return rc;
+      if ((rc = stage_input(ctx, ctx->w, weights, static_cast<size_t>(n_grid), &d_w))) return rc;
+      if ((rc = stage_input(ctx, ctx->phi, phi, static_cast<size_t>(n_grid) * n_orb, &d_phi))) return rc;
+      if ((rc = stage_input(ctx, ctx->k_dphi, dphi, static_cast<size_t>(n_grid) * n_orb * 3, &d_dphi))) return rc;
+      if (c0 == ob) {
+        CUDA_OK(cudaMemsetAsync(ctx->flag_dev.p, 0, 16, st));
+        launch_check_finite(d_dphi, n_grid * n_orb * 3, ctx->flag_dev.as<int>(), st);
+        int flag = 0;
+        CUDA_OK(cudaMemcpyAsync(&flag, ctx->flag_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_OK(cudaStreamSynchronize(st));
+        if (flag) return fail(ctx, XTC_ERR_NONFINITE, "NaN or Inf in the orbital gradients");
+      }
+      launch_k_chunk(d_grid, d_w, d_phi, d_dphi, ctx->jp_dev.as<JastrowParams>(), n_grid, N, ctx->pair_p.as<int>(),
+                     ctx->pair_q.as<int>(), c0, n_c, ctx->k_V.as<double>(), ctx->k_Ft.as<double>(),
+                     ctx->k_W.as<double>(), ctx->k_S.as<double>(), ctx->n_sm, st);
+      CUDA_OK(cudaGetLastError());
+    }
+    launch_k_unpack(ctx->k_S.as<double>(), N, Kd, ctx->n_sm, st);
+    CUDA_OK(cudaGetLastError());
+  }
+  if (!out_dev) CUDA_OK(cudaMemcpyAsync(K, Kd, n4 * 8, cudaMemcpyDeviceToHost, st));
   if ((rc = check_device_error(ctx))) return rc;
   return XTC_OK;
 }

@@ -22,7 +22,7 @@ EXPORTED = ("xtc_default_params", "xtc_create", "xtc_destroy", "xtc_strerror", "
             "xtc_set_jastrow", "xtc_set_outer_range", "xtc_build_1b2b", "xtc_jastrow_grad", "xtc_vfield",
             "xtc_get_timings", "xtc_vfield_noalloc", "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf",
             "xtc_three_body_L", "xtc_autotune_chunk", "xtc_selftest_wait_timeout", "xtc_engine_revision",
-            "xtc_selftest_reciprocals", "xtc_frozen_core_fold")
+            "xtc_selftest_reciprocals", "xtc_frozen_core_fold", "xtc_two_body_K")
 
 
 class XtcParams(ctypes.Structure):
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
     lib.xtc_build_1b2b_batched.argtypes = [P, I, ctypes.POINTER(XtcInstance), I]
     lib.xtc_build_1b2b_rohf.argtypes = [P, I64, I, D, D, D, D, D, D, D, D, D, D, D]
     lib.xtc_three_body_L.argtypes = [P, I64, I, D, D, D, D]
+    lib.xtc_two_body_K.argtypes = [P, I64, I, D, D, D, D, D]
     lib.xtc_autotune_chunk.argtypes = [P, I64, I, D, D, D, D, ctypes.POINTER(ctypes.c_int64)]
     lib.xtc_selftest_wait_timeout.argtypes = [P, I]
     lib.xtc_engine_revision.argtypes = []
@@ -91,7 +92,7 @@ def load(path: str = LIB_PATH):
                  "xtc_jastrow_grad", "xtc_vfield", "xtc_get_timings", "xtc_vfield_noalloc",
                  "xtc_build_1b2b_batched", "xtc_build_1b2b_rohf", "xtc_three_body_L", "xtc_autotune_chunk",
                  "xtc_selftest_wait_timeout", "xtc_engine_revision", "xtc_selftest_reciprocals",
-                 "xtc_frozen_core_fold"):
+                 "xtc_frozen_core_fold", "xtc_two_body_K"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -329,6 +330,21 @@ class Context:
         _need(out, n_orb ** 6, "L")
         self._check(self._lib.xtc_three_body_L(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
                                                _ptr(out)))
+        return out
+
+    def two_body_K(self, grid, weights, phi, dphi, out=None):
+        """The two-body integrals K of the similarity-transformed Hamiltonian (xtc_two_body_K):
+        out[p, q, r, s] = K_pr^qs over the context's outer range, from the orbitals phi
+        (n_grid, n_orb) and their gradients dphi (n_grid, n_orb, 3); a numpy array unless out is
+        given."""
+        grid, weights, phi, dphi = _f64(grid), _f64(weights), _f64(phi), _f64(dphi)
+        n_grid, n_orb = _grid_inputs(grid, weights, phi)
+        _need(dphi, n_grid * n_orb * 3, "dphi")
+        if out is None:
+            out = np.empty((n_orb,) * 4)
+        _need(out, n_orb ** 4, "K")
+        self._check(self._lib.xtc_two_body_K(self._h, n_grid, n_orb, _ptr(grid), _ptr(weights), _ptr(phi),
+                                             _ptr(dphi), _ptr(out)))
         return out
 
     def jastrow_grad(self, r1, r2, out=None):
