@@ -19,9 +19,11 @@ and the derivative acting on phi_S.
 Output: K[p, q, r, s] = K_pr^qs (electron 1: p -> q, electron 2: r -> s), the index order of
 Delta U in this package.
 
-Readings where the paper is silent: a coincident pair of grid points (r_ij < 1e-14 bohr, i.e.
-j = i) contributes 0, as in the three-body sums; the Laplacian's 2 a'/r terms follow the
-readings of ``jastrow.lap1``.
+Readings where the paper is silent: the coincident pair of grid points (j = i) stays in the double
+sum, with the readings of ``jastrow.grad1`` and ``jastrow.lap1`` (unit vectors and the 2 a'/r terms
+of the Laplacian are 0 below 1e-14 bohr; the rest is evaluated as written), the same reading as
+for the gradient in V.  ``coincident=False`` drops the pair instead (for comparisons that cannot
+evaluate it, such as differences).
 
 Test infrastructure only: only the tests, the smoke entry point and the CPU baseline may import it.
 """
@@ -34,17 +36,15 @@ from . import jastrow
 
 def _pair_fields(first, second, jas):
     """(nabla_1 u, nabla_1^2 u + |nabla_1 u|^2) with u's first slot at ``first`` and its second at
-    ``second``, both broadcast (n, n, 3) views of the grid; coincident pairs set to 0."""
+    ``second``, both broadcast (n, n, 3) views of the grid."""
     g = jastrow.grad1(first, second, *jas)
     f = jastrow.lap1(first, second, *jas) + np.sum(g * g, axis=-1)
-    coincident = np.linalg.norm(first - second, axis=-1) < jastrow.EPS
-    g = np.where(coincident[..., None], 0.0, g)
-    f = np.where(coincident, 0.0, f)
     return g, f
 
 
-def k_integrals(grid, weights, phi, dphi, nuc_xyz, nuc_set, terms, coef):
-    """K[p, q, r, s] for the orbitals ``phi`` (n_grid, N) with gradients ``dphi`` (n_grid, N, 3)."""
+def k_integrals(grid, weights, phi, dphi, nuc_xyz, nuc_set, terms, coef, coincident=True):
+    """K[p, q, r, s] for the orbitals ``phi`` (n_grid, N) with gradients ``dphi`` (n_grid, N, 3);
+    ``coincident=False`` leaves out the pairs j = i."""
     X = np.asarray(grid, dtype=np.float64)
     w = np.asarray(weights, dtype=np.float64)
     phi = np.asarray(phi, dtype=np.float64)
@@ -56,6 +56,10 @@ def k_integrals(grid, weights, phi, dphi, nuc_xyz, nuc_set, terms, coef):
     # f(1,2): u's first slot holds electron 1;  f(2,1): it holds electron 2
     g12, f12 = _pair_fields(ri, rj, jas)
     g21, f21 = _pair_fields(rj, ri, jas)
+    if not coincident:
+        off = 1.0 - np.eye(n)
+        g12, g21 = g12 * off[..., None], g21 * off[..., None]
+        f12, f21 = f12 * off, f21 * off
 
     wphi = w[:, None] * phi                                   # w_i phi_P(i)
     pair = (wphi[:, :, None] * phi[:, None, :]).reshape(n, N * N)  # w_i phi_P(i) phi_Q(i), (P, Q)

@@ -14,7 +14,7 @@
 // Per chunk of outer points: F w_j as a table (FP64, inner points x outer points), W = that table
 // times the pair products (an FP64 GEMM with the pair products formed while staging), then S
 // accumulates an FP64 GEMM over K = 4 x outer points whose left operand (rho / 2, psi_x) is formed
-// from phi, grad phi and w while staging.  Coincident points (r12 < 1e-14) contribute 0.
+// from phi, grad phi and w while staging.
 #include <algorithm>
 
 #include "xtc_internal.cuh"
@@ -28,13 +28,13 @@ constexpr double K_EPS = 1e-14;
 // a = r / (1 + r) for the electron-nucleus distances, b the same for r12.  Each term is P(a1) Q(b):
 // lap(P Q) = Q lap P + P lap Q + 2 grad P . grad Q, and a function f(a(r)) of one distance has
 // lap f = f_aa a'^2 + f_a (a'' + 2 a'/r) with a' = (1+r)^-2, a'' = -2 (1+r)^-3.  Unit vectors and
-// the 2 a'/r terms are 0 below 1e-14 bohr.
+// the 2 a'/r terms are 0 below 1e-14 bohr and everything else is kept, as for the gradient of
+// step (a): at a coincident pair (j = i) the electron-nucleus parts stay in the sums.
 __device__ double lap_plus_square(const JastrowParams& jp, double x1, double y1, double z1, double x2, double y2,
                                   double z2) {
   const double dx = x1 - x2, dy = y1 - y2, dz = z1 - z2;
   const double r12 = sqrt(dx * dx + dy * dy + dz * dz);
-  if (r12 < K_EPS) return 0.0;
-  const double i12 = 1.0 / r12;
+  const double i12 = r12 < K_EPS ? 0.0 : 1.0 / r12;
   const double e12x = dx * i12, e12y = dy * i12, e12z = dz * i12;
   const double s12 = 1.0 / (1.0 + r12);
   const double b = r12 * s12, bp = s12 * s12, bpp = -2.0 * bp * s12;

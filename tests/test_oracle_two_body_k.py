@@ -7,6 +7,8 @@
   so K can be formed from values of u and of analytic orbitals alone, with Laplacians taken by
   differences (no gradient formula, no orbital gradient, no index bookkeeping shared with the
   oracle);
+* the coincident pair (j = i), which differences cannot reach, against a closed form of the
+  reading on a one-point grid;
 * the pair-swap symmetry that P12 gives, the split into the part linear and the part quadratic in
   the Jastrow coefficients, and K = 0 without a Jastrow factor;
 * planted mistakes in the oracle's Jastrow derivatives fail the difference pin.
@@ -148,7 +150,7 @@ def _case(seed, terms, n=18, n_orb=3):
 def _fd_error(seed, terms):
     grid, w, orbs, n_orb, jas, dphi = _case(seed, terms)
     K_fd, phi = _k_by_similarity_transform(grid, w, orbs, n_orb, jas)
-    K = two_body_k.k_integrals(grid, w, phi, dphi, *jas)
+    K = two_body_k.k_integrals(grid, w, phi, dphi, *jas, coincident=False)
     return np.abs(K - K_fd).max() / np.abs(K_fd).max()
 
 
@@ -177,6 +179,31 @@ def test_k_pins_catch_planted_mistakes(monkeypatch):
         return real(first, second, jas) if len(calls) % 2 == 1 else real(second, first, jas)
     monkeypatch.setattr(two_body_k, "_pair_fields", same_slot)
     assert _fd_error(1, synth.CANONICAL_TERMS) > 1e-3
+
+
+def test_k_coincident_pair_reading_closed_form():
+    """One grid point r, one nucleus at the origin, u = c1 (a1 + a2) + 2 c2 b (terms (0,1,0) and
+    (0,0,1)).  At the coincident pair the electron-electron unit vector and 1/r12 are 0 while the
+    rest is kept: grad_1 u = c1 a'(d) r/d, and with b = 0, b' = 1, b'' = -2,
+        F = lap_1 u + |grad_1 u|^2 = c1 (a'' + 2 a'/d) - 4 c2 + c1^2 a'^2,
+    so K[p,q,r,s] = w^2 phi_p phi_r [F phi_q phi_s + (g . dphi_q) phi_s + phi_q (g . dphi_s)]."""
+    rng = np.random.default_rng(4)
+    r = np.array([[0.48, 0.0, 0.64]])
+    d = 0.8
+    c1, c2, w = 0.13, -0.07, np.array([0.7])
+    terms = np.array([(0, 1, 0), (0, 0, 1)])
+    phi = rng.uniform(-1, 1, size=(1, 3))
+    dphi = rng.uniform(-1, 1, size=(1, 3, 3))
+    K = two_body_k.k_integrals(r, w, phi, dphi, np.zeros((1, 3)), [0], terms, np.array([[c1, c2]]))
+    ap, app = 1 / (1 + d) ** 2, -2 / (1 + d) ** 3
+    g = c1 * ap * r[0] / d
+    F = c1 * (app + 2 * ap / d) - 4 * c2 + c1 ** 2 * ap ** 2
+    f, gd = phi[0], dphi[0] @ g
+    want = w[0] ** 2 * (F * np.einsum("p,q,r,s->pqrs", f, f, f, f)
+                        + np.einsum("p,q,r,s->pqrs", f, gd, f, f) + np.einsum("p,q,r,s->pqrs", f, f, f, gd))
+    assert np.abs(K - want).max() < 1e-14 * np.abs(want).max()
+    assert np.all(two_body_k.k_integrals(r, w, phi, dphi, np.zeros((1, 3)), [0], terms, np.array([[c1, c2]]),
+                                         coincident=False) == 0.0)
 
 
 def test_k_symmetries_and_jastrow_dependence():
