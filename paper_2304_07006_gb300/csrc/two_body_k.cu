@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(256) kfield_table_kernel(const double* __restr
 
 // ------------------------------------------------------------------ FP64 SIMT GEMM
 // C[m][n] (+)= sum_k A(k, m) B(k, n) with both operands produced element by element by Op while
-// staging: 64 x 64 tiles, 16-deep K steps, 4 x 4 results per thread.
+// staging: 64 x 64 tiles, 16-deep K steps, 4 x 4 results per thread.  blockIdx.z selects a slice
+// [z kslice, (z+1) kslice) of K and an output block C + z zstride (split K for small outputs).
 constexpr int KG_T = 64, KG_K = 16;
 
 // W[i][rs] = sum_j Ft[j][i] phi_r(j) phi_s(j)   (m: outer point of the chunk, n: pair, k: inner point)
@@ -136,24 +137,27 @@ struct SOperands {
 };
 
 template <class Op, bool ACC>
-__global__ void __launch_bounds__(256) gemm_f64_kernel(Op op, int64_t M, int64_t Nn, int64_t K, double* __restrict__ C,
-                                                       int64_t ldc) {
+__global__ void __launch_bounds__(256) gemm_f64_kernel(Op op, int64_t M, int64_t Nn, int64_t K, int64_t kslice,
+                                                       double* __restrict__ C, int64_t ldc, int64_t zstride) {
   __shared__ double As[KG_K][KG_T];
   __shared__ double Bs[KG_K][KG_T];
   const int t = threadIdx.x;
   const int tn = t & 15, tm = t >> 4;
   const int64_t m0 = static_cast<int64_t>(blockIdx.y) * KG_T, n0 = static_cast<int64_t>(blockIdx.x) * KG_T;
+  const int64_t kb = static_cast<int64_t>(blockIdx.z) * kslice;
+  const int64_t ke = kb + kslice < K ? kb + kslice : K;
+  C += static_cast<int64_t>(blockIdx.z) * zstride;
   double acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
-  for (int64_t k0 = 0; k0 < K; k0 += KG_K) {
+  for (int64_t k0 = kb; k0 < ke; k0 += KG_K) {
     for (int e = t; e < KG_K * KG_T; e += 256) {
       const int kk = e / KG_T, c = e % KG_T;
       const int64_t k = k0 + kk;
-      As[kk][c] = (k < K && m0 + c < M) ? op.a(k, m0 + c) : 0.0;
-      Bs[kk][c] = (k < K && n0 + c < Nn) ? op.b(k, n0 + c) : 0.0;
+      As[kk][c] = (k < ke && m0 + c < M) ? op.a(k, m0 + c) : 0.0;
+      Bs[kk][c] = (k < ke && n0 + c < Nn) ? op.b(k, n0 + c) : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -207,26 +211,66 @@ __global__ void k_unpack_kernel(const double* __restrict__ S, int N, int NP, dou
   }
 }
 
+// C[m][n] (+)= sum_z P[z][m][n], the slices in order (the same result for the same split).
+template <bool ACC>
+__global__ void slice_sum_kernel(const double* __restrict__ P, int splits, int64_t M, int64_t Nn,
+                                 double* __restrict__ C, int64_t ldc) {
+  const int64_t total = M * Nn;
+  for (int64_t o = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; o < total;
+       o += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double sum = 0.0;
+    for (int z = 0; z < splits; ++z) sum += P[z * total + o];
+    const int64_t m = o / Nn, n = o - m * Nn;
+    if (ACC)
+      C[m * ldc + n] += sum;
+    else
+      C[m * ldc + n] = sum;
+  }
+}
+
+// One GEMM; when its output has fewer tiles than two per SM, K is split into slices (at most 64,
+// each at least 8 K steps) whose partial results go to `partial` (room for partial_elems
+// doubles) and are summed in order afterwards.
 template <class Op, bool ACC>
-void launch_gemm(const Op& op, int64_t M, int64_t Nn, int64_t K, double* C, int64_t ldc, cudaStream_t st) {
-  dim3 grid(static_cast<unsigned>((Nn + KG_T - 1) / KG_T), static_cast<unsigned>((M + KG_T - 1) / KG_T));
-  gemm_f64_kernel<Op, ACC><<<grid, 256, 0, st>>>(op, M, Nn, K, C, ldc);
+void launch_gemm(const Op& op, int64_t M, int64_t Nn, int64_t K, double* C, int64_t ldc, double* partial,
+                 int64_t partial_elems, int n_sm, cudaStream_t st) {
+  const int64_t tm = (M + KG_T - 1) / KG_T, tn = (Nn + KG_T - 1) / KG_T, tiles = tm * tn;
+  int64_t splits = 1;
+  if (partial && tiles < 2 * static_cast<int64_t>(n_sm))
+    splits = std::min<int64_t>(std::min<int64_t>((2 * n_sm + tiles - 1) / tiles, (K + 8 * KG_K - 1) / (8 * KG_K)),
+                               64);
+  while (splits > 1 && splits * M * Nn > partial_elems) --splits;
+  int64_t kslice = K;
+  if (splits > 1) {
+    kslice = ((K + splits - 1) / splits + KG_K - 1) / KG_K * KG_K;
+    splits = (K + kslice - 1) / kslice;
+  }
+  dim3 grid(static_cast<unsigned>(tn), static_cast<unsigned>(tm), static_cast<unsigned>(splits));
+  if (splits <= 1) {
+    gemm_f64_kernel<Op, ACC><<<grid, 256, 0, st>>>(op, M, Nn, K, K, C, ldc, 0);
+    return;
+  }
+  gemm_f64_kernel<Op, false><<<grid, 256, 0, st>>>(op, M, Nn, K, kslice, partial, Nn, M * Nn);
+  const int64_t blocks = std::min<int64_t>((M * Nn + 255) / 256, static_cast<int64_t>(n_sm) * 16);
+  slice_sum_kernel<ACC><<<static_cast<unsigned>(blocks), 256, 0, st>>>(partial, static_cast<int>(splits), M, Nn, C,
+                                                                      ldc);
 }
 
 }  // namespace
 
 void launch_k_chunk(const double* grid, const double* w, const double* phi, const double* dphi,
                     const JastrowParams* jp_dev, int64_t n_grid, int n_orb, const int* pair_p, const int* pair_q,
-                    int64_t i0, int64_t n_i, const double* V, double* Ft, double* W, double* S, int n_sm,
-                    cudaStream_t st) {
+                    int64_t i0, int64_t n_i, const double* V, double* Ft, double* W, double* S, double* partial,
+                    int64_t partial_elems, int n_sm, cudaStream_t st) {
   const int NP = n_orb * (n_orb + 1) / 2;
   const int64_t total = n_grid * n_i;
   const int64_t blocks = std::min<int64_t>((total + 255) / 256, static_cast<int64_t>(n_sm) * 16);
   kfield_table_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(grid, w, jp_dev, n_grid, i0, n_i, Ft);
   const WOperands wop{Ft, n_i, phi, n_orb, pair_p, pair_q};
-  launch_gemm<WOperands, false>(wop, n_i, NP, n_grid, W, NP, st);
+  launch_gemm<WOperands, false>(wop, n_i, NP, n_grid, W, NP, partial, partial_elems, n_sm, st);
   const SOperands sop{phi, dphi, w, i0, n_orb, NP, W, V};
-  launch_gemm<SOperands, true>(sop, static_cast<int64_t>(n_orb) * n_orb, NP, 4 * n_i, S, NP, st);
+  launch_gemm<SOperands, true>(sop, static_cast<int64_t>(n_orb) * n_orb, NP, 4 * n_i, S, NP, partial, partial_elems,
+                               n_sm, st);
 }
 
 void launch_k_unpack(const double* S, int n_orb, double* K, int n_sm, cudaStream_t st) {

@@ -97,7 +97,7 @@ struct xtc_ctx {
   DBuf Lv, T3;                 // explicit three-body L: V of the outer points, the packed T
   DBuf fc_U, fc_h, fc_hout, fc_Uout;  // frozen-core folding: staged host inputs and outputs
   DBuf G2;                     // second gradient table: step (a) of the next chunk on stream st2
-  DBuf k_dphi, k_V, k_Ft, k_W, k_S;  // two-body integrals K: staged gradients, V, F table, W, S
+  DBuf k_dphi, k_V, k_Ft, k_W, k_S, k_P;  // two-body integrals K: staged gradients, V, F table, W, S, split-K slices
   cudaStream_t st2 = nullptr;  // created on first use
   cudaEvent_t ev_g[2] = {nullptr, nullptr};  // gradient table b written
   cudaEvent_t ev_b[2] = {nullptr, nullptr};  // step (b) GEMM that read table b done
@@ -122,7 +122,7 @@ struct xtc_ctx {
     return {&jp_dev, &err_dev, &flag_dev, &grid, &w, &phi, &gamma, &phiT, &phi32, &pair_p, &pair_q, &jtab, &jtab64,
             &rho, &colmax, &colexp, &G, &V, &Vacc, &L, &R, &L32, &R32, &eL, &eR, &M, &evec, &lam, &dU_tmp,
             &dh_tmp, &e0_tmp, &vout, &r1, &r2, &lamd, &gamma_b, &M2, &M3, &lam2, &R2, &R32b, &eR2, &Lv, &T3,
-            &fc_U, &fc_h, &fc_hout, &fc_Uout, &G2, &k_dphi, &k_V, &k_Ft, &k_W, &k_S};
+            &fc_U, &fc_h, &fc_hout, &fc_Uout, &G2, &k_dphi, &k_V, &k_Ft, &k_W, &k_S, &k_P};
   }
 };
 
@@ -1386,7 +1386,8 @@ extern "C" int xtc_two_body_K(xtc_ctx* ctx, int64_t n_grid, int n_orb, const dou
     ch = std::min<int64_t>(std::min<int64_t>(ch, n_i), int64_t{65535} * 64);  // grid.y of the W GEMM
     const size_t s_bytes = static_cast<size_t>(N) * N * NP * 8;
     if (!ensure(ctx->k_S, s_bytes) || !ensure(ctx->k_V, static_cast<size_t>(ch) * 3 * NP * 8) ||
-        !ensure(ctx->k_W, static_cast<size_t>(ch) * NP * 8) || !ensure(ctx->k_Ft, static_cast<size_t>(ch) * n_grid * 8))
+        !ensure(ctx->k_W, static_cast<size_t>(ch) * NP * 8) || !ensure(ctx->k_Ft, static_cast<size_t>(ch) * n_grid * 8) ||
+        !ensure(ctx->k_P, static_cast<size_t>(4) * ctx->n_sm * 4096 * 8))
       return fail(ctx, XTC_ERR_OOM, "two_body_K workspace (%.2f GB)",
                   (s_bytes + static_cast<size_t>(ch) * per_point) * 1e-9);
     CUDA_OK(cudaMemsetAsync(ctx->k_S.p, 0, s_bytes, st));
@@ -1410,7 +1411,8 @@ extern "C" int xtc_two_body_K(xtc_ctx* ctx, int64_t n_grid, int n_orb, const dou
       }
       launch_k_chunk(d_grid, d_w, d_phi, d_dphi, ctx->jp_dev.as<JastrowParams>(), n_grid, N, ctx->pair_p.as<int>(),
                      ctx->pair_q.as<int>(), c0, n_c, ctx->k_V.as<double>(), ctx->k_Ft.as<double>(),
-                     ctx->k_W.as<double>(), ctx->k_S.as<double>(), ctx->n_sm, st);
+                     ctx->k_W.as<double>(), ctx->k_S.as<double>(), ctx->k_P.as<double>(),
+                     static_cast<int64_t>(4) * ctx->n_sm * 4096, ctx->n_sm, st);
       CUDA_OK(cudaGetLastError());
     }
     launch_k_unpack(ctx->k_S.as<double>(), N, Kd, ctx->n_sm, st);

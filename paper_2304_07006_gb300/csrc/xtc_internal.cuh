@@ -254,11 +254,12 @@ void launch_three_body_t(const double* phi, const double* w, int64_t i0, int64_t
                          const int* pair_q, const double* V, double* T, cudaStream_t st);
 void launch_three_body_unpack(const double* T, int n_orb, double* L, cudaStream_t st);
 // Two-body integrals K: one chunk of outer points [i0, i0 + n_i) adds into S (N^2 x n_pair, FP64)
-// from V of the chunk ([n_i][3][n_pair]); Ft (n_grid x n_i) and W (n_i x n_pair) are workspace.
+// from V of the chunk ([n_i][3][n_pair]); Ft (n_grid x n_i), W (n_i x n_pair) and partial
+// (split-K slices of small GEMMs, partial_elems doubles; 4 x n_sm x 4096 suffice) are workspace.
 void launch_k_chunk(const double* grid, const double* w, const double* phi, const double* dphi,
                     const JastrowParams* jp_dev, int64_t n_grid, int n_orb, const int* pair_p, const int* pair_q,
-                    int64_t i0, int64_t n_i, const double* V, double* Ft, double* W, double* S, int n_sm,
-                    cudaStream_t st);
+                    int64_t i0, int64_t n_i, const double* V, double* Ft, double* W, double* S, double* partial,
+                    int64_t partial_elems, int n_sm, cudaStream_t st);
 // K[p][q][r][s] = S[pq][rs] + S[rs][pq].
 void launch_k_unpack(const double* S, int n_orb, double* K, int n_sm, cudaStream_t st);
 // Spin builds: U = Delta U^{ab} = -(Fb + Fa^T) (packed pairs, row stride m_stride(n_pair)).
