@@ -3,8 +3,9 @@
 
 The Laplacian table, its product with the pair densities and the contraction are FP64 on the GPU;
 V comes from steps (a)+(b) in the context's precision, so the mixed paths carry V's split error
-(tolerance 1e-5 of max |K|, as for the three-body L; 1e-11 in FP64).  The cases span several 64-wide tiles of every
-GEMM dimension with ragged tails (N = 13: N^2 = 169 rows, 91 pairs; 210 and 600 grid points)."""
+(measured 2.2e-7 for fp16x2 and 9.5e-8 for bf16x3 of max |K| on the 13-orbital case; the tests allow
+2e-6, and 1e-11 in FP64).  The cases span several 64-wide tiles of every GEMM dimension with ragged
+tails (N = 13: N^2 = 169 rows, 91 pairs; 210 and 600 grid points)."""
 import numpy as np
 import pytest
 
@@ -13,7 +14,7 @@ from oracle import two_body_k
 
 pytestmark = pytest.mark.gpu
 
-REL = {"fp64": 1e-11, "fp16x2": 1e-5, "bf16x3": 1e-5}
+REL = {"fp64": 1e-11, "fp16x2": 2e-6, "bf16x3": 2e-6}
 
 
 def ctx_for(p, prec, **kw):
